@@ -1,0 +1,17 @@
+"""CPU ORACLE for fast polynomial evaluation -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously correct CPU restatement of Algorithm A_p of
+Anton, Mihalache and Vigneron, "Fast Evaluation of Real and Complex
+Polynomials" (arXiv 2211.06320): exact scales and concave cover, the good
+index set G_p, the per-point windows, and extended double-double Horner
+sums.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import, call or link it.  It shares no code with the CUDA
+path and never imports it.
+"""
+from .fpe_oracle import (NEG_INF, ExtValues, Preconditioned, concave_cover, cover_value, fpe_eval,
+                         good_mask, horner_ref, log2_abs, num_threads, offset_T, precondition, scale,
+                         scale_of_int, window_sum, windows, windows_bruteforce)
+
+__all__ = ["NEG_INF", "ExtValues", "Preconditioned", "concave_cover", "cover_value", "fpe_eval",
+           "good_mask", "horner_ref", "log2_abs", "num_threads", "offset_T", "precondition", "scale",
+           "scale_of_int", "window_sum", "windows", "windows_bruteforce"]
