@@ -1,0 +1,318 @@
+"""Benchmark: polynomial evaluations/s of the fast polynomial evaluator
+(Algorithm A_p of arXiv 2211.06320) on the GPU, at d = 2^20.
+
+Workload (default): d = 2^20, a_k uniform in the unit disk (seed 1), 2^20
+sphere-uniform points per GPU, p = 53, FP64.  A step is one fpe_eval call over
+all points (locate, bucket, window sums, valuation power); the polynomial is
+preconditioned once before timing (reported separately, as the paper does).
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
+2^20 points of the same polynomial (weak scaling, no collective on the data
+path); value = all ranks' evaluations / max-over-ranks time.
+
+--impl reference times the CPU oracle (the plain restatement of the method)
+on this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "polynomial evaluations/s at d=2^20 (FPE vs GPU Horner, same accuracy), % of roofline"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fpe", choices=["fpe", "reference"])
+    ap.add_argument("--points", type=int, default=1 << 20)
+    ap.add_argument("--degree", type=int, default=1 << 20)
+    ap.add_argument("--no-extras", action="store_true", help="skip Horner baselines, accuracy and CPU legs")
+    return ap.parse_args()
+
+
+def workload(args, rank: int = 0):
+    import workloads as W
+    wl = W.unit_disk_d2pow20(n_points=args.points, d=args.degree)
+    if rank:  # each rank its own points, same polynomial
+        rng = np.random.default_rng(1000 + rank)
+        wl.points = W.sphere_points(args.points, rng)
+    return wl
+
+
+def config(args, flush: bool):
+    return {"workload": f"unit_disk_complex d={args.degree} (a_k uniform in unit disk, seed 1), "
+                        f"{args.points} sphere-uniform points per GPU, p=53",
+            "degree": args.degree, "points_per_gpu": args.points, "p": 53,
+            "l2": "flushed between steps (256 MiB write)" if flush else "not flushed"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_cpu_baseline(wl, n_sample: int):
+    """Algorithm A_p restated by the CPU oracle on a bounded sample of points."""
+    import oracle
+    t0 = time.perf_counter()
+    pre = oracle.precondition(wl.coeffs, wl.p)
+    t_pre = time.perf_counter() - t0
+    zr, zi = wl.points.re[:n_sample], wl.points.im[:n_sample]
+    oracle.fpe_eval(pre, zr[:16], zi[:16])  # warm-up (builds the C part)
+    t0 = time.perf_counter()
+    oracle.fpe_eval(pre, zr, zi)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_sample} of the workload's points (Alg. A_p windows + extended double-double "
+                      f"window sums); preconditioning {t_pre:.2f} s not included"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args)
+    n_sample = 4096
+    steps = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        b = oracle_cpu_baseline(wl, n_sample)
+        if i >= args.warmup:
+            steps.append(b["value"])
+        base = b
+    v = float(np.median(steps))
+    base["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_sample / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, False), "cpu_baseline": base,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_2211_06320_gb300 as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    F._load()
+
+    wl = workload(args, rank)
+    n = wl.points.n
+    t0 = time.perf_counter()
+    P = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, None, 53)
+    t_pre = time.perf_counter() - t0
+    zr = torch.from_numpy(wl.points.re).cuda()
+    zi = torch.from_numpy(wl.points.im).cuda()
+    out = F.empty_out(n)
+    nterms = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        F.fpe_eval(P, zr, zi, out, nterms)
+    F.fpe_sync(P)
+    # per-point work counts of this workload (same every step)
+    nt = nterms.cpu().numpy().astype(np.int64)
+    l, r, _ = F.fpe_get_windows(P, n)
+    L = (r - l + 1).cpu().numpy()
+
+    # timed region: K steps, L2 flushed between steps, each step's eval timed by events
+    F.fpe_profile_reset()
+    F.fpe_profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(st)
+        F.fpe_eval(P, zr, zi, out, nterms)
+        ev[i][1].record(st)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    F.fpe_profile_enable(False)
+    F.fpe_sync(P)
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    t_dev = float(step_ms.sum()) / 1e3
+    k_short, n_short = F.fpe_profile_read("k_sum_short")
+    k_long, n_long = F.fpe_profile_read("k_sum_groups")
+    k_fin, _ = F.fpe_profile_read("k_finalize_long")
+    k_all, launches = F.fpe_profile_read("")
+    if world > 1:
+        t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = world * n * args.steps / t_dev
+
+    extras = {}
+    if rank == 0:
+        # roofline of the dominant kernel: algorithmic FP64 flops of the kept terms
+        # (8 per complex x complex term, eq. complexityAlgo's Horner part) / its event time
+        long_mask = L > 4096
+        fl_short = 8.0 * float(nt[~long_mask].sum())
+        fl_long = 8.0 * float(nt[long_mask].sum())
+        fma_peak = F.fpe_measure_fma_peak(64, 5)
+        peak_tflops = 2.0 * fma_peak / 1e12
+        kern = {"k_sum_short": (k_short / max(n_short, 1), fl_short),
+                "k_sum_groups": (k_long / max(n_long, 1), fl_long)}
+        dom = max(kern, key=lambda k: kern[k][0])
+        ms, fl = kern[dom]
+        achieved = fl / (ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                    "peak_source": "measured: fpe_measure_fma_peak(64) on this GPU in this run (FP64 FMA x2)",
+                    "share": {k: (v[0] * args.steps) / max(k_all, 1e-9) for k, v in kern.items()},
+                    "all_window_kernels_frac": ((fl_short + fl_long) / ((k_short + k_long + k_fin) / args.steps
+                                                                        * 1e-3) / 1e12 / peak_tflops),
+                    "whole_step_frac": (fl_short + fl_long) / (float(step_ms.mean()) * 1e-3) / 1e12 / peak_tflops,
+                    "flops_per_launch": fl, "launch_ms": ms,
+                    "algorithmic_flops": "8 per kept complex term (4 FMA: one complex multiply-add of "
+                                         "Horner's scheme on G_p cap [l, r])"}
+        extras["roofline"] = roofline
+        extras["gpu_launches"] = int(launches)
+        extras["avg_kept_terms"] = float(nt.mean())
+        extras["avg_window"] = float(L.mean())
+        extras["precondition_ms"] = t_pre * 1e3
+        extras["wall_s_timed_region"] = wall
+
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        hz_r = torch.from_numpy(wl.points.re).pin_memory()
+        hz_i = torch.from_numpy(wl.points.im).pin_memory()
+        hout = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            F.host_eval_raw(P, hz_r.data_ptr(), hz_i.data_ptr(), n, hout.data_ptr())
+        t0 = time.perf_counter()
+        e2e_steps = max(3, min(args.steps, 10))
+        for _ in range(e2e_steps):
+            s = F.host_eval_raw(P, hz_r.data_ptr(), hz_i.data_ptr(), n, hout.data_ptr())
+            assert s == 0
+        dt = time.perf_counter() - t0
+        extras["e2e"] = {"value": n * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+                         "d2h_bytes_per_step": 24 * n}
+
+        if not args.no_extras:
+            # GPU Horner baselines over all d+1 terms (subset of points: per-point work is fixed)
+            for comp, m in ((False, 1 << 14), (True, 1 << 12)):
+                sub_r, sub_i = zr[:m].contiguous(), zi[:m].contiguous()
+                o2 = F.empty_out(m)
+                F.fpe_horner(P, sub_r, sub_i, compensated=comp, out=o2)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                F.fpe_horner(P, sub_r, sub_i, compensated=comp, out=o2)
+                b.record(st)
+                torch.cuda.synchronize()
+                extras["horner_compensated_evals_per_s" if comp else "horner_plain_evals_per_s"] = \
+                    m / (a.elapsed_time(b) * 1e-3)
+            # accuracy on a sample against the oracle's extended-precision Horner
+            import oracle
+            sample = np.unique(np.concatenate([np.arange(48), np.argsort(-L)[:16]]))
+            ref, (Sm, Se), _ = oracle.horner_ref(wl.coeffs, wl.points.re[sample], wl.points.im[sample])
+            got = out.cpu().numpy()[sample]
+            ge = np.ascontiguousarray(got[:, 2]).view(np.int64)
+            sc = lambda mm, ee: np.ldexp(mm, np.clip(ee - Se, -2000, 2000).astype(np.int32))
+            err = np.hypot(sc(got[:, 0], ge) - sc(ref.re_hi, ref.e) - sc(ref.re_lo, ref.e),
+                           sc(got[:, 1], ge) - sc(ref.im_hi, ref.e) - sc(ref.im_lo, ref.e)) / Sm
+            extras["accuracy"] = {"max_err_over_S": float(err.max()), "tolerance": 2.0 ** -50,
+                                  "sample_points": int(sample.size)}
+            # FPE_ACCURATE throughput (compensated window sums)
+            PA = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, None, 53, F.FPE_ACCURATE)
+            F.fpe_eval(PA, zr, zi, out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            F.fpe_eval(PA, zr, zi, out)
+            b.record(st)
+            torch.cuda.synchronize()
+            extras["fpe_accurate_evals_per_s"] = n / (a.elapsed_time(b) * 1e-3)
+            extras["cpu_baseline"] = oracle_cpu_baseline(wl, 4096)
+
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config(args, True), "clocks": clk}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * fpe.h -- C ABI of a GPU (sm_103a) implementation of the fast polynomial
+ * evaluator of Anton, Mihalache and Vigneron, "Fast Evaluation of Real and
+ * Complex Polynomials" (arXiv 2211.06320).
+ *
+ * Problem (Alg. A_p, §4.3): given coefficients a_0..a_d and a precision p,
+ * precondition once (scales s(a_k), concave cover of k -> s(a_k), good index
+ * set G_p), then evaluate at many points z the reduced polynomial
+ *     Q_lambda(z) = sum_{k in G_p cap [l, r]} a_k z^k          (eq. reducedQlambda)
+ * where lambda = log2|z| and [l, r] is the largest integer interval on which
+ * the cover plus lambda*k stays within T = p + s(d) + 3 of its maximum N
+ * (def. LRN).  Thm. equivAlgo: Q_lambda(z) is as accurate as Horner over all
+ * terms.
+ *
+ * Conventions for every call:
+ *  - Errors are returned, never thrown; nothing is written to outputs on an
+ *    argument error.  Device-side conditions (non-finite points) are recorded
+ *    in the handle and returned by fpe_sync().
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device (e.g. torch tensor data); "host" pointers are ordinary memory.
+ *  - The caller owns every buffer it passes; a handle owns its own device
+ *    copies and its scratch memory, freed by fpe_destroy().
+ *  - Calls on one handle must not run concurrently from several host threads,
+ *    and evaluations on one handle must not overlap on different streams
+ *    (they share the handle's scratch memory).  fpe_destroy() must not race
+ *    with work in flight on the handle.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream); the
+ *    evaluation calls are asynchronous on it unless stated otherwise.
+ */
+#ifndef FPE_H_
+#define FPE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque preconditioned polynomial (host metadata plus device arrays). */
+typedef struct fpe_poly_s *fpe_poly_t;
+
+/* Extended-exponent complex value (re + i*im) * 2^e.  Normalised:
+ * max(|re|, |im|) lies in [0.5, 1), or re = im = 0 and e = 0.  24 bytes. */
+typedef struct {
+  double re, im;
+  int64_t e;
+} fpe_xc64;
+
+typedef enum {
+  FPE_OK = 0,
+  FPE_ERR_INVALID_ARG = 1, /* NULL handle/pointer, negative size, bad p or flags  */
+  FPE_ERR_NONFINITE = 2,   /* a coefficient or an evaluation point is NaN or inf  */
+  FPE_ERR_ZERO_POLY = 3,   /* every coefficient is zero                           */
+  FPE_ERR_OOM = 4,         /* host or device allocation failed                    */
+  FPE_ERR_CUDA = 5,        /* a CUDA runtime call failed (see fpe_last_error)     */
+  FPE_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                  */
+  FPE_ERR_UNSUPPORTED = 7  /* valid request this build does not implement         */
+} fpe_status;
+
+/* fpe_precondition flags */
+enum {
+  FPE_REAL = 1,        /* treat the coefficients as real (im ignored)           */
+  FPE_WITH_DERIV = 2,  /* also precondition P' for fpe_eval_deriv               */
+  FPE_FP32 = 4,        /* evaluate in FP32 mantissas (requires p <= 24)         */
+  FPE_HOST_ONLY = 8,   /* host analysis only (scales, cover, G_p; the -analyse
+                          task of §8.1): no device memory is touched and the
+                          handle cannot be evaluated                           */
+  FPE_ACCURATE = 16    /* compensated window sums: error <= u|P| + gamma^2 S
+                          for every input, at ~10x the FP64 work (see fpe_eval) */
+};
+
+/*
+ * fpe_precondition -- preconditioning of Alg. A_p (lines 2-4; §5.1).
+ *
+ * Computes the exact integer scales s(a_k) = 1 + floor(log2|a_k|) (eq. dsz),
+ * the concave cover of k -> s(a_k) over the nonzero coefficients (def. EP),
+ * the offset T = p + s(d) + 3 and the good set G_p = {k : s(a_k) >= cover(k)
+ * - T} (eq. threshold), then uploads the coefficients to the current device
+ * with bad ones zeroed.
+ *
+ *   re, im   host arrays of n_coef doubles: a_k = (re[k] + i*im[k]) * 2^e2[k].
+ *            im == NULL (or flag FPE_REAL) gives a real polynomial.
+ *   e2       host array of n_coef int64 binary exponents, or NULL for all 0;
+ *            lets coefficients exceed the FP64 range.  |e2[k]| < 2^40.
+ *   n_coef   d + 1 >= 1 (leading zeros are trimmed: d is the last nonzero
+ *            index, v the first; z^v is factored out as in §4.3).
+ *   p        precision in significand bits, 2 <= p <= 53 (p <= 24 with FPE_FP32).
+ *   flags    FPE_REAL | FPE_WITH_DERIV | FPE_FP32 | FPE_HOST_ONLY | FPE_ACCURATE.
+ *   out      receives the handle.
+ * Synchronous (uploads finish before return).  Errors: FPE_ERR_INVALID_ARG,
+ * FPE_ERR_NONFINITE (a coefficient is NaN/inf), FPE_ERR_ZERO_POLY, FPE_ERR_OOM,
+ * FPE_ERR_CUDA.
+ */
+fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e2, int64_t n_coef, int p,
+                            uint32_t flags, fpe_poly_t *out);
+
+/*
+ * fpe_eval -- evaluation of Alg. A_p (lines 6-11; §5.2) at n points.
+ *
+ * For each point: lambda = log2|z| (eq. defLambda), k_lambda = argmax of
+ * cover(k) + lambda*k by binary search on the cover's slopes (eq. defN),
+ * [l, r] by two binary searches (def. LRN), and
+ *     out[j] = z^l * sum_{k in G_p cap [l, r]} a_k z^{k-l}
+ * summed by Horner over the window (eq. complexityAlgo) with exact
+ * power-of-two rescaling, so no intermediate overflows.  z = 0 gives a_0.
+ *
+ *   z_re, z_im  device arrays of n doubles; z_im == NULL means real points.
+ *   n           number of points, 0 <= n < 2^31.
+ *   out         device array of n fpe_xc64 (the value of P(z_j)).
+ *   nterms      device int32[n] or NULL: #(G_p cap [l, r]) per point.
+ *   bits_lost   device int32[n] or NULL: estimated leading bits cancelled,
+ *               max(0, ceil(N) - e) (Remark rmk:cancel, eq. slice).
+ * Summation: by default each window is summed in FP64 toward its peak term
+ * (top-down above k_lambda, bottom-up with a double-double 1/z below), which
+ * keeps |P_gpu - P| within 2^-50 sum |a_k||z|^k for coefficients of random
+ * phase; long runs of aligned terms (e.g. all a_k = 1 near z = 1) or of
+ * negligible terms after a dominant one can exceed it by a small factor.
+ * With FPE_ACCURATE the window is summed by compensated Horner (error-free
+ * transformations), which bounds the error by u|P| + gamma_2n^2 S for every
+ * input.
+ * Asynchronous on cuda_stream.  The first call (and any call with a larger n
+ * than before) allocates scratch memory on the handle.  Non-finite points
+ * give NaN outputs and FPE_ERR_NONFINITE from the next fpe_sync().
+ */
+fpe_status fpe_eval(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                    int32_t *nterms, int32_t *bits_lost, void *cuda_stream);
+
+/*
+ * fpe_eval_host -- fpe_eval on host buffers: copies z to the device, evaluates,
+ * copies the results back and waits for them.  Same arguments as fpe_eval
+ * with host pointers (nterms, bits_lost may be NULL).  Synchronous; returns
+ * the device-side status as fpe_sync() would.
+ */
+fpe_status fpe_eval_host(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                         int32_t *nterms, int32_t *bits_lost);
+
+/*
+ * fpe_eval_deriv -- P'(z) (§7.2: derivative coefficients j*a_j, rounded once
+ * to the FP64 mantissa, preconditioned separately as the paper allows).
+ * Requires FPE_WITH_DERIV at preconditioning, else FPE_ERR_INVALID_ARG.
+ * Arguments as fpe_eval (device pointers).
+ */
+fpe_status fpe_eval_deriv(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                          void *cuda_stream);
+
+/*
+ * fpe_eval_batch -- many polynomials, each at its own points (§8.1: the
+ * algorithm is embarrassingly parallel over points).  Polynomial i is
+ * evaluated at points pt_offsets[i] .. pt_offsets[i+1]-1.
+ *   P           host array of npoly handles (all on the current device,
+ *               all FP64 or all FP32).
+ *   pt_offsets  HOST array of npoly+1 nondecreasing int64, pt_offsets[0] = 0.
+ *   z_re, z_im  device arrays of pt_offsets[npoly] doubles (z_im may be NULL).
+ *   out         device array of pt_offsets[npoly] fpe_xc64.
+ * Asynchronous; one launch per kernel stage for the whole batch.
+ */
+fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,
+                          const double *z_im, fpe_xc64 *out, void *cuda_stream);
+
+/*
+ * fpe_horner -- the plain form beside FPE: Horner's scheme over all d+1
+ * coefficients (§1, "Horner's scheme") on the GPU, with exact power-of-two
+ * renormalisation so that no intermediate overflows.
+ *   compensated = 0: FP64 Horner (4 FMA per complex term).
+ *   compensated = 1: compensated Horner with error-free transformations
+ *                    (TwoSum, FMA TwoProd; the compensated schemes cited in
+ *                    §1), about 2^-53 relative error plus a second-order term.
+ * Arguments as fpe_eval (device pointers).  Asynchronous.
+ */
+fpe_status fpe_horner(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                      int compensated, void *cuda_stream);
+
+/* fpe_info -- degree d (last nonzero index), valuation v (first nonzero index),
+ * number of cover vertices, |G_p|, and T = p + s(d) + 3.  Any output may be NULL. */
+fpe_status fpe_info(fpe_poly_t P, int64_t *d, int64_t *valuation, int64_t *n_hull, int64_t *n_good, int *T);
+
+/* fpe_get_hull -- the cover's vertices (k_i, s(a_{k_i})) in untrimmed indices,
+ * left to right, strict vertices only.  k, s: host arrays of capacity cap >= n_hull. */
+fpe_status fpe_get_hull(fpe_poly_t P, int64_t *k, int64_t *s, int64_t cap);
+
+/* fpe_get_good -- G_p as a host 0/1 mask of n_coef bytes (untrimmed indices). */
+fpe_status fpe_get_good(fpe_poly_t P, uint8_t *mask, int64_t n_coef);
+
+/* fpe_get_windows -- the per-point data of the last fpe_eval on this handle,
+ * for inspection: l, r (untrimmed; l > r for z = 0) and N (eq. defN), as
+ * device arrays of n entries in the caller's point order.  Asynchronous. */
+fpe_status fpe_get_windows(fpe_poly_t P, int64_t n, int64_t *l, int64_t *r, double *N, void *cuda_stream);
+
+/* fpe_sync -- wait for the stream and return the first device-side status
+ * recorded on the handle since the last fpe_sync (then clear it). */
+fpe_status fpe_sync(fpe_poly_t P, void *cuda_stream);
+
+/* fpe_destroy -- free the handle and its device memory.  NULL is a no-op. */
+void fpe_destroy(fpe_poly_t P);
+
+/* fpe_status_string -- static description of a status code. */
+const char *fpe_status_string(fpe_status s);
+
+/* fpe_last_error -- thread-local message for the last failing call (static storage). */
+const char *fpe_last_error(void);
+
+/*
+ * Kernel timing (measurement support, no counterpart in the paper).  When
+ * enabled, every kernel launch of this library records CUDA events around
+ * itself on its launching stream; fpe_profile_read() synchronises with the
+ * events and returns, for kernels whose name contains `name`, the total
+ * device time in milliseconds and the number of launches since the last reset.
+ */
+void fpe_profile_enable(int on);
+void fpe_profile_reset(void);
+fpe_status fpe_profile_read(const char *name, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPE_H_ */

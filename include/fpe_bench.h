@@ -1,0 +1,33 @@
+/*
+ * fpe_bench.h -- measurement support for libfpe (no counterpart in the paper).
+ *
+ * The evaluation kernels of fpe.h are bound by the FP64 FMA pipe, whose peak
+ * is not a published constant for this GPU; this call measures it on the
+ * current device so that roofline fractions use a denominator taken on the
+ * same GPU at the same time.
+ */
+#ifndef FPE_BENCH_H_
+#define FPE_BENCH_H_
+
+#include "fpe.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * fpe_measure_fma_peak -- FMA throughput of the current device.
+ *   precision   64 for FP64 (double) FMA, 32 for FP32 (float) FMA.
+ *   fma_per_s   receives the best of `reps` timed launches, in fused
+ *               multiply-adds per second (flop/s is twice that).
+ *   reps        >= 1 timed launches after one warm-up launch.
+ * Each launch runs 8 independent FMA chains per thread on 4 blocks of 256
+ * threads per SM.  Synchronous (uses its own CUDA events on the legacy
+ * default stream).  Errors: FPE_ERR_INVALID_ARG, FPE_ERR_CUDA.
+ */
+fpe_status fpe_measure_fma_peak(int precision, int reps, double *fma_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPE_BENCH_H_ */

@@ -217,22 +217,79 @@ void oracle_horner(int64_t n_coef, const double *are, const double *aim, const d
   }
 }
 
+/* S over a window: sum over k in [lo, hi] with good[k] of |a_k| |z|^k, as (m, e) */
+static void window_abs_sum(int64_t lo, int64_t hi, double az, const double *are, const double *aim,
+                           const double *are_lo, const double *aim_lo, const int64_t *ae,
+                           const uint8_t *good, double *Sm, int64_t *Se) {
+  double sm = 0.0;
+  int64_t se = 0;
+  int fz;
+  double mz = frexp(az, &fz);
+  for (int64_t k = hi; k >= lo; --k) {
+    if (sm != 0.0) {
+      sm *= mz;
+      se += fz;
+    }
+    if (good && !good[k]) continue;
+    double ar = are[k] + (are_lo ? are_lo[k] : 0.0);
+    double ai = (aim ? aim[k] : 0.0) + (aim_lo ? aim_lo[k] : 0.0);
+    double am = hypot(ar, ai);
+    if (am == 0.0) continue;
+    int fa;
+    double ma = frexp(am, &fa);
+    int64_t ea = (ae ? ae[k] : 0) + fa;
+    if (sm == 0.0) {
+      sm = ma;
+      se = ea;
+    } else {
+      int64_t sh = ea - se;
+      if (sh > 1000) {
+        sm = ma;
+        se = ea;
+      } else if (sh >= -1100) {
+        sm += ldexp(ma, (int)sh);
+      }
+    }
+    int f;
+    sm = frexp(sm, &f);
+    se += f;
+  }
+  if (sm != 0.0 && lo > 0) { /* times |z|^lo = 2^(lo log2|z|) */
+    double t = (double)lo * log2(az);
+    double fl = floor(t);
+    sm *= exp2(t - fl);
+    int f;
+    sm = frexp(sm, &f);
+    se += (int64_t)fl + f;
+  }
+  *Sm = sm;
+  *Se = se;
+}
+
 void oracle_window_sum(int64_t n_coef, const double *are, const double *aim, const double *are_lo,
                        const double *aim_lo, const int64_t *ae, const uint8_t *good, int64_t npts,
                        const double *zre, const double *zim, const int64_t *lo, const int64_t *hi,
-                       double *out, int64_t *oute) {
+                       double *out, int64_t *oute, double *S_m, int64_t *S_e) {
   (void)n_coef;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t j = 0; j < npts; ++j) {
     xdd z = xdd_from(zre[j], 0.0, zim ? zim[j] : 0.0, 0.0, 0);
     xdd v;
+    double sm = 0.0;
+    int64_t se = 0;
     if (hi[j] < lo[j]) {
       v = xdd_from(0.0, 0.0, 0.0, 0.0, 0);
     } else {
       xdd h = horner_range(lo[j], hi[j], z, are, aim, are_lo, aim_lo, ae, good);
       v = xdd_mul(h, xdd_pow(z, lo[j]));
+      if (S_m) window_abs_sum(lo[j], hi[j], hypot(zre[j], zim ? zim[j] : 0.0), are, aim, are_lo, aim_lo, ae,
+                              good, &sm, &se);
     }
     store(v, j, out, oute);
+    if (S_m) {
+      S_m[j] = sm;
+      S_e[j] = se;
+    }
   }
 }
 

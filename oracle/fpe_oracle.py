@@ -385,7 +385,7 @@ def _load():
         I = ctypes.c_int64
         lib.oracle_horner.argtypes = [I, P, P, P, P, P, I, P, P, P, P, P, P, P]
         lib.oracle_horner.restype = None
-        lib.oracle_window_sum.argtypes = [I, P, P, P, P, P, P, I, P, P, P, P, P, P]
+        lib.oracle_window_sum.argtypes = [I, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P]
         lib.oracle_window_sum.restype = None
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -436,8 +436,9 @@ def horner_ref(coef, zre, zim=None, coef_lo=None):
     return ExtValues(out, oute), (Sm, Se), lm
 
 
-def window_sum(coef, good: Optional[np.ndarray], zre, zim, lo, hi, coef_lo=None):
-    """sum over k in [lo_j, hi_j] with good[k] of a_k z_j^k (ext double-double)."""
+def window_sum(coef, good: Optional[np.ndarray], zre, zim, lo, hi, coef_lo=None, with_S: bool = False):
+    """sum over k in [lo_j, hi_j] with good[k] of a_k z_j^k (ext double-double);
+    with_S also returns the window's sum of |a_k||z_j|^k as (mantissa, exponent)."""
     lib = _load()
     are = _c(coef.re, np.float64)
     aim = _c(coef.im, np.float64)
@@ -452,8 +453,13 @@ def window_sum(coef, good: Optional[np.ndarray], zre, zim, lo, hi, coef_lo=None)
     n = zre.shape[0]
     out = np.zeros((n, 4))
     oute = np.zeros(n, dtype=np.int64)
+    Sm = np.zeros(n) if with_S else None
+    Se = np.zeros(n, dtype=np.int64) if with_S else None
     lib.oracle_window_sum(are.shape[0], _ptr(are), _ptr(aim), _ptr(are_lo), _ptr(aim_lo), _ptr(ae),
-                          _ptr(g), n, _ptr(zre), _ptr(zim), _ptr(lo), _ptr(hi), _ptr(out), _ptr(oute))
+                          _ptr(g), n, _ptr(zre), _ptr(zim), _ptr(lo), _ptr(hi), _ptr(out), _ptr(oute),
+                          _ptr(Sm), _ptr(Se))
+    if with_S:
+        return ExtValues(out, oute), (Sm, Se)
     return ExtValues(out, oute)
 
 
@@ -486,7 +492,7 @@ def precondition(coef, p: int) -> Preconditioned:
     return Preconditioned(coef, p)
 
 
-def fpe_eval(pre: Preconditioned, zre, zim=None):
+def fpe_eval(pre: Preconditioned, zre, zim=None, with_S: bool = False):
     """Algorithm A_p evaluation (lines 6-11): returns (values, (k_lambda, N, l, r)).
     At z = 0 the value is a_0 (§4.2: P(0) = a_0 is immediately available)."""
     lam = log2_abs(np.asarray(zre, dtype=np.float64), None if zim is None else np.asarray(zim, dtype=np.float64))
@@ -496,5 +502,5 @@ def fpe_eval(pre: Preconditioned, zre, zim=None):
     R2 = R.copy()
     L2[zero] = 0
     R2[zero] = 0  # window {0}: P(0) = a_0 (0 when a_0 = 0)
-    vals = window_sum(pre.coef, pre.good, zre, zim, L2, R2)
+    vals = window_sum(pre.coef, pre.good, zre, zim, L2, R2, with_S=with_S)
     return vals, (kl, N, L, R)

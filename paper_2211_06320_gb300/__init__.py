@@ -1,0 +1,299 @@
+"""Python binding of ``libfpe.so`` (include/fpe.h): fast evaluation of real and
+complex polynomials (arXiv 2211.06320, Algorithm A_p) on a GB300 GPU.
+
+Argument marshalling only: every step of preconditioning and evaluation runs
+in the C/CUDA library.  Device buffers are torch CUDA tensors (float64 for
+points; results as an (n, 3) float64 tensor whose rows are the C struct
+fpe_xc64 = {re, im, e}, e stored as int64 bits -- see ``split_xc64``).
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+FPE_OK = 0
+FPE_ERR_INVALID_ARG = 1
+FPE_ERR_NONFINITE = 2
+FPE_ERR_ZERO_POLY = 3
+FPE_ERR_OOM = 4
+FPE_ERR_CUDA = 5
+FPE_ERR_TIMEOUT = 6
+FPE_ERR_UNSUPPORTED = 7
+
+FPE_REAL = 1
+FPE_WITH_DERIV = 2
+FPE_FP32 = 4
+FPE_HOST_ONLY = 8
+FPE_ACCURATE = 16
+
+# every symbol include/fpe.h declares
+EXPORTED = [
+    "fpe_precondition", "fpe_eval", "fpe_eval_host", "fpe_eval_deriv", "fpe_eval_batch", "fpe_horner",
+    "fpe_info", "fpe_get_hull", "fpe_get_good", "fpe_get_windows", "fpe_sync", "fpe_destroy",
+    "fpe_status_string", "fpe_last_error", "fpe_profile_enable", "fpe_profile_reset", "fpe_profile_read",
+    "fpe_measure_fma_peak",
+]
+
+
+class FpeError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class XC64(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double), ("e", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()  # no-op when the in-tree library is up to date
+    lib = ctypes.CDLL(path)
+    P, I64, I32, U32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_double
+    sig = {
+        "fpe_precondition": ([P, P, P, I64, I32, U32, ctypes.POINTER(P)], I32),
+        "fpe_eval": ([P, P, P, I64, P, P, P, P], I32),
+        "fpe_eval_host": ([P, P, P, I64, P, P, P], I32),
+        "fpe_eval_deriv": ([P, P, P, I64, P, P], I32),
+        "fpe_eval_batch": ([P, I64, P, P, P, P, P], I32),
+        "fpe_horner": ([P, P, P, I64, P, I32, P], I32),
+        "fpe_info": ([P, P, P, P, P, P], I32),
+        "fpe_get_hull": ([P, P, P, I64], I32),
+        "fpe_get_good": ([P, P, I64], I32),
+        "fpe_get_windows": ([P, I64, P, P, P, P], I32),
+        "fpe_sync": ([P, P], I32),
+        "fpe_destroy": ([P], None),
+        "fpe_status_string": ([I32], ctypes.c_char_p),
+        "fpe_last_error": ([], ctypes.c_char_p),
+        "fpe_profile_enable": ([I32], None),
+        "fpe_profile_reset": ([], None),
+        "fpe_profile_read": ([ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], I32),
+        "fpe_measure_fma_peak": ([I32, I32, ctypes.POINTER(D)], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != FPE_OK:
+        lib = _load()
+        raise FpeError(st, where, lib.fpe_last_error().decode(errors="replace") or
+                       lib.fpe_status_string(st).decode())
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Poly:
+    """A preconditioned polynomial (owns an fpe_poly_t handle)."""
+
+    def __init__(self, handle: int, n_coef: int):
+        self._h = ctypes.c_void_p(handle)
+        self.n_coef = n_coef
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                _load().fpe_destroy(self._h)
+                self._h = ctypes.c_void_p(None)
+        except Exception:
+            pass
+
+
+def fpe_precondition(re, im=None, e2=None, p: int = 53, flags: int = 0) -> Poly:
+    """Preconditioning (Alg. A_p lines 2-4) of a_k = (re[k] + i im[k]) 2^e2[k]; host arrays."""
+    lib = _load()
+    re = np.ascontiguousarray(re, dtype=np.float64)
+    im = None if im is None else np.ascontiguousarray(im, dtype=np.float64)
+    e2 = None if e2 is None else np.ascontiguousarray(e2, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(lib.fpe_precondition(_np_ptr(re), _np_ptr(im), _np_ptr(e2), re.shape[0], int(p), int(flags),
+                                ctypes.byref(h)), "fpe_precondition")
+    return Poly(h.value, re.shape[0])
+
+
+def empty_out(n: int, device=None):
+    import torch
+    return torch.empty((n, 3), dtype=torch.float64, device=device or "cuda")
+
+
+def split_xc64(out):
+    """(re, im, e) of an (n, 3) fpe_xc64 array (torch tensor or numpy); e as int64."""
+    if isinstance(out, np.ndarray):
+        return out[:, 0].copy(), out[:, 1].copy(), np.ascontiguousarray(out[:, 2]).view(np.int64)
+    import torch
+    return out[:, 0], out[:, 1], out[:, 2].contiguous().view(torch.int64)
+
+
+def fpe_eval(P: Poly, z_re, z_im=None, out=None, nterms=None, bits_lost=None, stream=None):
+    """Evaluation (Alg. A_p lines 6-11) at device points; returns the (n, 3) result tensor."""
+    lib = _load()
+    n = int(z_re.shape[0])
+    if out is None:
+        out = empty_out(n, z_re.device)
+    _check(lib.fpe_eval(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _dptr(nterms), _dptr(bits_lost),
+                        _stream(stream)), "fpe_eval")
+    return out
+
+
+def fpe_eval_host(P: Poly, z_re: np.ndarray, z_im: Optional[np.ndarray] = None, want_diag: bool = False):
+    """fpe_eval on host buffers (copies in, evaluates, copies out, waits)."""
+    lib = _load()
+    z_re = np.ascontiguousarray(z_re, dtype=np.float64)
+    z_im = None if z_im is None else np.ascontiguousarray(z_im, dtype=np.float64)
+    n = z_re.shape[0]
+    out = np.zeros((n, 3), dtype=np.float64)
+    nt = np.zeros(n, dtype=np.int32) if want_diag else None
+    bl = np.zeros(n, dtype=np.int32) if want_diag else None
+    _check(lib.fpe_eval_host(P.handle, _np_ptr(z_re), _np_ptr(z_im), n, _np_ptr(out), _np_ptr(nt), _np_ptr(bl)),
+           "fpe_eval_host")
+    return (out, nt, bl) if want_diag else out
+
+
+def host_eval_raw(P: Poly, z_re_ptr: int, z_im_ptr: Optional[int], n: int, out_ptr: int) -> int:
+    """fpe_eval_host on raw host addresses (e.g. pinned torch tensors); returns the status."""
+    lib = _load()
+    return lib.fpe_eval_host(P.handle, ctypes.c_void_p(z_re_ptr), ctypes.c_void_p(z_im_ptr) if z_im_ptr else None,
+                             n, ctypes.c_void_p(out_ptr), None, None)
+
+
+def fpe_eval_deriv(P: Poly, z_re, z_im=None, out=None, stream=None):
+    lib = _load()
+    n = int(z_re.shape[0])
+    if out is None:
+        out = empty_out(n, z_re.device)
+    _check(lib.fpe_eval_deriv(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _stream(stream)), "fpe_eval_deriv")
+    return out
+
+
+def fpe_eval_batch(polys: Sequence[Poly], pt_offsets, z_re, z_im=None, out=None, stream=None):
+    lib = _load()
+    npoly = len(polys)
+    hs = (ctypes.c_void_p * npoly)(*[p.handle.value for p in polys])
+    offs = np.ascontiguousarray(pt_offsets, dtype=np.int64)
+    n = int(offs[-1]) if npoly else 0
+    if out is None:
+        out = empty_out(n, z_re.device)
+    _check(lib.fpe_eval_batch(hs, npoly, _np_ptr(offs), _dptr(z_re), _dptr(z_im), _dptr(out), _stream(stream)),
+           "fpe_eval_batch")
+    return out
+
+
+def fpe_horner(P: Poly, z_re, z_im=None, compensated: bool = False, out=None, stream=None):
+    """GPU Horner over all d+1 terms (plain or compensated)."""
+    lib = _load()
+    n = int(z_re.shape[0])
+    if out is None:
+        out = empty_out(n, z_re.device)
+    _check(lib.fpe_horner(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), int(bool(compensated)),
+                          _stream(stream)), "fpe_horner")
+    return out
+
+
+def fpe_info(P: Poly) -> dict:
+    lib = _load()
+    d, v, nh, ng = (ctypes.c_int64() for _ in range(4))
+    T = ctypes.c_int()
+    _check(lib.fpe_info(P.handle, ctypes.byref(d), ctypes.byref(v), ctypes.byref(nh), ctypes.byref(ng),
+                        ctypes.byref(T)), "fpe_info")
+    return {"d": d.value, "valuation": v.value, "n_hull": nh.value, "n_good": ng.value, "T": T.value}
+
+
+def fpe_get_hull(P: Poly):
+    lib = _load()
+    nh = fpe_info(P)["n_hull"]
+    k = np.zeros(nh, dtype=np.int64)
+    s = np.zeros(nh, dtype=np.int64)
+    _check(lib.fpe_get_hull(P.handle, _np_ptr(k), _np_ptr(s), nh), "fpe_get_hull")
+    return k, s
+
+
+def fpe_get_good(P: Poly):
+    lib = _load()
+    m = np.zeros(P.n_coef, dtype=np.uint8)
+    _check(lib.fpe_get_good(P.handle, _np_ptr(m), P.n_coef), "fpe_get_good")
+    return m
+
+
+def fpe_get_windows(P: Poly, n: int, stream=None):
+    import torch
+    lib = _load()
+    l = torch.empty(n, dtype=torch.int64, device="cuda")
+    r = torch.empty(n, dtype=torch.int64, device="cuda")
+    N = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(lib.fpe_get_windows(P.handle, n, _dptr(l), _dptr(r), _dptr(N), _stream(stream)), "fpe_get_windows")
+    return l, r, N
+
+
+def fpe_sync(P: Poly, stream=None):
+    _check(_load().fpe_sync(P.handle, _stream(stream)), "fpe_sync")
+
+
+def fpe_status_string(st: int) -> str:
+    return _load().fpe_status_string(int(st)).decode()
+
+
+def fpe_profile_enable(on: bool = True):
+    _load().fpe_profile_enable(int(bool(on)))
+
+
+def fpe_profile_reset():
+    _load().fpe_profile_reset()
+
+
+def fpe_profile_read(name: str = ""):
+    """(total device ms, launches) of this library's kernels whose name contains `name`."""
+    lib = _load()
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(lib.fpe_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(cnt)), "fpe_profile_read")
+    return ms.value, cnt.value
+
+
+def fpe_measure_fma_peak(precision: int = 64, reps: int = 5) -> float:
+    """Measured FMA/s of the current device (FP64 or FP32)."""
+    v = ctypes.c_double()
+    _check(_load().fpe_measure_fma_peak(int(precision), int(reps), ctypes.byref(v)), "fpe_measure_fma_peak")
+    return v.value

@@ -1,0 +1,296 @@
+// extern "C" entry points of fpe.h: argument checks, handle management,
+// host-buffer staging, and kernel timing.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fpe_internal.h"
+
+namespace fpe {
+const char *last_error_cstr();
+
+// ------------------------------------------------------------------ timing
+namespace {
+struct ProfRec {
+  std::string name;
+  cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+}  // namespace
+
+ProfScope::ProfScope(const char *n, cudaStream_t s) : name(n), st(s) {
+  if (!g_prof_on) return;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+}
+ProfScope::~ProfScope() {
+  if (!e0) return;
+  cudaEventRecord(e1, st);
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof.push_back({name, e0, e1});
+}
+
+static fpe_status check_eval_args(fpe_poly_t P, const double *z_re, int64_t n, const void *out) {
+  if (!P) {
+    set_error("NULL handle");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (P->flags & FPE_HOST_ONLY) {
+    set_error("handle was preconditioned with FPE_HOST_ONLY");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (n < 0 || n >= ((int64_t)1 << 31)) {
+    set_error("n must be in [0, 2^31)");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (n > 0 && (!z_re || !out)) {
+    set_error("NULL point or output pointer");
+    return FPE_ERR_INVALID_ARG;
+  }
+  return FPE_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace fpe
+
+using namespace fpe;
+
+extern "C" {
+
+fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e2, int64_t n_coef, int p,
+                            uint32_t flags, fpe_poly_t *out) {
+  return precondition_host(re, im, e2, n_coef, p, flags, out);
+}
+
+fpe_status fpe_eval(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                    int32_t *nterms, int32_t *bits_lost, void *cuda_stream) {
+  fpe_status s = check_eval_args(P, z_re, n, out);
+  if (s != FPE_OK) return s;
+  DeviceGuard g(P->device);
+  return launch_eval(P, z_re, z_im, n, out, nterms, bits_lost, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_eval_host(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                         int32_t *nterms, int32_t *bits_lost) {
+  fpe_status s = check_eval_args(P, z_re, n, out);
+  if (s != FPE_OK) return s;
+  if (n == 0) return FPE_OK;
+  DeviceGuard g(P->device);
+  // device staging: z (1 or 2 arrays), out, nterms, bits_lost
+  const size_t nz = (z_im ? 2 : 1) * n * sizeof(double);
+  const size_t no = n * sizeof(fpe_xc64), ni = n * sizeof(int32_t);
+  const size_t need = nz + no + 2 * ni + 256;
+  Workspace &w = P->ws;
+  cudaError_t e;
+  if (w.dev_io_bytes < need) {
+    if (w.dev_io) cudaFree(w.dev_io);
+    w.dev_io = nullptr;
+    w.dev_io_bytes = 0;
+    if ((e = cudaMalloc(&w.dev_io, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(io)");
+    w.dev_io_bytes = need;
+  }
+  char *base = (char *)w.dev_io;
+  double *dzr = (double *)base;
+  double *dzi = z_im ? dzr + n : nullptr;
+  fpe_xc64 *dout = (fpe_xc64 *)(base + nz);
+  int32_t *dnt = nterms ? (int32_t *)(base + nz + no) : nullptr;
+  int32_t *dbl = bits_lost ? (int32_t *)(base + nz + no + ni) : nullptr;
+  cudaStream_t st = nullptr;
+  if ((e = cudaMemcpyAsync(dzr, z_re, n * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(z)");
+  if (z_im && (e = cudaMemcpyAsync(dzi, z_im, n * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(z)");
+  s = launch_eval(P, dzr, dzi, n, dout, dnt, dbl, st);
+  if (s != FPE_OK) return s;
+  if ((e = cudaMemcpyAsync(out, dout, no, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(out)");
+  if (nterms && (e = cudaMemcpyAsync(nterms, dnt, ni, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(nterms)");
+  if (bits_lost && (e = cudaMemcpyAsync(bits_lost, dbl, ni, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(bits_lost)");
+  return fpe_sync(P, st);
+}
+
+fpe_status fpe_eval_deriv(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                          void *cuda_stream) {
+  fpe_status s = check_eval_args(P, z_re, n, out);
+  if (s != FPE_OK) return s;
+  if (!(P->flags & FPE_WITH_DERIV)) {
+    set_error("fpe_eval_deriv: handle was preconditioned without FPE_WITH_DERIV");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  if (P->deriv_zero || !P->deriv) {
+    cudaError_t e = cudaMemsetAsync(out, 0, n * sizeof(fpe_xc64), (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? FPE_OK : cuda_fail(e, "cudaMemsetAsync");
+  }
+  return launch_eval(P->deriv, z_re, z_im, n, out, nullptr, nullptr, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,
+                          const double *z_im, fpe_xc64 *out, void *cuda_stream) {
+  if (!P || npoly < 0 || !pt_offsets || pt_offsets[0] != 0) {
+    set_error("fpe_eval_batch: bad arguments");
+    return FPE_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < npoly; ++i) {
+    if (!P[i] || pt_offsets[i + 1] < pt_offsets[i]) {
+      set_error("fpe_eval_batch: NULL handle or decreasing offsets");
+      return FPE_ERR_INVALID_ARG;
+    }
+  }
+  for (int64_t i = 0; i < npoly; ++i) {
+    int64_t a = pt_offsets[i], b = pt_offsets[i + 1];
+    if (b == a) continue;
+    fpe_status s = fpe_eval(P[i], z_re + a, z_im ? z_im + a : nullptr, b - a, out + a, nullptr, nullptr, cuda_stream);
+    if (s != FPE_OK) return s;
+  }
+  return FPE_OK;
+}
+
+fpe_status fpe_horner(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                      int compensated, void *cuda_stream) {
+  fpe_status s = check_eval_args(P, z_re, n, out);
+  if (s != FPE_OK) return s;
+  DeviceGuard g(P->device);
+  return launch_horner(P, z_re, z_im, n, out, compensated, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_info(fpe_poly_t P, int64_t *d, int64_t *valuation, int64_t *n_hull, int64_t *n_good, int *T) {
+  if (!P) {
+    set_error("NULL handle");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (d) *d = P->d;
+  if (valuation) *valuation = P->v;
+  if (n_hull) *n_hull = (int64_t)P->hull_k.size();
+  if (n_good) *n_good = P->n_good;
+  if (T) *T = P->T;
+  return FPE_OK;
+}
+
+fpe_status fpe_get_hull(fpe_poly_t P, int64_t *k, int64_t *s, int64_t cap) {
+  if (!P || !k || !s || cap < (int64_t)P->hull_k.size()) {
+    set_error("fpe_get_hull: bad arguments or capacity too small");
+    return FPE_ERR_INVALID_ARG;
+  }
+  std::memcpy(k, P->hull_k.data(), P->hull_k.size() * sizeof(int64_t));
+  std::memcpy(s, P->hull_s.data(), P->hull_s.size() * sizeof(int64_t));
+  return FPE_OK;
+}
+
+fpe_status fpe_get_good(fpe_poly_t P, uint8_t *mask, int64_t n_coef) {
+  if (!P || !mask || n_coef != P->n_coef) {
+    set_error("fpe_get_good: bad arguments");
+    return FPE_ERR_INVALID_ARG;
+  }
+  std::memcpy(mask, P->good.data(), (size_t)n_coef);
+  return FPE_OK;
+}
+
+fpe_status fpe_get_windows(fpe_poly_t P, int64_t n, int64_t *l, int64_t *r, double *N, void *cuda_stream) {
+  if (!P || (P->flags & FPE_HOST_ONLY) || n != P->last_n || n > P->ws.cap) {
+    set_error("fpe_get_windows: n must equal the size of the last fpe_eval");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSuccess;
+  if (l && e == cudaSuccess) e = cudaMemcpyAsync(l, P->ws.lo, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+  if (r && e == cudaSuccess) e = cudaMemcpyAsync(r, P->ws.hi, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+  if (N && e == cudaSuccess) e = cudaMemcpyAsync(N, P->ws.N, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? FPE_OK : cuda_fail(e, "cudaMemcpyAsync");
+}
+
+fpe_status fpe_sync(fpe_poly_t P, void *cuda_stream) {
+  if (!P || (P->flags & FPE_HOST_ONLY)) {
+    set_error("NULL handle");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int32_t h = 0;
+  if ((e = cudaMemcpy(&h, P->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy(status)");
+  if (h) {
+    cudaMemset(P->d_status, 0, sizeof(int32_t));
+    if (h & kStatusNonFinite) {
+      set_error("non-finite evaluation point");
+      return FPE_ERR_NONFINITE;
+    }
+    set_error("device status " + std::to_string(h));
+    return FPE_ERR_CUDA;
+  }
+  return FPE_OK;
+}
+
+void fpe_destroy(fpe_poly_t P) { free_handle(P); }
+
+const char *fpe_status_string(fpe_status s) {
+  switch (s) {
+    case FPE_OK: return "ok";
+    case FPE_ERR_INVALID_ARG: return "invalid argument";
+    case FPE_ERR_NONFINITE: return "non-finite input";
+    case FPE_ERR_ZERO_POLY: return "zero polynomial";
+    case FPE_ERR_OOM: return "out of memory";
+    case FPE_ERR_CUDA: return "CUDA error";
+    case FPE_ERR_TIMEOUT: return "device wait timed out";
+    case FPE_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *fpe_last_error(void) { return last_error_cstr(); }
+
+void fpe_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof_on = on != 0;
+}
+
+void fpe_profile_reset(void) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (auto &r : g_prof) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  g_prof.clear();
+}
+
+fpe_status fpe_profile_read(const char *name, double *total_ms, int64_t *launches) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (auto &r : g_prof) {
+    if (name && !std::strstr(r.name.c_str(), name)) continue;
+    cudaError_t e = cudaEventSynchronize(r.e1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    tot += ms;
+    ++cnt;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = cnt;
+  return FPE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,696 @@
+// Evaluation phase of Algorithm A_p (lines 6-11; §5.2) on the GPU.
+//
+// Stages, all asynchronous on the caller's stream, with grid sizes that depend
+// only on n (so the sequence can be captured in a CUDA graph):
+//   k_locate    per point: lambda = log2|z|, k_lambda and N by binary search on
+//               the cover's slopes (eq. defN), l and r by two binary searches
+//               (def. LRN); bucket key from lambda; histogram.
+//   k_scan_bins exclusive scan of the bucket histogram (one block).
+//   k_scatter   points to bucketed order (points of similar |z| together, so a
+//               warp's lanes get windows of similar length and position);
+//               long windows listed separately.
+//   k_sum_short one thread per point: the window's sum on the rescaled
+//               coefficients b_k, then the power z^(k_lambda - 1 + v) in
+//               extended double-double (§8.2).
+//   k_sum_groups   windows longer than kLongWindow: warp groups of 32 lane
+//               chunks, combined by a shuffle tree with powers of z^chunk.
+//   k_finalize_long  one thread per long window: combines its groups and
+//               applies the power z^(l + v).
+//
+// Summation order.  The terms of a window peak at k_lambda.  Horner's scheme
+// is accurate when each step adds a term no smaller than the ones already
+// summed, so the window is summed in two parts that both move toward the
+// peak: [k_lambda, r] top-down with multiplier z (4 FMA per complex term),
+// and [l, k_lambda - 1] bottom-up with multiplier 1/z held in double-double
+// (8 FMA per term).  Top-down over the whole window (the paper's z^l times
+// Horner) rounds a partial sum already as large as P(z) at every one of the
+// ~T/lambda steps below the peak, which in FP64 exceeds 2^-50 S(z).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "fpe_device.cuh"
+#include "fpe_internal.h"
+
+namespace fpe {
+
+// ---------------------------------------------------------------------------
+// location (Alg. A_p lines 7-10)
+// ---------------------------------------------------------------------------
+
+struct Window {
+  long long lo, hi;  // trimmed
+  long long kl;      // trimmed k_lambda
+  double N;          // trimmed maximum
+  double lam;
+  int flags;
+};
+
+template <bool CZ>
+__device__ __forceinline__ Window locate_point(const DevPoly &P, double zr, double zi) {
+  Window w;
+  w.lo = 1;
+  w.hi = 0;
+  w.kl = 0;
+  w.N = 0.0;
+  w.lam = 0.0;
+  w.flags = 0;
+  if (!isfinite(zr) || (CZ && !isfinite(zi))) {
+    w.flags = kPointNonFinite;
+    return w;
+  }
+  if (zr == 0.0 && (!CZ || zi == 0.0)) {
+    w.flags = kPointZero;
+    return w;
+  }
+  double lam;
+  if (CZ) {
+    // lambda = log2|z| = f + log2|z 2^-f| with |z 2^-f| in [0.5, sqrt 2)
+    int f = frexp_exp(fmax(fabs(zr), fabs(zi)));
+    double xr = scale2(zr, -f), xi = scale2(zi, -f);
+    lam = (double)f + 0.5 * log2(fma(xr, xr, xi * xi));
+  } else {
+    lam = log2(fabs(zr));
+  }
+  w.lam = lam;
+  const int nh = P.n_hull;
+  const double *hk = P.hull_k, *hs = P.hull_s, *sg = P.hull_sig;
+  // k_lambda: first vertex whose right segment has slope <= -lambda (ties: leftmost)
+  int a = 0, b = nh - 1;
+  while (a < b) {
+    int m = (a + b) >> 1;
+    if (sg[m] <= -lam)
+      b = m;
+    else
+      a = m + 1;
+  }
+  const int is = a;
+  const double N = fma(lam, hk[is], hs[is]);
+  const double thr = N - P.T;
+  // left branch: cover + lambda Id increases on vertices [0, is]
+  long long lo;
+  if (is == 0 || fma(lam, hk[0], hs[0]) >= thr) {
+    lo = (long long)hk[0];
+  } else {
+    int x = 0, y = is;  // f(x) < thr <= f(y)
+    while (y - x > 1) {
+      int m = (x + y) >> 1;
+      if (fma(lam, hk[m], hs[m]) < thr)
+        x = m;
+      else
+        y = m;
+    }
+    double fx = fma(lam, hk[x], hs[x]);
+    double t = hk[x] + (thr - fx) / (sg[x] + lam);
+    lo = (long long)ceil(t);
+    lo = max(lo, (long long)hk[x] + 1);
+    lo = min(lo, (long long)hk[x + 1]);
+  }
+  // right branch: decreases on vertices [is, nh - 1]
+  long long hi;
+  if (is == nh - 1 || fma(lam, hk[nh - 1], hs[nh - 1]) >= thr) {
+    hi = (long long)hk[nh - 1];
+  } else {
+    int x = is, y = nh - 1;  // f(x) >= thr > f(y)
+    while (y - x > 1) {
+      int m = (x + y) >> 1;
+      if (fma(lam, hk[m], hs[m]) < thr)
+        y = m;
+      else
+        x = m;
+    }
+    double fx = fma(lam, hk[x], hs[x]);
+    double t = hk[x] + (thr - fx) / (sg[x] + lam);
+    hi = (long long)floor(t);
+    hi = max(hi, (long long)hk[x]);
+    hi = min(hi, (long long)hk[y] - 1);
+  }
+  w.lo = lo;
+  w.hi = hi;
+  w.kl = (long long)hk[is];
+  w.N = N;
+  return w;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(double lam, int flags) {
+  if (flags) return 0;
+  // monotone squashing of lambda onto [0, 1): atan(lambda / 4) / pi + 1/2
+  float t = atanf((float)lam * 0.25f) * 0.318309886f + 0.5f;
+  int b = (int)(t * (float)kNumBins);
+  return (uint32_t)min(max(b, 0), kNumBins - 1);
+}
+
+template <bool CZ>
+__global__ void k_locate(DevPoly P, int n, const double *__restrict__ zre, const double *__restrict__ zim,
+                         long long *__restrict__ lo_out, long long *__restrict__ hi_out,
+                         long long *__restrict__ kl_out, double *__restrict__ N_out, uint32_t *__restrict__ key,
+                         uint32_t *__restrict__ hist) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double zr = zre[p], zi = CZ ? zim[p] : 0.0;
+  Window w = locate_point<CZ>(P, zr, zi);
+  lo_out[p] = w.lo + (w.flags ? 0 : P.v);
+  hi_out[p] = w.hi + (w.flags ? 0 : P.v);
+  kl_out[p] = w.kl;
+  N_out[p] = w.flags ? 0.0 : w.N + w.lam * (double)P.v;
+  uint32_t k = bucket_of(w.lam, w.flags);
+  key[p] = k;
+  atomicAdd(&hist[k], 1u);
+}
+
+// exclusive scan of the histogram into cursors; resets the long-window counters
+__global__ void k_scan_bins(uint32_t *bins) {
+  __shared__ uint32_t part[1024];
+  const int per = kNumBins / 1024;
+  int t = threadIdx.x;
+  uint32_t loc[kNumBins / 1024];
+  uint32_t s = 0;
+  for (int i = 0; i < per; ++i) {
+    loc[i] = bins[t * per + i];
+    s += loc[i];
+  }
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t v = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - s;
+  for (int i = 0; i < per; ++i) {
+    bins[kNumBins + t * per + i] = run;
+    run += loc[i];
+  }
+  if (t < kNumCounters) bins[2 * kNumBins + t] = 0;
+}
+
+template <bool CZ>
+__global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, const double *__restrict__ zim,
+                          const long long *__restrict__ lo, const long long *__restrict__ hi,
+                          const long long *__restrict__ kl, const double *__restrict__ N,
+                          const uint32_t *__restrict__ key, uint32_t *bins,
+                          PointRec *__restrict__ rec, int32_t *__restrict__ long_list,
+                          int32_t *__restrict__ long_ngroups, int32_t *__restrict__ long_gbase,
+                          int32_t *__restrict__ extra_owner, int32_t *__restrict__ extra_group, int extra_cap,
+                          int32_t *status) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t pos = atomicAdd(&bins[kNumBins + key[p]], 1u);
+  PointRec r;
+  r.zr = zre[p];
+  r.zi = CZ ? zim[p] : 0.0;
+  long long l = lo[p], h = hi[p];
+  r.flags = 0;
+  if (!isfinite(r.zr) || !isfinite(r.zi)) {
+    r.flags = kPointNonFinite;
+    atomicOr(status, kStatusNonFinite);
+  } else if (r.zr == 0.0 && r.zi == 0.0) {
+    r.flags = kPointZero;
+  }
+  r.lo = r.flags ? 1 : l - P.v;
+  r.hi = r.flags ? 0 : h - P.v;
+  r.kl = kl[p];
+  r.N = N[p];
+  r.orig = p;
+  rec[pos] = r;
+  const long long L = r.hi - r.lo + 1;
+  if (!r.flags && L > kLongWindow) {
+    // group 0 lives in slot i; groups 1.. in reserved extra slots (one group if none are left)
+    uint32_t i = atomicAdd(&bins[2 * kNumBins + kCntLong], 1u);
+    long_list[i] = (int32_t)pos;
+    int ng = (int)((L + kGroupSpan - 1) / kGroupSpan);
+    int gb = 0;
+    if (ng > 1) {
+      gb = (int)atomicAdd(&bins[2 * kNumBins + kCntExtra], (uint32_t)(ng - 1));
+      if (gb + ng - 1 > extra_cap) {
+        // no room: one group; mark the slots of this reservation that exist as unused
+        for (int g = 1; g < ng && gb + g - 1 < extra_cap; ++g) extra_owner[gb + g - 1] = -1;
+        ng = 1;
+      } else {
+        for (int g = 1; g < ng; ++g) {
+          extra_owner[gb + g - 1] = (int32_t)i;
+          extra_group[gb + g - 1] = g;
+        }
+      }
+    }
+    long_ngroups[i] = ng;
+    long_gbase[i] = gb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// window sums (Alg. A_p line 11)
+// ---------------------------------------------------------------------------
+
+// Horner over trimmed indices [lo, hi] on the rescaled coefficients b:
+// returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-lo) = h * 2^rho(lo).
+// Piece j runs at w_j = 2^beta_j z; entering piece j from j+1 multiplies h by
+// 2^delta_j (both exact).  Every term of a window has |h| <= L 2^(T + 66),
+// so nothing overflows.
+template <bool CC, bool CZ, bool COMP>
+__device__ __forceinline__ void window_horner(const DevPoly &P, const double *__restrict__ b, double zr, double zi,
+                                              long long lo, long long hi, double &hr, double &hm, double &cr,
+                                              double &cm, long long &rho_lo) {
+  int j = P.piece_first[hi >> kLog2PieceLen];
+  while (P.piece_k0[j + 1] <= hi) ++j;
+  if (CC) {
+    double2 c = reinterpret_cast<const double2 *>(b)[hi];
+    hr = c.x;
+    hm = c.y;
+  } else {
+    hr = b[hi];
+    hm = 0.0;
+  }
+  cr = 0.0;
+  cm = 0.0;
+  long long k = hi - 1;
+  long long k0 = max((long long)P.piece_k0[j], lo);
+  while (true) {
+    const int beta = P.piece_beta[j];
+    const double wr = scale2(zr, beta);
+    const double wi = CZ ? scale2(zi, beta) : 0.0;
+    if (CC) {
+      const double2 *b2 = reinterpret_cast<const double2 *>(b);
+#pragma unroll 4
+      for (; k >= k0; --k) {
+        double2 c = __ldg(&b2[k]);
+        horner_step<CC, CZ, COMP>(hr, hm, cr, cm, wr, wi, c.x, c.y);
+      }
+    } else {
+#pragma unroll 4
+      for (; k >= k0; --k) {
+        double c = __ldg(&b[k]);
+        horner_step<CC, CZ, COMP>(hr, hm, cr, cm, wr, wi, c, 0.0);
+      }
+    }
+    if (k < lo) break;
+    --j;  // k == piece_k0[j + 1] - 1: enter piece j
+    const double s = pow2i(P.piece_delta[j]);
+    hr *= s;
+    hm *= s;
+    if (COMP) {
+      cr *= s;
+      cm *= s;
+    }
+    k0 = max((long long)P.piece_k0[j], lo);
+  }
+  rho_lo = P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
+}
+
+__device__ __forceinline__ fpe_xc64 special_value(const DevPoly &P, int flags) {
+  fpe_xc64 o;
+  if (flags & kPointNonFinite) {
+    o.re = __longlong_as_double(0x7ff8000000000000ll);
+    o.im = o.re;
+    o.e = 0;
+  } else {  // z = 0: P(0) = a_0 (0 when the valuation is positive)
+    o.re = P.a0_re;
+    o.im = P.a0_im;
+    o.e = (P.a0_re == 0.0 && P.a0_im == 0.0) ? 0 : P.a0_e;
+  }
+  return o;
+}
+
+__device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, const fpe_xc64 &o,
+                                           int32_t *nterms, int32_t *bits_lost) {
+  if (nterms) nterms[r.orig] = r.flags ? (r.flags == kPointZero ? (P.v == 0 ? 1 : 0) : 0)
+                                       : P.gcount[r.hi + 1] - P.gcount[r.lo];
+  if (bits_lost) {
+    int bl = 0;
+    if (!r.flags && (o.re != 0.0 || o.im != 0.0)) {
+      double c = ceil(r.N) - (double)o.e;
+      bl = c > 0.0 ? (int)fmin(c, 2.0e9) : 0;
+    }
+    bits_lost[r.orig] = bl;
+  }
+}
+
+// Bottom-up Horner over trimmed indices [lo, hi] with multiplier 1/z:
+// returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-hi) = h * 2^rho(hi).
+// 1/z = u 2^ue with u in double-double.  Within piece j the step from k-1 to
+// k multiplies by v_j = 2^-beta_j / z; crossing from piece j to j+1 first
+// scales h by 2^-delta_j.  Each step is 8 FMA for complex z and coefficients.
+template <bool CC, bool CZ>
+__device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b, const cdd &u,
+                                                  int ue, long long lo, long long hi, double &hr, double &hm,
+                                                  long long &rho_hi) {
+  int j = P.piece_first[lo >> kLog2PieceLen];
+  while (P.piece_k0[j + 1] <= lo) ++j;
+  if (CC) {
+    double2 c = reinterpret_cast<const double2 *>(b)[lo];
+    hr = c.x;
+    hm = c.y;
+  } else {
+    hr = b[lo];
+    hm = 0.0;
+  }
+  long long k = lo + 1;
+  while (k <= hi) {
+    const int sh = ue - P.piece_beta[j];
+    const double vhr = scale2(u.rh, sh), vlr = scale2(u.rl, sh);
+    const double vhi = CZ ? scale2(u.ih, sh) : 0.0, vli = CZ ? scale2(u.il, sh) : 0.0;
+    const long long kend = min((long long)P.piece_k0[j + 1] - 1, hi);
+    bool cross = false;
+    for (;;) {
+      if (k > kend) {
+        if (k > hi) break;
+        // k is the first index of piece j + 1: rescale, one step with v_j, move on
+        const double s2 = pow2i(-P.piece_delta[j]);
+        hr *= s2;
+        hm *= s2;
+        cross = true;
+      }
+      double br, bi;
+      if (CC) {
+        double2 c = __ldg(reinterpret_cast<const double2 *>(b) + k);
+        br = c.x;
+        bi = c.y;
+      } else {
+        br = __ldg(b + k);
+        bi = 0.0;
+      }
+      double nr, ni;
+      if (CZ) {
+        nr = fma(hr, vhr, fma(-hm, vhi, fma(hr, vlr, fma(-hm, vli, br))));
+        ni = fma(hr, vhi, fma(hm, vhr, fma(hr, vli, fma(hm, vlr, bi))));
+      } else {
+        nr = fma(hr, vhr, fma(hr, vlr, br));
+        ni = CC ? fma(hm, vhr, fma(hm, vlr, bi)) : 0.0;
+      }
+      hr = nr;
+      hm = ni;
+      ++k;
+      if (cross) break;
+    }
+    if (cross) ++j;
+  }
+  rho_hi = P.piece_rho0[j] + (long long)P.piece_beta[j] * (hi - P.piece_k0[j]);
+}
+
+__device__ __forceinline__ xdd xdd_from_cdd(const cdd &u, int ue) {
+  xdd x = {u.rh, u.rl, u.ih, u.il, ue};
+  return xdd_norm(x);
+}
+
+// sum_{k=lo}^{hi} a_k z^(k - base) in extended double-double for a range on
+// either side of the peak kl or straddling it.  The part at or above kl is
+// summed top-down (relative to z^max(kl, lo)), the part below bottom-up
+// (relative to z^(its top index)); base is kl - 1 when both parts exist.
+template <bool CC, bool CZ>
+__device__ __forceinline__ xdd range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
+                                         const cdd &u, long long lo, long long hi, long long kl, long long &base) {
+  xdd X = xdd_zero();
+  const long long top_lo = max(kl, lo);
+  const long long low_hi = min(top_lo - 1, hi);
+  const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
+  if (has_up) {
+    double hr, hm, cr, cm;
+    long long rho;
+    window_horner<CC, CZ, false>(P, P.b, zr, zi, top_lo, hi, hr, hm, cr, cm, rho);
+    if (hr != 0.0 || hm != 0.0) X = xdd_from(hr, hm, rho);
+    base = top_lo;
+  }
+  if (has_low) {
+    double hr, hm;
+    long long rho;
+    window_horner_rev<CC, CZ>(P, P.b, u, -f, lo, low_hi, hr, hm, rho);
+    if (has_up && (X.rh != 0.0 || X.ih != 0.0)) X = xdd_mul_d(X, mr, mi, f);  // z^top_lo = z * z^low_hi
+    if (hr != 0.0 || hm != 0.0) X = xdd_add(X, xdd_from(hr, hm, rho));
+    base = low_hi;
+  }
+  return X;
+}
+
+// Compensated top-down sum over [lo, hi] relative to z^lo (FPE_ACCURATE).
+template <bool CC, bool CZ>
+__device__ __forceinline__ xdd range_sum_comp(const DevPoly &P, double zr, double zi, long long lo, long long hi) {
+  double hr, hm, cr, cm;
+  long long rho;
+  window_horner<CC, CZ, true>(P, P.b, zr, zi, lo, hi, hr, hm, cr, cm, rho);
+  dd re = two_sum(hr, cr), im = two_sum(hm, cm);
+  xdd x = {re.hi, re.lo, im.hi, im.lo, rho};
+  return xdd_norm(x);
+}
+
+template <bool CC, bool CZ, bool ACC>
+__global__ void __launch_bounds__(128) k_sum_short(DevPoly P, int n, const PointRec *__restrict__ rec,
+                                                   fpe_xc64 *__restrict__ out, int32_t *nterms,
+                                                   int32_t *bits_lost) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  PointRec r = rec[q];
+  fpe_xc64 o;
+  if (r.flags) {
+    o = special_value(P, r.flags);
+  } else {
+    if (r.hi - r.lo + 1 > kLongWindow) return;  // summed by k_sum_groups
+    xdd X;
+    long long base;
+    if (ACC) {
+      X = range_sum_comp<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
+      base = r.lo;
+    } else {
+      const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+      const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
+      cdd u = {0.0, 0.0, 0.0, 0.0};
+      if (r.lo < r.kl) u = recip_dd(mr, mi);
+      X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+    }
+    xdd pw = xdd_pow(r.zr, r.zi, base + P.v);
+    o = xdd_out(xdd_mul(X, pw));
+  }
+  out[r.orig] = o;
+  write_diag(P, r, o, nterms, bits_lost);
+}
+
+__device__ __forceinline__ xdd shfl_down_xdd(xdd x, int s) {
+  xdd y;
+  y.rh = __shfl_down_sync(0xffffffffu, x.rh, s);
+  y.rl = __shfl_down_sync(0xffffffffu, x.rl, s);
+  y.ih = __shfl_down_sync(0xffffffffu, x.ih, s);
+  y.il = __shfl_down_sync(0xffffffffu, x.il, s);
+  y.e = __shfl_down_sync(0xffffffffu, x.e, s);
+  return y;
+}
+__device__ __forceinline__ xdd shfl_up_xdd(xdd x, int s) {
+  xdd y;
+  y.rh = __shfl_up_sync(0xffffffffu, x.rh, s);
+  y.rl = __shfl_up_sync(0xffffffffu, x.rl, s);
+  y.ih = __shfl_up_sync(0xffffffffu, x.ih, s);
+  y.il = __shfl_up_sync(0xffffffffu, x.il, s);
+  y.e = __shfl_up_sync(0xffffffffu, x.e, s);
+  return y;
+}
+
+// Long windows: warp groups.  A window of length L gets ng = ceil(L / kGroupSpan)
+// groups of S = 32 C terms with C = ceil(L / (32 ng)); lane i of group g owns
+// the chunk [c_i, c_i + C - 1], c_i = l + g S + i C, and a slot value s_i with
+//   sum over the window = z^l sum_g (z^S)^g sum_i (z^C)^i s_i:
+//   chunk above the peak:     s_i = sum a_k z^(k - c_i) (top-down);
+//   chunk below the peak:     its sum z^(c_{i+1} - 1) R goes to slot i+1 as R / z;
+//   chunk holding the peak:   both parts, times z^(base - c_i).
+// A group's value is combined by a shuffle tree with w, w^2, w^4, ... (w = z^C);
+// lane 31's carry goes to the next group.  k_finalize_long combines the groups
+// and applies z^(l + v), one point per thread.
+__device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
+  return g == 0 ? i : cap + gbase + g - 1;
+}
+
+template <bool CC, bool CZ, bool ACC>
+__global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *__restrict__ rec,
+                                                    const int32_t *__restrict__ long_list,
+                                                    const int32_t *__restrict__ long_ngroups,
+                                                    const int32_t *__restrict__ long_gbase,
+                                                    const int32_t *__restrict__ extra_owner,
+                                                    const int32_t *__restrict__ extra_group, uint32_t *bins, int cap,
+                                                    int extra_cap, xdd *__restrict__ gval, xdd *__restrict__ gcarry) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nlong = *(volatile uint32_t *)&bins[2 * kNumBins + kCntLong];
+  const uint32_t nextra = min(*(volatile uint32_t *)&bins[2 * kNumBins + kCntExtra], (uint32_t)extra_cap);
+  // every extra slot below min(reserved, extra_cap) is written by k_scatter: an owner, or -1
+  while (true) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&bins[2 * kNumBins + kCntGroupWork], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= nlong + nextra) break;
+    int i, g;
+    if (t < nlong) {
+      i = (int)t;
+      g = 0;
+    } else {
+      i = extra_owner[t - nlong];
+      if (i < 0) continue;  // slot of a reservation that did not fit
+      g = extra_group[t - nlong];
+    }
+    const int ng = long_ngroups[i];
+    const PointRec r = rec[long_list[i]];
+    const long long L = r.hi - r.lo + 1;
+    const long long C = (L + 32LL * ng - 1) / (32LL * ng);
+    const long long clo = r.lo + (long long)g * 32 * C + lane * C;
+    const long long chi = min(clo + C - 1, r.hi);
+    xdd sv = xdd_zero(), carry = xdd_zero();
+    if (ACC) {
+      if (clo <= chi) sv = range_sum_comp<CC, CZ>(P, r.zr, r.zi, clo, chi);
+    } else if (clo <= chi) {
+      const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+      const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
+      const cdd u = recip_dd(mr, mi);
+      long long base;
+      xdd X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
+      if (chi < r.kl) {
+        carry = xdd_mul(X, xdd_from_cdd(u, -f));  // below the peak: X / z to the next slot
+      } else if (base > clo) {
+        sv = xdd_mul(X, xdd_pow(r.zr, r.zi, base - clo));
+      } else {
+        sv = X;
+      }
+    }
+    xdd gout = xdd_zero();
+    if (!ACC) {
+      xdd inc = shfl_up_xdd(carry, 1);
+      if (lane > 0) sv = xdd_add(sv, inc);
+      gout = shfl_down_xdd(carry, 31);  // lane 31's carry, read by lane 0
+    }
+    xdd w = xdd_pow(r.zr, r.zi, C);
+    for (int s = 1; s < 32; s <<= 1) {
+      xdd other = shfl_down_xdd(sv, s);
+      if ((lane & (2 * s - 1)) == 0) sv = xdd_add(sv, xdd_mul(w, other));
+      if (s < 16) w = xdd_sqr(w);
+    }
+    if (lane == 0) {
+      const int slot = group_slot(i, g, long_gbase[i], cap);
+      gval[slot] = sv;
+      gcarry[slot] = gout;
+    }
+  }
+}
+
+// One thread per long-window point: sum_g (z^S)^g (val_g + carry_{g-1}) by
+// Horner from the top group, then times z^(l + v).
+__global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec *__restrict__ rec,
+                                                       const int32_t *__restrict__ long_list,
+                                                       const int32_t *__restrict__ long_ngroups,
+                                                       const int32_t *__restrict__ long_gbase, uint32_t *bins,
+                                                       int cap, const xdd *__restrict__ gval,
+                                                       const xdd *__restrict__ gcarry, fpe_xc64 *__restrict__ out,
+                                                       int32_t *nterms, int32_t *bits_lost) {
+  const uint32_t nlong = *(volatile uint32_t *)&bins[2 * kNumBins + kCntLong];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nlong; i += gridDim.x * blockDim.x) {
+    const PointRec r = rec[long_list[i]];
+    const int ng = long_ngroups[i], gb = long_gbase[i];
+    xdd acc = gval[group_slot(i, ng - 1, gb, cap)];
+    if (ng > 1) {
+      const long long L = r.hi - r.lo + 1;
+      const long long C = (L + 32LL * ng - 1) / (32LL * ng);
+      const xdd W = xdd_pow(r.zr, r.zi, 32 * C);
+      acc = xdd_add(acc, gcarry[group_slot(i, ng - 2, gb, cap)]);
+      for (int g = ng - 2; g >= 0; --g) {
+        xdd sg = gval[group_slot(i, g, gb, cap)];
+        if (g > 0) sg = xdd_add(sg, gcarry[group_slot(i, g - 1, gb, cap)]);
+        acc = xdd_add(xdd_mul(acc, W), sg);
+      }
+    }
+    const xdd pw = xdd_pow(r.zr, r.zi, r.lo + P.v);
+    const fpe_xc64 o = xdd_out(xdd_mul(acc, pw));
+    out[r.orig] = o;
+    write_diag(P, r, o, nterms, bits_lost);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launch
+// ---------------------------------------------------------------------------
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <bool CC, bool CZ, bool ACC>
+static void launch_sums3(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
+                         cudaStream_t st) {
+  Workspace &w = P->ws;
+  const int cap = (int)w.cap, xcap = (int)w.extra_cap;
+  {
+    ProfScope ps("k_sum_short", st);
+    k_sum_short<CC, CZ, ACC><<<(n + 127) / 128, 128, 0, st>>>(P->dev, n, w.rec, out, nterms, bits_lost);
+  }
+  {
+    ProfScope ps("k_sum_groups", st);
+    k_sum_groups<CC, CZ, ACC><<<num_sms() * 4, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups,
+                                                             w.long_gbase, w.extra_owner, w.extra_group, w.bins,
+                                                             cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
+  }
+  {
+    ProfScope ps("k_finalize_long", st);
+    k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase,
+                                                   w.bins, cap, (const xdd *)w.group_val,
+                                                   (const xdd *)w.group_carry, out, nterms, bits_lost);
+  }
+}
+
+template <bool CC, bool CZ>
+static void launch_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
+  if (P->dev.accurate)
+    launch_sums3<CC, CZ, true>(P, n, out, nterms, bits_lost, st);
+  else
+    launch_sums3<CC, CZ, false>(P, n, out, nterms, bits_lost, st);
+}
+
+fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, fpe_xc64 *out,
+                       int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
+  if (n64 == 0) return FPE_OK;
+  fpe_status s = ensure_workspace(P, n64);
+  if (s != FPE_OK) return s;
+  const int n = (int)n64;
+  Workspace &w = P->ws;
+  const bool cz = z_im != nullptr;
+  const bool cc = P->complex_coef;
+  cudaError_t e = cudaMemsetAsync(w.bins, 0, kNumBins * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const int nb = (n + 255) / 256;
+  {
+    ProfScope ps("k_locate", st);
+    if (cz)
+      k_locate<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+    else
+      k_locate<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+  }
+  {
+    ProfScope ps("k_scan_bins", st);
+    k_scan_bins<<<1, 1024, 0, st>>>(w.bins);
+  }
+  {
+    ProfScope ps("k_scatter", st);
+    if (cz)
+      k_scatter<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+                                          w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
+                                          w.extra_group, (int)w.extra_cap, P->d_status);
+    else
+      k_scatter<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+                                           w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
+                                           w.extra_group, (int)w.extra_cap, P->d_status);
+  }
+  if (cc && cz)
+    launch_sums<true, true>(P, n, out, nterms, bits_lost, st);
+  else if (cc)
+    launch_sums<true, false>(P, n, out, nterms, bits_lost, st);
+  else if (cz)
+    launch_sums<false, true>(P, n, out, nterms, bits_lost, st);
+  else
+    launch_sums<false, false>(P, n, out, nterms, bits_lost, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  P->last_n = n64;
+  return FPE_OK;
+}
+
+}  // namespace fpe

@@ -1,0 +1,154 @@
+// Internal declarations shared by the host preconditioner (precondition.cpp),
+// the CUDA kernels (fpe_eval.cu, fpe_horner.cu) and the ABI glue (api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fpe.h"
+
+namespace fpe {
+
+// Coefficient "pieces": the trimmed index range [0, D] is cut at every
+// multiple of kPieceLen and at every cover vertex.  On piece j the
+// coefficients are stored as b_k = a_k * 2^-rho(k) with
+// rho(k) = rho0[j] + beta[j] * (k - k0[j]) an integer line that follows the
+// cover to within kPieceLen/2 + 1 bits, so that every kept b_k lies in
+// [2^-(T + kPieceLen/2 + 3), 2^(kPieceLen/2 + 2)] and Horner's recurrence on
+// piece j runs at the exactly rescaled point w_j = 2^beta[j] * z.
+constexpr int kLog2PieceLen = 7;
+constexpr int kPieceLen = 1 << kLog2PieceLen;
+
+// Bucketing of points by log2|z| before summation (points of similar modulus
+// get similar windows; §8.1 suggests grouping evaluations of similar size).
+constexpr int kNumBins = 4096;
+
+// Points whose window is longer than kLongWindow are summed by warp groups:
+// a group is 32 lane chunks of at most kMaxLaneChunk terms, and a window gets
+// ceil(L / kGroupSpan) groups, so no warp's serial chain exceeds
+// kMaxLaneChunk terms however long the window is.
+constexpr int64_t kLongWindow = 4096;
+constexpr int64_t kMaxLaneChunk = 1024;
+constexpr int64_t kGroupSpan = 32 * kMaxLaneChunk;
+
+// Counters after the 2 * kNumBins histogram words.
+constexpr int kCntLong = 0;        // long-window points listed
+constexpr int kCntGroupWork = 1;   // group work cursor
+constexpr int kCntExtra = 2;       // extra group slots reserved (groups 1.. of very long windows)
+constexpr int kCntFinal = 3;       // finalize cursor
+constexpr int kNumCounters = 8;
+
+// Device view of a preconditioned polynomial, passed to kernels by value.
+struct DevPoly {
+  const double *b;             // FPE coefficients (bad ones zeroed), trimmed k = 0..D;
+                               // complex: interleaved (re, im); real: one double
+  const double *b_full;        // every coefficient, same layout (Horner baselines)
+  const int32_t *piece_k0;     // npieces + 1 entries, last = D + 1
+  const int32_t *piece_beta;   // integer slope of rho on the piece
+  const int32_t *piece_delta;  // exponent shift applied to h when entering piece j from j + 1
+  const int64_t *piece_rho0;   // rho at the piece's first index
+  const int32_t *piece_first;  // per block of kPieceLen indices: first piece overlapping it
+  const double *hull_k;        // trimmed abscissae of the cover's vertices
+  const double *hull_s;        // their scales
+  const double *hull_sig;      // slopes of the n_hull - 1 segments
+  const int32_t *gcount;       // gcount[k] = #{good j < k}, D + 2 entries
+  int64_t D;                   // trimmed degree d - v
+  int64_t v;                   // valuation (first nonzero index)
+  double T;                    // p + s(d) + 3
+  int32_t n_hull;
+  int32_t npieces;
+  int32_t complex_coef;
+  int32_t fp32;
+  int32_t accurate;  // FPE_ACCURATE: compensated window sums
+  int32_t pad0;
+  double a0_re, a0_im;  // a_0 as a normalised mantissa (0 when v > 0)
+  int64_t a0_e;
+};
+
+// One evaluation point after location, in bucketed order.
+struct PointRec {
+  double zr, zi;
+  long long lo, hi;  // window in trimmed indices; lo > hi: no window (z = 0 or non-finite)
+  long long kl;      // k_lambda (trimmed): the window's peak term
+  double N;          // max of cover(k) + lambda k, untrimmed (eq. defN)
+  int32_t orig;      // index in the caller's order
+  int32_t flags;     // kPointZero, kPointNonFinite
+};
+constexpr int32_t kPointZero = 1;
+constexpr int32_t kPointNonFinite = 2;
+
+// Device status word bits.
+constexpr int32_t kStatusNonFinite = 1;
+
+// Scratch memory of one handle, grown on demand.
+struct Workspace {
+  int64_t cap = 0;
+  long long *lo = nullptr, *hi = nullptr;  // per point, caller order (untrimmed)
+  long long *kl = nullptr;                 // per point, caller order (trimmed k_lambda)
+  double *N = nullptr;
+  uint32_t *key = nullptr;
+  PointRec *rec = nullptr;       // bucketed order
+  int32_t *long_list = nullptr;     // bucketed positions of long-window points
+  int32_t *long_ngroups = nullptr;  // warp groups per long-window point
+  int32_t *long_gbase = nullptr;    // first extra group slot (groups 1..)
+  int32_t *extra_owner = nullptr;   // per extra group slot: long-point index
+  int32_t *extra_group = nullptr;   // per extra group slot: group number
+  void *group_val = nullptr;        // per group: value (40-byte extended double-double)
+  void *group_carry = nullptr;      // per group: carry into the next group
+  int64_t extra_cap = 0;            // extra group slots (after the cap group-0 slots)
+  uint32_t *bins = nullptr;         // 2 * kNumBins histogram words + kNumCounters counters
+  void *host_pinned = nullptr;   // staging for fpe_eval_host
+  size_t host_pinned_bytes = 0;
+  void *dev_io = nullptr;        // device staging for fpe_eval_host
+  size_t dev_io_bytes = 0;
+};
+
+}  // namespace fpe
+
+struct fpe_poly_s {
+  fpe::DevPoly dev{};
+  int device = 0;
+  int p = 53;
+  uint32_t flags = 0;
+  int64_t n_coef = 0, d = 0, v = 0;
+  int T = 0;
+  bool complex_coef = false;
+  std::vector<int64_t> hull_k, hull_s;  // untrimmed
+  std::vector<uint8_t> good;            // untrimmed mask, n_coef entries
+  int64_t n_good = 0;
+  std::vector<void *> allocs;           // device allocations owned by the handle
+  fpe::Workspace ws;
+  int32_t *d_status = nullptr;          // device status word
+  fpe_poly_s *deriv = nullptr;          // P' (FPE_WITH_DERIV), nullptr if P' = 0
+  bool deriv_zero = false;
+  int64_t last_n = 0;                   // points of the last fpe_eval
+};
+
+namespace fpe {
+// precondition.cpp
+fpe_status precondition_host(const double *re, const double *im, const int64_t *e2, int64_t n_coef, int p,
+                             uint32_t flags, fpe_poly_s **out);
+void set_error(const std::string &msg);
+fpe_status cuda_fail(cudaError_t e, const char *what);
+void free_handle(fpe_poly_s *P);
+fpe_status ensure_workspace(fpe_poly_s *P, int64_t n);
+
+// fpe_eval.cu
+fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                       int32_t *nterms, int32_t *bits_lost, cudaStream_t st);
+// fpe_horner.cu
+fpe_status launch_horner(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                         int compensated, cudaStream_t st);
+
+// kernel timing (api.cu)
+struct ProfScope {
+  const char *name;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ProfScope(const char *name, cudaStream_t st);
+  ~ProfScope();
+};
+}  // namespace fpe
