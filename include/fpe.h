@@ -127,6 +127,31 @@ fpe_status fpe_eval(fpe_poly_t P, const double *z_re, const double *z_im, int64_
                     int32_t *nterms, int32_t *bits_lost, void *cuda_stream);
 
 /*
+ * fpe_eval_noalloc -- fpe_eval for callers that cannot allocate device memory
+ * while they evaluate (the paper has no counterpart: it is a property of this
+ * library, not of the method).  Examples: a process whose device-memory budget
+ * is fixed at start-up, a latency-bound loop that must not pay for cudaMalloc
+ * and the device synchronisation it implies, a host program that gives the
+ * library only the buffers it owns.  fpe_eval allocates its per-call scratch
+ * on the handle; this call instead uses one built-in scratch array of
+ * 9,036,032 bytes (8.6 MiB) in the library's device memory, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ *   Arguments and results as fpe_eval (device pointers, async on cuda_stream).
+ *   n            0 <= n <= 32768 points; larger n returns FPE_ERR_INVALID_ARG
+ *                with a message (use fpe_eval, or split the points).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls, on every handle and stream, share the one array: calls that overlap
+ * on the GPU race and give wrong results; serialise them (one stream, or
+ * events).  The array keeps the last call's contents; each call clears what it
+ * needs cleared (the bucket histogram) itself.
+ */
+fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
+                            int32_t *nterms, int32_t *bits_lost, void *cuda_stream);
+
+/*
  * fpe_eval_host -- fpe_eval on host buffers: copies z to the device, evaluates,
  * copies the results back and waits for them.  Same arguments as fpe_eval
  * with host pointers (nterms, bits_lost may be NULL).  Synchronous; returns

@@ -37,7 +37,7 @@ EXPORTED = [
     "fpe_precondition", "fpe_eval", "fpe_eval_host", "fpe_eval_deriv", "fpe_eval_batch", "fpe_horner",
     "fpe_info", "fpe_get_hull", "fpe_get_good", "fpe_get_windows", "fpe_sync", "fpe_destroy",
     "fpe_status_string", "fpe_last_error", "fpe_profile_enable", "fpe_profile_reset", "fpe_profile_read",
-    "fpe_measure_fma_peak",
+    "fpe_measure_fma_peak", "fpe_eval_noalloc",
 ]
 
 
@@ -84,6 +84,7 @@ def _load():
         "fpe_profile_reset": ([], None),
         "fpe_profile_read": ([ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], I32),
         "fpe_measure_fma_peak": ([I32, I32, ctypes.POINTER(D)], I32),
+        "fpe_eval_noalloc": ([P, P, P, I64, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -297,3 +298,18 @@ def fpe_measure_fma_peak(precision: int = 64, reps: int = 5) -> float:
     v = ctypes.c_double()
     _check(_load().fpe_measure_fma_peak(int(precision), int(reps), ctypes.byref(v)), "fpe_measure_fma_peak")
     return v.value
+
+
+NOALLOC_MAX_POINTS = 32768
+
+
+def fpe_eval_noalloc(P: Poly, z_re, z_im=None, out=None, nterms=None, bits_lost=None, stream=None):
+    """fpe_eval without any device allocation (at most NOALLOC_MAX_POINTS points;
+    calls share one built-in scratch array and must not overlap on the GPU)."""
+    lib = _load()
+    n = int(z_re.shape[0])
+    if out is None:
+        out = empty_out(n, z_re.device)
+    _check(lib.fpe_eval_noalloc(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _dptr(nterms),
+                                _dptr(bits_lost), _stream(stream)), "fpe_eval_noalloc")
+    return out

@@ -29,6 +29,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "fpe_device.cuh"
 #include "fpe_internal.h"
@@ -694,3 +696,155 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
 }
 
 }  // namespace fpe
+
+// ---------------------------------------------------------------------------
+// Evaluation without any allocation (fpe_eval_noalloc)
+//
+// Some callers cannot allocate device memory when they evaluate: a process
+// whose device-memory budget is fixed at start-up, a latency-bound loop that
+// must not pay cudaMalloc's cost and implicit device synchronisation, or a
+// host program that hands the library only the buffers it owns.  For them the
+// per-call scratch of fpe_eval comes from the file-scope array below instead
+// of the handle: at most kNoAllocMaxPoints points per call.  Every GPU that
+// loads this library holds the array until the process exits, and all calls on
+// all handles share it, so calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+
+namespace fpe {
+
+constexpr int64_t kNoAllocMaxPoints = 32768;
+constexpr int64_t kNoAllocExtra = kNoAllocMaxPoints + 1024;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaLo = 0;
+constexpr size_t kNaHi = kNaLo + align256(kNoAllocMaxPoints * sizeof(long long));
+constexpr size_t kNaKl = kNaHi + align256(kNoAllocMaxPoints * sizeof(long long));
+constexpr size_t kNaN = kNaKl + align256(kNoAllocMaxPoints * sizeof(long long));
+constexpr size_t kNaKey = kNaN + align256(kNoAllocMaxPoints * sizeof(double));
+constexpr size_t kNaRec = kNaKey + align256(kNoAllocMaxPoints * sizeof(uint32_t));
+constexpr size_t kNaLong = kNaRec + align256(kNoAllocMaxPoints * sizeof(PointRec));
+constexpr size_t kNaNg = kNaLong + align256(kNoAllocMaxPoints * sizeof(int32_t));
+constexpr size_t kNaGb = kNaNg + align256(kNoAllocMaxPoints * sizeof(int32_t));
+constexpr size_t kNaOwner = kNaGb + align256(kNoAllocMaxPoints * sizeof(int32_t));
+constexpr size_t kNaGroup = kNaOwner + align256(kNoAllocExtra * sizeof(int32_t));
+constexpr size_t kNaVal = kNaGroup + align256(kNoAllocExtra * sizeof(int32_t));
+constexpr size_t kNaCarry = kNaVal + align256((kNoAllocMaxPoints + kNoAllocExtra) * sizeof(xdd));
+constexpr size_t kNaBins = kNaCarry + align256((kNoAllocMaxPoints + kNoAllocExtra) * sizeof(xdd));
+constexpr size_t kNoAllocBytes = kNaBins + align256((2 * kNumBins + kNumCounters) * sizeof(uint32_t));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (host code must not use the array's name as an address).
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64] = {nullptr};
+
+static fpe_status noalloc_scratch(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= 64) {
+    set_error("fpe_eval_noalloc: device ordinal out of range");
+    return FPE_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (unsigned char *)g_noalloc_addr[dev];
+  return FPE_OK;
+}
+
+}  // namespace fpe
+
+extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n,
+                                       fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost, void *cuda_stream) {
+  using namespace fpe;
+  if (!P || (P->flags & FPE_HOST_ONLY)) {
+    set_error("fpe_eval_noalloc: NULL handle or a FPE_HOST_ONLY handle");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (n < 0 || n > kNoAllocMaxPoints) {
+    set_error("fpe_eval_noalloc: n must be in [0, " + std::to_string(kNoAllocMaxPoints) +
+              "] (the size of the built-in scratch); use fpe_eval for more points");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (n > 0 && (!z_re || !out)) {
+    set_error("fpe_eval_noalloc: NULL point or output pointer");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (n == 0) return FPE_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != P->device) cudaSetDevice(P->device);
+  unsigned char *base = nullptr;
+  fpe_status s = noalloc_scratch(P->device, &base);
+  if (s == FPE_OK) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Workspace w;  // a view into the built-in scratch; nothing is allocated or freed
+    w.cap = kNoAllocMaxPoints;
+    w.extra_cap = kNoAllocExtra;
+    w.lo = (long long *)(base + kNaLo);
+    w.hi = (long long *)(base + kNaHi);
+    w.kl = (long long *)(base + kNaKl);
+    w.N = (double *)(base + kNaN);
+    w.key = (uint32_t *)(base + kNaKey);
+    w.rec = (PointRec *)(base + kNaRec);
+    w.long_list = (int32_t *)(base + kNaLong);
+    w.long_ngroups = (int32_t *)(base + kNaNg);
+    w.long_gbase = (int32_t *)(base + kNaGb);
+    w.extra_owner = (int32_t *)(base + kNaOwner);
+    w.extra_group = (int32_t *)(base + kNaGroup);
+    w.group_val = base + kNaVal;
+    w.group_carry = base + kNaCarry;
+    w.bins = (uint32_t *)(base + kNaBins);
+    const int ni = (int)n;
+    const int nb = (ni + 255) / 256;
+    const bool cz = z_im != nullptr, cc = P->complex_coef;
+    // the histogram must start at zero (cursors and counters are written by k_scan_bins)
+    cudaError_t e = cudaMemsetAsync(w.bins, 0, kNumBins * sizeof(uint32_t), st);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "cudaMemsetAsync");
+    } else {
+      if (cz)
+        k_locate<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+      else
+        k_locate<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+      k_scan_bins<<<1, 1024, 0, st>>>(w.bins);
+      if (cz)
+        k_scatter<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+                                            w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
+                                            w.extra_group, (int)w.extra_cap, P->d_status);
+      else
+        k_scatter<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+                                             w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
+                                             w.extra_group, (int)w.extra_cap, P->d_status);
+      const int cap = (int)w.cap, xcap = (int)w.extra_cap;
+      const bool acc = P->dev.accurate != 0;
+#define FPE_NOALLOC_SUMS(CCv, CZv, ACCv)                                                                       \
+  do {                                                                                                         \
+    k_sum_short<CCv, CZv, ACCv><<<(ni + 127) / 128, 128, 0, st>>>(P->dev, ni, w.rec, out, nterms, bits_lost); \
+    k_sum_groups<CCv, CZv, ACCv><<<num_sms() * 4, 128, 0, st>>>(                                              \
+        P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group, w.bins, cap,   \
+        xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                                                       \
+    k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase,   \
+                                                   w.bins, cap, (const xdd *)w.group_val,                      \
+                                                   (const xdd *)w.group_carry, out, nterms, bits_lost);        \
+  } while (0)
+      if (cc && cz) {
+        if (acc) FPE_NOALLOC_SUMS(true, true, true); else FPE_NOALLOC_SUMS(true, true, false);
+      } else if (cc) {
+        if (acc) FPE_NOALLOC_SUMS(true, false, true); else FPE_NOALLOC_SUMS(true, false, false);
+      } else if (cz) {
+        if (acc) FPE_NOALLOC_SUMS(false, true, true); else FPE_NOALLOC_SUMS(false, true, false);
+      } else {
+        if (acc) FPE_NOALLOC_SUMS(false, false, true); else FPE_NOALLOC_SUMS(false, false, false);
+      }
+#undef FPE_NOALLOC_SUMS
+      e = cudaGetLastError();
+      if (e != cudaSuccess) s = cuda_fail(e, "fpe_eval_noalloc launch");
+    }
+  }
+  if (prev >= 0 && prev != P->device) cudaSetDevice(prev);
+  return s;
+}
