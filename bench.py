@@ -301,6 +301,18 @@ def main():
             b.record(st)
             torch.cuda.synchronize()
             extras["fpe_accurate_evals_per_s"] = n / (a.elapsed_time(b) * 1e-3)
+            # FP32 mode (p = 24: windows from T = 24 + s(d) + 3, FP32 coefficients and Horner)
+            P32 = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, None, 24, F.FPE_FP32)
+            nt32 = torch.empty(n, dtype=torch.int32, device="cuda")
+            F.fpe_eval(P32, zr, zi, out, nt32)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            F.fpe_eval(P32, zr, zi, out, nt32)
+            b.record(st)
+            torch.cuda.synchronize()
+            extras["fpe_fp32_p24_evals_per_s"] = n / (a.elapsed_time(b) * 1e-3)
+            extras["fpe_fp32_p24_avg_kept_terms"] = float(nt32.double().mean().item())
             extras["cpu_baseline"] = oracle_cpu_baseline(wl, 4096)
 
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -62,7 +62,13 @@ typedef enum {
 enum {
   FPE_REAL = 1,        /* treat the coefficients as real (im ignored)           */
   FPE_WITH_DERIV = 2,  /* also precondition P' for fpe_eval_deriv               */
-  FPE_FP32 = 4,        /* evaluate in FP32 mantissas (requires p <= 24)         */
+  FPE_FP32 = 4,        /* FP32 mode (requires p <= 24): coefficients rounded to
+                          FP32 and windows summed on the FP32 pipe with a
+                          float-float multiplier; the window search and the
+                          exponent bookkeeping stay FP64/integer.  Error
+                          <= 2^-21 sum |a_k||z|^k for p = 24 (same caveat on
+                          aligned terms as the default FP64 summation).
+                          Not combinable with FPE_ACCURATE.                    */
   FPE_HOST_ONLY = 8,   /* host analysis only (scales, cover, G_p; the -analyse
                           task of §8.1): no device memory is touched and the
                           handle cannot be evaluated                           */

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "fpe_internal.h"
 
@@ -238,6 +239,177 @@ __device__ __forceinline__ cdd recip_dd(double mr, double mi) {
   dd n2 = fast_two_sum(s.hi, s.lo + p1.lo + p2.lo);
   dd ur = dd_div_d(mr, n2), ui = dd_div_d(-mi, n2);
   return {ur.hi, ur.lo, ui.hi, ui.lo};
+}
+
+// ---------------------------------------------------------------------------
+// z^n on the integer pipe.  On this GPU a 64-bit integer multiply-high issues
+// about four times as fast as an FP64 FMA and 32-bit multiply-adds about 37
+// times, so the valuation power (§8.2: z^l by repeated squaring) is computed
+// in 128-bit fixed-point mantissas: a value is ((-1)^sx X + i (-1)^sy Y) 2^(e-126)
+// with X, Y unsigned 128-bit and max(X, Y) in [2^126, 2^127).  Each product
+// keeps the top 128 bits of the 256-bit product (truncation error below 2^-123
+// relative), so after the at most 62 squarings and products of a 31-bit
+// exponent the relative error stays below 2^-85, far inside double-double use.
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+struct xint {
+  u128 x, y;
+  int sx, sy;  // signs (1 = negative)
+  long long e;
+};
+
+__host__ __device__ __forceinline__ unsigned long long umulhi64(unsigned long long a, unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((u128)a * b) >> 64);
+#endif
+}
+
+// top 128 bits of the 256-bit product a b (the two lowest partial products dropped)
+__host__ __device__ __forceinline__ u128 mulhi128(u128 a, u128 b) {
+  const unsigned long long a1 = (unsigned long long)(a >> 64), a0 = (unsigned long long)a;
+  const unsigned long long b1 = (unsigned long long)(b >> 64), b0 = (unsigned long long)b;
+  u128 p = (u128)a1 * b1;
+  p += umulhi64(a1, b0);
+  p += umulhi64(a0, b1);
+  return p;
+}
+
+__host__ __device__ __forceinline__ int clz128(u128 v) {
+  const unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;
+#ifdef __CUDA_ARCH__
+  return hi ? __clzll(hi) : 64 + __clzll(lo);
+#else
+  return hi ? __builtin_clzll(hi) : (lo ? 64 + __builtin_clzll(lo) : 128);
+#endif
+}
+
+// signed magnitude addition (a, sa) + (b, sb)
+__host__ __device__ __forceinline__ void sadd128(u128 a, int sa, u128 b, int sb, u128 &r, int &sr) {
+  if (sa == sb) {
+    r = a + b;
+    sr = sa;
+  } else if (a >= b) {
+    r = a - b;
+    sr = sa;
+  } else {
+    r = b - a;
+    sr = sb;
+  }
+}
+
+__host__ __device__ __forceinline__ xint xint_norm(u128 x, int sx, u128 y, int sy, long long e) {
+  const u128 m = x > y ? x : y;
+  xint r;
+  if (m == 0) {
+    r.x = r.y = 0;
+    r.sx = r.sy = 0;
+    r.e = 0;
+    return r;
+  }
+  const int sh = clz128(m) - 1;  // bring the top bit to position 126
+  if (sh > 0) {
+    x <<= sh;
+    y <<= sh;
+  } else if (sh < 0) {
+    x >>= 1;
+    y >>= 1;
+  }
+  r.x = x;
+  r.y = y;
+  r.sx = x ? sx : 0;
+  r.sy = y ? sy : 0;
+  r.e = e - sh;
+  return r;
+}
+
+__host__ __device__ __forceinline__ unsigned long long dbl_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+
+// a normalised double component (|c| < 1) as a 128-bit magnitude at scale 2^127
+__host__ __device__ __forceinline__ u128 u128_from_unit(double c) {
+  const unsigned long long bits = dbl_bits(c) & 0x7fffffffffffffffull;
+  const int ex = (int)(bits >> 52);
+  if (ex == 0) return 0;  // zero or below 2^-1022: negligible against the unit-size component
+  const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;
+  const int sh = ex - 948;  // |c| = m 2^(ex - 1075), scaled by 2^127
+  if (sh >= 0) return (u128)m << sh;
+  if (sh <= -64) return 0;
+  return (u128)(m >> (-sh));
+}
+
+__host__ __device__ __forceinline__ xint xint_mul(const xint &a, const xint &b) {
+  u128 p1 = mulhi128(a.x, b.x), p2 = mulhi128(a.y, b.y), p3 = mulhi128(a.x, b.y), p4 = mulhi128(a.y, b.x);
+  u128 re, im;
+  int sre, sim;
+  sadd128(p1, a.sx ^ b.sx, p2, 1 ^ a.sy ^ b.sy, re, sre);
+  sadd128(p3, a.sx ^ b.sy, p4, a.sy ^ b.sx, im, sim);
+  return xint_norm(re, sre, im, sim, a.e + b.e + 2);
+}
+
+__host__ __device__ __forceinline__ xint xint_sqr(const xint &a) {
+  u128 p1 = mulhi128(a.x, a.x), p2 = mulhi128(a.y, a.y), p3 = mulhi128(a.x, a.y);
+  u128 re;
+  int sre;
+  sadd128(p1, 0, p2, 1, re, sre);
+  return xint_norm(re, sre, p3 << 1, a.sx ^ a.sy, 2 * a.e + 2);
+}
+
+// (mr + i mi)^n for a unit-size complex (max(|mr|, |mi|) in [0.5, 1)), n >= 1
+__host__ __device__ __forceinline__ xint xint_pow_unit(double mr, double mi, long long n) {
+  xint z = xint_norm(u128_from_unit(mr), mr < 0.0, u128_from_unit(mi), mi < 0.0, -1);
+  xint r = z;
+#ifdef __CUDA_ARCH__
+  const int top = 63 - __clzll(n);
+#else
+  const int top = 63 - __builtin_clzll((unsigned long long)n);
+#endif
+  for (int b = top - 1; b >= 0; --b) {
+    r = xint_sqr(r);
+    if ((n >> b) & 1) r = xint_mul(r, z);
+  }
+  return r;
+}
+
+// the low 74 bits of a 128-bit magnitude, as a double scaled by 2^-74
+__host__ __device__ __forceinline__ double low74_scaled(u128 x) {
+  const unsigned long long lo = (unsigned long long)x, up = (unsigned long long)(x >> 64) & 0x3ffull;
+  return (double)up * 0x1p-10 + (double)lo * 0x1p-74;
+}
+
+// extended double-double from a 128-bit mantissa pair
+__device__ __forceinline__ xdd xdd_from_xint(const xint &v) {
+  // component = (-1)^s (H + L 2^-74) 2^(e - 52), H = X >> 74 (53 bits), L = X mod 2^74
+  const double hx = (double)(unsigned long long)(v.x >> 74);
+  const double lx = low74_scaled(v.x);
+  const double hy = (double)(unsigned long long)(v.y >> 74);
+  const double ly = low74_scaled(v.y);
+  xdd x;
+  x.rh = (v.sx ? -hx : hx) * 0x1p-53;
+  x.rl = (v.sx ? -lx : lx) * 0x1p-53;
+  x.ih = (v.sy ? -hy : hy) * 0x1p-53;
+  x.il = (v.sy ? -ly : ly) * 0x1p-53;
+  x.e = v.e + 1;
+  return xdd_norm(x);
+}
+
+// z^n (n >= 0) as extended double-double, computed on the integer pipe.
+__device__ __forceinline__ xdd xdd_pow_int(double zr, double zi, long long n) {
+  if (n <= 0) return {0.5, 0.0, 0.0, 0.0, 1};
+  const int f = frexp_exp(fmax(fabs(zr), fabs(zi)));
+  xint r = xint_pow_unit(scale2(zr, -f), scale2(zi, -f), n);
+  xdd x = xdd_from_xint(r);
+  x.e += (long long)f * n;
+  return x;
 }
 
 // Normalised FP64 output (fpe_xc64) from an extended double-double value.

@@ -255,7 +255,7 @@ template <bool CC, bool CZ, bool COMP>
 __device__ __forceinline__ void window_horner(const DevPoly &P, const double *__restrict__ b, double zr, double zi,
                                               long long lo, long long hi, double &hr, double &hm, double &cr,
                                               double &cm, long long &rho_lo) {
-  int j = P.piece_first[hi >> kLog2PieceLen];
+  int j = P.piece_first[hi >> P.log2_piece];
   while (P.piece_k0[j + 1] <= hi) ++j;
   if (CC) {
     double2 c = reinterpret_cast<const double2 *>(b)[hi];
@@ -338,7 +338,7 @@ template <bool CC, bool CZ>
 __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b, const cdd &u,
                                                   int ue, long long lo, long long hi, double &hr, double &hm,
                                                   long long &rho_hi) {
-  int j = P.piece_first[lo >> kLog2PieceLen];
+  int j = P.piece_first[lo >> P.log2_piece];
   while (P.piece_k0[j + 1] <= lo) ++j;
   if (CC) {
     double2 c = reinterpret_cast<const double2 *>(b)[lo];
@@ -425,6 +425,147 @@ __device__ __forceinline__ xdd range_sum(const DevPoly &P, double zr, double zi,
   return X;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 mode (FPE_FP32, p <= 24): coefficients rounded to FP32 on 32-term
+// pieces, Horner on the FP32 pipe.  The multiplier (2^beta z top-down,
+// 2^-beta / z bottom-up) is a float-float pair: an FP32-rounded multiplier
+// would put a relative error L 2^-24 on the L-th power, while 48 bits keep
+// it below 2^-28 for L <= 2^20.  8 FP32 FMA per complex term.
+// ---------------------------------------------------------------------------
+struct ff2 {
+  float rh, rl, ih, il;
+};
+__device__ __forceinline__ ff2 ff_split(double r, double i) {
+  const float rh = __double2float_rn(r), ih = __double2float_rn(i);
+  return {rh, __double2float_rn(r - (double)rh), ih, __double2float_rn(i - (double)ih)};
+}
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+template <bool CC, bool CZ>
+__device__ __forceinline__ void ff_step(float &hr, float &hm, const ff2 &w, float br, float bi) {
+  if (CZ) {
+    const float nr = fmaf(hr, w.rh, fmaf(-hm, w.ih, fmaf(hr, w.rl, fmaf(-hm, w.il, br))));
+    const float ni = fmaf(hr, w.ih, fmaf(hm, w.rh, fmaf(hr, w.il, fmaf(hm, w.rl, bi))));
+    hr = nr;
+    hm = ni;
+  } else {
+    hr = fmaf(hr, w.rh, fmaf(hr, w.rl, br));
+    if (CC) hm = fmaf(hm, w.rh, fmaf(hm, w.rl, bi));
+  }
+}
+
+template <bool CC>
+__device__ __forceinline__ void load_bf(const float *__restrict__ b, long long k, float &br, float &bi) {
+  if (CC) {
+    const float2 c = __ldg(reinterpret_cast<const float2 *>(b) + k);
+    br = c.x;
+    bi = c.y;
+  } else {
+    br = __ldg(b + k);
+    bi = 0.0f;
+  }
+}
+
+// top-down over [lo, hi]: sum b_k 2^rho(k) z^(k-lo) = h 2^rho(lo)
+template <bool CC, bool CZ>
+__device__ __forceinline__ void window_horner_f32(const DevPoly &P, double zr, double zi, long long lo,
+                                                  long long hi, float &hr, float &hm, long long &rho_lo) {
+  const float *__restrict__ b = P.bf;
+  int j = P.piece_first[hi >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= hi) ++j;
+  load_bf<CC>(b, hi, hr, hm);
+  long long k = hi - 1;
+  long long k0 = max((long long)P.piece_k0[j], lo);
+  while (true) {
+    const int beta = P.piece_beta[j];
+    const ff2 w = ff_split(scale2(zr, beta), CZ ? scale2(zi, beta) : 0.0);
+#pragma unroll 4
+    for (; k >= k0; --k) {
+      float br, bi;
+      load_bf<CC>(b, k, br, bi);
+      ff_step<CC, CZ>(hr, hm, w, br, bi);
+    }
+    if (k < lo) break;
+    --j;
+    const float s = pow2f(P.piece_delta[j]);
+    hr *= s;
+    hm *= s;
+    k0 = max((long long)P.piece_k0[j], lo);
+  }
+  rho_lo = P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
+}
+
+// bottom-up over [lo, hi] with multiplier 1/z = u 2^ue: sum b_k 2^rho(k) z^(k-hi) = h 2^rho(hi)
+template <bool CC, bool CZ>
+__device__ __forceinline__ void window_horner_rev_f32(const DevPoly &P, const cdd &u, int ue, long long lo,
+                                                      long long hi, float &hr, float &hm, long long &rho_hi) {
+  const float *__restrict__ b = P.bf;
+  int j = P.piece_first[lo >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= lo) ++j;
+  load_bf<CC>(b, lo, hr, hm);
+  long long k = lo + 1;
+  while (k <= hi) {
+    const int sh = ue - P.piece_beta[j];
+    const ff2 v = ff_split(scale2(u.rh, sh), CZ ? scale2(u.ih, sh) : 0.0);
+    const long long kend = min((long long)P.piece_k0[j + 1] - 1, hi);
+#pragma unroll 4
+    for (; k <= kend; ++k) {
+      float br, bi;
+      load_bf<CC>(b, k, br, bi);
+      ff_step<CC, CZ>(hr, hm, v, br, bi);
+    }
+    if (k > hi) break;
+    // k is the first index of piece j + 1: rescale, one step with v_j, then piece j + 1
+    const float s = pow2f(-P.piece_delta[j]);
+    hr *= s;
+    hm *= s;
+    float br, bi;
+    load_bf<CC>(b, k, br, bi);
+    ff_step<CC, CZ>(hr, hm, v, br, bi);
+    ++k;
+    ++j;
+  }
+  rho_hi = P.piece_rho0[j] + (long long)P.piece_beta[j] * (hi - P.piece_k0[j]);
+}
+
+// FP32 counterpart of range_sum
+template <bool CC, bool CZ>
+__device__ __forceinline__ xdd range_sum_f32(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
+                                             const cdd &u, long long lo, long long hi, long long kl,
+                                             long long &base) {
+  xdd X = xdd_zero();
+  const long long top_lo = max(kl, lo);
+  const long long low_hi = min(top_lo - 1, hi);
+  const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
+  if (has_up) {
+    float hr, hm;
+    long long rho;
+    window_horner_f32<CC, CZ>(P, zr, zi, top_lo, hi, hr, hm, rho);
+    if (hr != 0.0f || hm != 0.0f) X = xdd_from((double)hr, (double)hm, rho);
+    base = top_lo;
+  }
+  if (has_low) {
+    float hr, hm;
+    long long rho;
+    window_horner_rev_f32<CC, CZ>(P, u, -f, lo, low_hi, hr, hm, rho);
+    if (has_up && (X.rh != 0.0 || X.ih != 0.0)) X = xdd_mul_d(X, mr, mi, f);
+    if (hr != 0.0f || hm != 0.0f) X = xdd_add(X, xdd_from((double)hr, (double)hm, rho));
+    base = low_hi;
+  }
+  return X;
+}
+
+template <bool CC, bool CZ, bool F32>
+__device__ __forceinline__ xdd range_sum_any(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
+                                             const cdd &u, long long lo, long long hi, long long kl,
+                                             long long &base) {
+  if constexpr (F32)
+    return range_sum_f32<CC, CZ>(P, zr, zi, mr, mi, f, u, lo, hi, kl, base);
+  else
+    return range_sum<CC, CZ>(P, zr, zi, mr, mi, f, u, lo, hi, kl, base);
+}
+
 // Compensated top-down sum over [lo, hi] relative to z^lo (FPE_ACCURATE).
 template <bool CC, bool CZ>
 __device__ __forceinline__ xdd range_sum_comp(const DevPoly &P, double zr, double zi, long long lo, long long hi) {
@@ -436,7 +577,7 @@ __device__ __forceinline__ xdd range_sum_comp(const DevPoly &P, double zr, doubl
   return xdd_norm(x);
 }
 
-template <bool CC, bool CZ, bool ACC>
+template <bool CC, bool CZ, bool ACC, bool F32>
 __global__ void __launch_bounds__(128) k_sum_short(DevPoly P, int n, const PointRec *__restrict__ rec,
                                                    fpe_xc64 *__restrict__ out, int32_t *nterms,
                                                    int32_t *bits_lost) {
@@ -458,9 +599,9 @@ __global__ void __launch_bounds__(128) k_sum_short(DevPoly P, int n, const Point
       const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
       cdd u = {0.0, 0.0, 0.0, 0.0};
       if (r.lo < r.kl) u = recip_dd(mr, mi);
-      X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+      X = range_sum_any<CC, CZ, F32>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
     }
-    xdd pw = xdd_pow(r.zr, r.zi, base + P.v);
+    xdd pw = xdd_pow_int(r.zr, r.zi, base + P.v);
     o = xdd_out(xdd_mul(X, pw));
   }
   out[r.orig] = o;
@@ -500,7 +641,7 @@ __device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
   return g == 0 ? i : cap + gbase + g - 1;
 }
 
-template <bool CC, bool CZ, bool ACC>
+template <bool CC, bool CZ, bool ACC, bool F32>
 __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *__restrict__ rec,
                                                     const int32_t *__restrict__ long_list,
                                                     const int32_t *__restrict__ long_ngroups,
@@ -540,11 +681,11 @@ __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *_
       const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
       const cdd u = recip_dd(mr, mi);
       long long base;
-      xdd X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
+      xdd X = range_sum_any<CC, CZ, F32>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
       if (chi < r.kl) {
         carry = xdd_mul(X, xdd_from_cdd(u, -f));  // below the peak: X / z to the next slot
       } else if (base > clo) {
-        sv = xdd_mul(X, xdd_pow(r.zr, r.zi, base - clo));
+        sv = xdd_mul(X, xdd_pow_int(r.zr, r.zi, base - clo));
       } else {
         sv = X;
       }
@@ -555,7 +696,7 @@ __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *_
       if (lane > 0) sv = xdd_add(sv, inc);
       gout = shfl_down_xdd(carry, 31);  // lane 31's carry, read by lane 0
     }
-    xdd w = xdd_pow(r.zr, r.zi, C);
+    xdd w = xdd_pow_int(r.zr, r.zi, C);
     for (int s = 1; s < 32; s <<= 1) {
       xdd other = shfl_down_xdd(sv, s);
       if ((lane & (2 * s - 1)) == 0) sv = xdd_add(sv, xdd_mul(w, other));
@@ -586,7 +727,7 @@ __global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec
     if (ng > 1) {
       const long long L = r.hi - r.lo + 1;
       const long long C = (L + 32LL * ng - 1) / (32LL * ng);
-      const xdd W = xdd_pow(r.zr, r.zi, 32 * C);
+      const xdd W = xdd_pow_int(r.zr, r.zi, 32 * C);
       acc = xdd_add(acc, gcarry[group_slot(i, ng - 2, gb, cap)]);
       for (int g = ng - 2; g >= 0; --g) {
         xdd sg = gval[group_slot(i, g, gb, cap)];
@@ -594,7 +735,7 @@ __global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec
         acc = xdd_add(xdd_mul(acc, W), sg);
       }
     }
-    const xdd pw = xdd_pow(r.zr, r.zi, r.lo + P.v);
+    const xdd pw = xdd_pow_int(r.zr, r.zi, r.lo + P.v);
     const fpe_xc64 o = xdd_out(xdd_mul(acc, pw));
     out[r.orig] = o;
     write_diag(P, r, o, nterms, bits_lost);
@@ -616,20 +757,20 @@ static int num_sms() {
   return sms;
 }
 
-template <bool CC, bool CZ, bool ACC>
-static void launch_sums3(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
+template <bool CC, bool CZ, bool ACC, bool F32>
+static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
                          cudaStream_t st) {
   Workspace &w = P->ws;
   const int cap = (int)w.cap, xcap = (int)w.extra_cap;
   {
     ProfScope ps("k_sum_short", st);
-    k_sum_short<CC, CZ, ACC><<<(n + 127) / 128, 128, 0, st>>>(P->dev, n, w.rec, out, nterms, bits_lost);
+    k_sum_short<CC, CZ, ACC, F32><<<(n + 127) / 128, 128, 0, st>>>(P->dev, n, w.rec, out, nterms, bits_lost);
   }
   {
     ProfScope ps("k_sum_groups", st);
-    k_sum_groups<CC, CZ, ACC><<<num_sms() * 4, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups,
-                                                             w.long_gbase, w.extra_owner, w.extra_group, w.bins,
-                                                             cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
+    k_sum_groups<CC, CZ, ACC, F32><<<num_sms() * 4, 128, 0, st>>>(
+        P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group, w.bins, cap, xcap,
+        (xdd *)w.group_val, (xdd *)w.group_carry);
   }
   {
     ProfScope ps("k_finalize_long", st);
@@ -641,10 +782,12 @@ static void launch_sums3(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
 
 template <bool CC, bool CZ>
 static void launch_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
-  if (P->dev.accurate)
-    launch_sums3<CC, CZ, true>(P, n, out, nterms, bits_lost, st);
+  if (P->dev.fp32)
+    launch_sums4<CC, CZ, false, true>(P, n, out, nterms, bits_lost, st);
+  else if (P->dev.accurate)
+    launch_sums4<CC, CZ, true, false>(P, n, out, nterms, bits_lost, st);
   else
-    launch_sums3<CC, CZ, false>(P, n, out, nterms, bits_lost, st);
+    launch_sums4<CC, CZ, false, false>(P, n, out, nterms, bits_lost, st);
 }
 
 fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, fpe_xc64 *out,
@@ -821,24 +964,34 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
                                              w.extra_group, (int)w.extra_cap, P->d_status);
       const int cap = (int)w.cap, xcap = (int)w.extra_cap;
       const bool acc = P->dev.accurate != 0;
-#define FPE_NOALLOC_SUMS(CCv, CZv, ACCv)                                                                       \
+#define FPE_NOALLOC_SUMS(CCv, CZv, ACCv, F32v)                                                                       \
   do {                                                                                                         \
-    k_sum_short<CCv, CZv, ACCv><<<(ni + 127) / 128, 128, 0, st>>>(P->dev, ni, w.rec, out, nterms, bits_lost); \
-    k_sum_groups<CCv, CZv, ACCv><<<num_sms() * 4, 128, 0, st>>>(                                              \
+    k_sum_short<CCv, CZv, ACCv, F32v><<<(ni + 127) / 128, 128, 0, st>>>(P->dev, ni, w.rec, out, nterms,       \
+                                                                        bits_lost);                           \
+    k_sum_groups<CCv, CZv, ACCv, F32v><<<num_sms() * 4, 128, 0, st>>>(                                        \
         P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group, w.bins, cap,   \
         xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                                                       \
     k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase,   \
                                                    w.bins, cap, (const xdd *)w.group_val,                      \
                                                    (const xdd *)w.group_carry, out, nterms, bits_lost);        \
   } while (0)
+      const bool f32 = P->dev.fp32 != 0;
       if (cc && cz) {
-        if (acc) FPE_NOALLOC_SUMS(true, true, true); else FPE_NOALLOC_SUMS(true, true, false);
+        if (f32) FPE_NOALLOC_SUMS(true, true, false, true);
+        else if (acc) FPE_NOALLOC_SUMS(true, true, true, false);
+        else FPE_NOALLOC_SUMS(true, true, false, false);
       } else if (cc) {
-        if (acc) FPE_NOALLOC_SUMS(true, false, true); else FPE_NOALLOC_SUMS(true, false, false);
+        if (f32) FPE_NOALLOC_SUMS(true, false, false, true);
+        else if (acc) FPE_NOALLOC_SUMS(true, false, true, false);
+        else FPE_NOALLOC_SUMS(true, false, false, false);
       } else if (cz) {
-        if (acc) FPE_NOALLOC_SUMS(false, true, true); else FPE_NOALLOC_SUMS(false, true, false);
+        if (f32) FPE_NOALLOC_SUMS(false, true, false, true);
+        else if (acc) FPE_NOALLOC_SUMS(false, true, true, false);
+        else FPE_NOALLOC_SUMS(false, true, false, false);
       } else {
-        if (acc) FPE_NOALLOC_SUMS(false, false, true); else FPE_NOALLOC_SUMS(false, false, false);
+        if (f32) FPE_NOALLOC_SUMS(false, false, false, true);
+        else if (acc) FPE_NOALLOC_SUMS(false, false, true, false);
+        else FPE_NOALLOC_SUMS(false, false, false, false);
       }
 #undef FPE_NOALLOC_SUMS
       e = cudaGetLastError();

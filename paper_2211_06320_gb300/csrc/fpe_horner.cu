@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(128) k_horner(DevPoly P, int n, const double *
     xdd x = {r.hi, r.lo, i.hi, i.lo, rho0 + E};
     v = xdd_norm(x);
   }
-  if (P.v > 0) v = xdd_mul(v, xdd_pow(zr, zi, P.v));
+  if (P.v > 0) v = xdd_mul(v, xdd_pow_int(zr, zi, P.v));
   out[p] = xdd_out(v);
 }
 

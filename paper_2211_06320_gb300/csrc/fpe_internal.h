@@ -13,14 +13,14 @@
 namespace fpe {
 
 // Coefficient "pieces": the trimmed index range [0, D] is cut at every
-// multiple of kPieceLen and at every cover vertex.  On piece j the
-// coefficients are stored as b_k = a_k * 2^-rho(k) with
+// multiple of the piece length (128 in FP64, 32 in FP32) and at every cover
+// vertex.  On piece j the coefficients are stored as b_k = a_k * 2^-rho(k) with
 // rho(k) = rho0[j] + beta[j] * (k - k0[j]) an integer line that follows the
-// cover to within kPieceLen/2 + 1 bits, so that every kept b_k lies in
-// [2^-(T + kPieceLen/2 + 3), 2^(kPieceLen/2 + 2)] and Horner's recurrence on
-// piece j runs at the exactly rescaled point w_j = 2^beta[j] * z.
-constexpr int kLog2PieceLen = 7;
-constexpr int kPieceLen = 1 << kLog2PieceLen;
+// cover to within half a piece length plus one bit, so that every kept b_k
+// lies in [2^-(T + len/2 + 3), 2^(len/2 + 2)] and Horner's recurrence on piece
+// j runs at the exactly rescaled point w_j = 2^beta[j] * z.
+constexpr int kLog2PieceLen = 7;       // FP64 coefficients
+constexpr int kLog2PieceLenF32 = 5;    // FP32 coefficients: keeps b_k and partial sums inside FP32 range
 
 // Bucketing of points by log2|z| before summation (points of similar modulus
 // get similar windows; §8.1 suggests grouping evaluations of similar size).
@@ -46,11 +46,12 @@ struct DevPoly {
   const double *b;             // FPE coefficients (bad ones zeroed), trimmed k = 0..D;
                                // complex: interleaved (re, im); real: one double
   const double *b_full;        // every coefficient, same layout (Horner baselines)
+  const float *bf;             // FPE_FP32: the FPE coefficients rounded to FP32 (same layout)
   const int32_t *piece_k0;     // npieces + 1 entries, last = D + 1
   const int32_t *piece_beta;   // integer slope of rho on the piece
   const int32_t *piece_delta;  // exponent shift applied to h when entering piece j from j + 1
   const int64_t *piece_rho0;   // rho at the piece's first index
-  const int32_t *piece_first;  // per block of kPieceLen indices: first piece overlapping it
+  const int32_t *piece_first;  // per block of 2^log2_piece indices: first piece overlapping it
   const double *hull_k;        // trimmed abscissae of the cover's vertices
   const double *hull_s;        // their scales
   const double *hull_sig;      // slopes of the n_hull - 1 segments
@@ -62,8 +63,8 @@ struct DevPoly {
   int32_t npieces;
   int32_t complex_coef;
   int32_t fp32;
-  int32_t accurate;  // FPE_ACCURATE: compensated window sums
-  int32_t pad0;
+  int32_t accurate;    // FPE_ACCURATE: compensated window sums
+  int32_t log2_piece;  // kLog2PieceLen or kLog2PieceLenF32
   double a0_re, a0_im;  // a_0 as a normalised mantissa (0 when v > 0)
   int64_t a0_e;
 };

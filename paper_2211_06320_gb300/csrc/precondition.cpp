@@ -207,8 +207,8 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
     set_error("fpe_precondition: p must be in [2, 53] ([2, 24] with FPE_FP32)");
     return FPE_ERR_INVALID_ARG;
   }
-  if (fp32) {
-    set_error("fpe_precondition: FPE_FP32 is not available in this build");
+  if (fp32 && (flags & FPE_ACCURATE)) {
+    set_error("fpe_precondition: FPE_FP32 with FPE_ACCURATE is not available in this build");
     return FPE_ERR_UNSUPPORTED;
   }
   bool cplx = im != nullptr && !(flags & FPE_REAL);
@@ -307,7 +307,9 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
     P->n_good = gcount[D + 1];
   }
 
-  // pieces: cut [0, D] at multiples of kPieceLen and at every vertex
+  // pieces: cut [0, D] at multiples of the piece length and at every vertex
+  const int log2_piece = fp32 ? kLog2PieceLenF32 : kLog2PieceLen;
+  const int64_t kPieceLen = (int64_t)1 << log2_piece;
   std::vector<int32_t> pk0, pbeta, pdelta, pfirst;
   std::vector<int64_t> prho0;
   {
@@ -361,6 +363,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   // coefficients b_k = a_k 2^-rho(k), trimmed; bad ones zeroed in b
   const int stride = cplx ? 2 : 1;
   std::vector<double> b((D + 1) * stride), bfull((D + 1) * stride);
+  std::vector<float> bf;
   {
     int j = 0;
     const int np = P->dev.npieces;
@@ -379,6 +382,11 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
         b[k * stride + 1] = g ? bi : 0.0;
       }
     }
+  }
+
+  if (fp32) {  // the p-bit representation of the kept coefficients (Thm. equivAlgo's tilde a_k)
+    bf.resize(b.size());
+    for (size_t i = 0; i < b.size(); ++i) bf[i] = (float)b[i];
   }
 
   // a_0 for z = 0 (§4.2: P(0) = a_0), normalised
@@ -401,7 +409,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   fpe_status st;
   DevPoly &dp = P->dev;
   if (!host_only) {
-    if ((st = upload(P, b, &dp.b)) != FPE_OK ||
+    if ((st = upload(P, b, &dp.b)) != FPE_OK || (st = upload(P, bf, &dp.bf)) != FPE_OK ||
         (st = upload(P, bfull, &dp.b_full)) != FPE_OK ||
         (st = upload(P, pk0, &dp.piece_k0)) != FPE_OK ||
         (st = upload(P, pbeta, &dp.piece_beta)) != FPE_OK ||
@@ -429,6 +437,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   dp.complex_coef = cplx ? 1 : 0;
   dp.fp32 = fp32 ? 1 : 0;
   dp.accurate = (flags & FPE_ACCURATE) ? 1 : 0;
+  dp.log2_piece = log2_piece;
 
   // P' (§7.2): coefficients (k+1) a_{k+1}, rounded once, preconditioned separately
   if (flags & FPE_WITH_DERIV) {

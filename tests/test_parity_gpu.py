@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _parity import TOL_FP64, error_ratio, windows_agree
+from _parity import TOL_FP32, TOL_FP64, error_ratio, windows_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -361,3 +361,52 @@ def test_long_windows_group_overflow(env):
     pts = W.Points(np.cos(t), np.sin(t))
     st = check_workload(env, coef, pts, n_full=0, check_full=False)
     print("unit circle, d=2^17-1", st)
+
+
+# --------------------------------------------------------------- FP32 mode (p = 24)
+
+@pytest.mark.parametrize("name", ["unit_square_d1000", "unit_disk_d2pow20", "inverse_factorial", "mandelbrot",
+                                  "half_circle_complex", "lognormal", "real_coef_complex_pts",
+                                  "complex_coef_real_pts", "unit_circle"])
+def test_fp32_mode(env, name):
+    """FPE_FP32: windows and G_p at p = 24, FP32 coefficients and Horner on the
+    FP32 pipe; |P_gpu - P_ref| <= 2^-21 S(z)."""
+    torch, F = env
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    n_full = 128
+    if name == "unit_square_d1000":
+        wl = W.unit_square_d1000()
+        coef, pts = wl.coeffs, wl.points
+    elif name == "unit_disk_d2pow20":
+        wl = W.unit_disk_d2pow20(n_points=1 << 18)
+        coef, pts = wl.coeffs, wl.points
+        n_full = 96
+    elif name == "inverse_factorial":
+        wl = W.inverse_factorial_d1e5(n_points=1 << 14)
+        coef, pts = wl.coeffs, wl.points
+    elif name == "mandelbrot":
+        wl = W.mandelbrot_real(11, n_points=1 << 14)
+        coef, pts = wl.coeffs, wl.points
+    elif name == "half_circle_complex":
+        coef, pts = W.half_circle(1000, True, rng), W.sphere_points(4096, rng)
+    elif name == "lognormal":
+        coef, pts = W.lognormal_profile(20000, 0.005, rng), W.sphere_points(4096, rng)
+    elif name == "real_coef_complex_pts":
+        coef, pts = W.Coeffs(rng.uniform(-1, 1, 5000)), W.sphere_points(4096, rng)
+    elif name == "complex_coef_real_pts":
+        coef, pts = W.unit_disk_complex(5000, rng), W.real_circle_points(4096, rng)
+    else:
+        coef = W.unit_disk_complex((1 << 16) - 1, rng)
+        t = rng.uniform(0, 2 * math.pi, 1024)
+        pts = W.Points(np.cos(t), np.sin(t))
+        n_full = 16
+    st = check_workload(env, coef, pts, p=24, n_full=n_full, tol=TOL_FP32, flags=F.FPE_FP32)
+    print("fp32", name, st)
+
+
+def test_fp32_flags(env):
+    torch, F = env
+    c = W.unit_square_complex(10, np.random.default_rng(0))
+    with pytest.raises(F.FpeError) as e:
+        F.fpe_precondition(c.re, c.im, None, 53, F.FPE_FP32)
+    assert e.value.status == F.FPE_ERR_INVALID_ARG
