@@ -124,6 +124,48 @@ def oracle_cpu_baseline(wl, n_sample: int):
                       f"window sums); preconditioning {t_pre:.2f} s not included"}
 
 
+def batched_leg(F, torch, st):
+    """4096 polynomials, degree log-uniform in [16, 2^16], log2|a_k| = s k + N(0,4),
+    256 sphere points each, one fpe_batch_eval (FP64 p = 53 and FP32 p = 24)."""
+    import workloads as W
+    wls = W.batched_lognormal(n_poly=4096, pts_per_poly=256, seed=3)
+    offs = np.concatenate([[0], np.cumsum([w.points.n for w in wls])]).astype(np.int64)
+    zr = torch.from_numpy(np.concatenate([w.points.re for w in wls])).cuda()
+    zi = torch.from_numpy(np.concatenate([w.points.im for w in wls])).cuda()
+    res = {"polynomials": len(wls), "points": int(offs[-1]),
+           "coefficients": int(sum(w.coeffs.n_coef for w in wls))}
+    for name, p, flags in (("fp64", 53, 0), ("fp32", 24, F.FPE_FP32)):
+        t0 = time.perf_counter()
+        polys = [F.fpe_precondition(w.coeffs.re, w.coeffs.im, None, p, flags) for w in wls]
+        res[f"{name}_precondition_s"] = time.perf_counter() - t0
+        B = F.fpe_batch_create(polys, offs)
+        out = F.empty_out(B.n)
+        F.fpe_batch_eval(B, zr, zi, out=out)
+        F.fpe_batch_sync(B)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(5):
+            F.fpe_batch_eval(B, zr, zi, out=out)
+        b.record(st)
+        torch.cuda.synchronize()
+        res[f"{name}_evals_per_s"] = 5 * B.n / (a.elapsed_time(b) * 1e-3)
+        # the same evaluation replayed from a captured CUDA graph
+        s2 = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s2):
+            F.fpe_batch_eval(B, zr, zi, out=out, stream=s2)
+        g.replay()
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(5):
+            g.replay()
+        b.record(st)
+        torch.cuda.synchronize()
+        res[f"{name}_graph_evals_per_s"] = 5 * B.n / (a.elapsed_time(b) * 1e-3)
+        del g, B, polys
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -314,6 +356,7 @@ def main():
             extras["fpe_fp32_p24_evals_per_s"] = n / (a.elapsed_time(b) * 1e-3)
             extras["fpe_fp32_p24_avg_kept_terms"] = float(nt32.double().mean().item())
             extras["cpu_baseline"] = oracle_cpu_baseline(wl, 4096)
+            extras["batched"] = batched_leg(F, torch, st)
 
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,

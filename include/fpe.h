@@ -176,16 +176,36 @@ fpe_status fpe_eval_deriv(fpe_poly_t P, const double *z_re, const double *z_im, 
                           void *cuda_stream);
 
 /*
- * fpe_eval_batch -- many polynomials, each at its own points (§8.1: the
- * algorithm is embarrassingly parallel over points).  Polynomial i is
- * evaluated at points pt_offsets[i] .. pt_offsets[i+1]-1.
- *   P           host array of npoly handles (all on the current device,
- *               all FP64 or all FP32).
- *   pt_offsets  HOST array of npoly+1 nondecreasing int64, pt_offsets[0] = 0.
- *   z_re, z_im  device arrays of pt_offsets[npoly] doubles (z_im may be NULL).
- *   out         device array of pt_offsets[npoly] fpe_xc64.
- * Asynchronous; one launch per kernel stage for the whole batch.
+ * Batched evaluation -- many polynomials, each at its own points, in one fixed
+ * sequence of kernel launches (§8.1: the algorithm is embarrassingly parallel
+ * over points).
+ *
+ * fpe_batch_create builds a batch over npoly handles (all on one device, all
+ * real or all complex, the same FPE_FP32 and FPE_ACCURATE flags; otherwise
+ * FPE_ERR_UNSUPPORTED).  Polynomial i owns points pt_offsets[i] ..
+ * pt_offsets[i+1]-1 (HOST array of npoly+1 nondecreasing int64 starting at 0,
+ * total below 2^31).  It uploads the polynomials' descriptors and allocates
+ * the scratch for every point once; the handles must outlive the batch and
+ * must not be re-preconditioned.  Synchronous.
+ *
+ * fpe_batch_eval evaluates all points: z_re, z_im (z_im NULL = real points)
+ * are device arrays of pt_offsets[npoly] doubles, out a device array of that
+ * many fpe_xc64, nterms a device int32 array or NULL.  It allocates nothing
+ * and does not synchronise, so the call can be recorded into a CUDA graph on
+ * a capturing stream and replayed.  Calls on one batch must not overlap.
+ *
+ * fpe_batch_sync waits for cuda_stream and returns FPE_ERR_NONFINITE if a
+ * point was NaN/inf since the last sync.  fpe_batch_destroy frees the batch.
+ *
+ * fpe_eval_batch is the one-shot form: create, evaluate, sync, destroy
+ * (synchronous; use the batch handle to evaluate the same polynomials again).
  */
+typedef struct fpe_batch_s *fpe_batch_t;
+fpe_status fpe_batch_create(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, fpe_batch_t *out);
+fpe_status fpe_batch_eval(fpe_batch_t B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
+                          void *cuda_stream);
+fpe_status fpe_batch_sync(fpe_batch_t B, void *cuda_stream);
+void fpe_batch_destroy(fpe_batch_t B);
 fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,
                           const double *z_im, fpe_xc64 *out, void *cuda_stream);
 

@@ -37,7 +37,8 @@ EXPORTED = [
     "fpe_precondition", "fpe_eval", "fpe_eval_host", "fpe_eval_deriv", "fpe_eval_batch", "fpe_horner",
     "fpe_info", "fpe_get_hull", "fpe_get_good", "fpe_get_windows", "fpe_sync", "fpe_destroy",
     "fpe_status_string", "fpe_last_error", "fpe_profile_enable", "fpe_profile_reset", "fpe_profile_read",
-    "fpe_measure_fma_peak", "fpe_eval_noalloc",
+    "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
+    "fpe_batch_destroy",
 ]
 
 
@@ -85,6 +86,10 @@ def _load():
         "fpe_profile_read": ([ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], I32),
         "fpe_measure_fma_peak": ([I32, I32, ctypes.POINTER(D)], I32),
         "fpe_eval_noalloc": ([P, P, P, I64, P, P, P, P], I32),
+        "fpe_batch_create": ([P, I64, P, ctypes.POINTER(P)], I32),
+        "fpe_batch_eval": ([P, P, P, P, P, P], I32),
+        "fpe_batch_sync": ([P, P], I32),
+        "fpe_batch_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -313,3 +318,45 @@ def fpe_eval_noalloc(P: Poly, z_re, z_im=None, out=None, nterms=None, bits_lost=
     _check(lib.fpe_eval_noalloc(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _dptr(nterms),
                                 _dptr(bits_lost), _stream(stream)), "fpe_eval_noalloc")
     return out
+
+
+class Batch:
+    """A batch of preconditioned polynomials with fixed point offsets (fpe_batch_t)."""
+
+    def __init__(self, polys: Sequence[Poly], pt_offsets):
+        lib = _load()
+        self.polys = list(polys)  # keep the handles alive
+        self.offsets = np.ascontiguousarray(pt_offsets, dtype=np.int64)
+        hs = (ctypes.c_void_p * len(self.polys))(*[p.handle.value for p in self.polys])
+        h = ctypes.c_void_p()
+        _check(lib.fpe_batch_create(hs, len(self.polys), _np_ptr(self.offsets), ctypes.byref(h)), "fpe_batch_create")
+        self._h = h
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                _load().fpe_batch_destroy(self._h)
+                self._h = ctypes.c_void_p(None)
+        except Exception:
+            pass
+
+
+def fpe_batch_create(polys: Sequence[Poly], pt_offsets) -> Batch:
+    return Batch(polys, pt_offsets)
+
+
+def fpe_batch_eval(B: Batch, z_re, z_im=None, out=None, nterms=None, stream=None):
+    lib = _load()
+    if out is None:
+        out = empty_out(B.n, z_re.device)
+    _check(lib.fpe_batch_eval(B._h, _dptr(z_re), _dptr(z_im), _dptr(out), _dptr(nterms), _stream(stream)),
+           "fpe_batch_eval")
+    return out
+
+
+def fpe_batch_sync(B: Batch, stream=None):
+    _check(_load().fpe_batch_sync(B._h, _stream(stream)), "fpe_batch_sync")

@@ -145,25 +145,126 @@ fpe_status fpe_eval_deriv(fpe_poly_t P, const double *z_re, const double *z_im, 
   return launch_eval(P->deriv, z_re, z_im, n, out, nullptr, nullptr, (cudaStream_t)cuda_stream);
 }
 
-fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,
-                          const double *z_im, fpe_xc64 *out, void *cuda_stream) {
-  if (!P || npoly < 0 || !pt_offsets || pt_offsets[0] != 0) {
-    set_error("fpe_eval_batch: bad arguments");
+fpe_status fpe_batch_create(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, fpe_batch_t *out) {
+  if (!out) {
+    set_error("fpe_batch_create: out is NULL");
+    return FPE_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!P || npoly < 1 || npoly > ((int64_t)1 << 26) || !pt_offsets || pt_offsets[0] != 0) {
+    set_error("fpe_batch_create: need npoly >= 1 handles and offsets starting at 0");
     return FPE_ERR_INVALID_ARG;
   }
   for (int64_t i = 0; i < npoly; ++i) {
-    if (!P[i] || pt_offsets[i + 1] < pt_offsets[i]) {
-      set_error("fpe_eval_batch: NULL handle or decreasing offsets");
+    if (!P[i] || (P[i]->flags & FPE_HOST_ONLY) || pt_offsets[i + 1] < pt_offsets[i]) {
+      set_error("fpe_batch_create: NULL or host-only handle, or decreasing offsets");
       return FPE_ERR_INVALID_ARG;
     }
+    if (P[i]->device != P[0]->device || P[i]->complex_coef != P[0]->complex_coef ||
+        P[i]->dev.fp32 != P[0]->dev.fp32 || P[i]->dev.accurate != P[0]->dev.accurate) {
+      set_error("fpe_batch_create: all handles must share the device, real/complex coefficients, FPE_FP32 and "
+                "FPE_ACCURATE");
+      return FPE_ERR_UNSUPPORTED;
+    }
   }
-  for (int64_t i = 0; i < npoly; ++i) {
-    int64_t a = pt_offsets[i], b = pt_offsets[i + 1];
-    if (b == a) continue;
-    fpe_status s = fpe_eval(P[i], z_re + a, z_im ? z_im + a : nullptr, b - a, out + a, nullptr, nullptr, cuda_stream);
-    if (s != FPE_OK) return s;
+  const int64_t ntotal = pt_offsets[npoly];
+  if (ntotal >= ((int64_t)1 << 31)) {
+    set_error("fpe_batch_create: at most 2^31 - 1 points in a batch");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P[0]->device);
+  fpe_batch_s *B = new fpe_batch_s();
+  B->device = P[0]->device;
+  B->npoly = npoly;
+  B->ntotal = ntotal;
+  B->complex_coef = P[0]->complex_coef;
+  B->fp32 = P[0]->dev.fp32 != 0;
+  B->accurate = P[0]->dev.accurate != 0;
+  B->polys.assign(P, P + npoly);
+  B->offsets.assign(pt_offsets, pt_offsets + npoly + 1);
+  std::vector<DevPoly> table(npoly);
+  for (int64_t i = 0; i < npoly; ++i) table[i] = P[i]->dev;
+  std::vector<int32_t> pid(std::max<int64_t>(ntotal, 1));
+  for (int64_t i = 0; i < npoly; ++i)
+    for (int64_t j = pt_offsets[i]; j < pt_offsets[i + 1]; ++j) pid[j] = (int32_t)i;
+  const int kBins = kBatchBins;
+  cudaError_t e = cudaSuccess;
+  auto A = [&e](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  A((void **)&B->d_table, npoly * sizeof(DevPoly));
+  A((void **)&B->d_pid, pid.size() * sizeof(int32_t));
+  A((void **)&B->d_offsets, (npoly + 1) * sizeof(int64_t));
+  A((void **)&B->d_hist, npoly * kBins * sizeof(uint32_t));
+  A((void **)&B->d_cursor, npoly * kBins * sizeof(uint32_t));
+  A((void **)&B->d_cnt, kNumCounters * sizeof(uint32_t));
+  A((void **)&B->d_status, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(B->d_table, table.data(), npoly * sizeof(DevPoly), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B->d_pid, pid.data(), pid.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->d_offsets, pt_offsets, (npoly + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(B->d_status, 0, sizeof(int32_t));
+  fpe_status st = e == cudaSuccess ? alloc_workspace(B->ws, ntotal) : cuda_fail(e, "fpe_batch_create");
+  if (st != FPE_OK) {
+    fpe_batch_destroy(B);
+    return st;
+  }
+  *out = B;
+  return FPE_OK;
+}
+
+fpe_status fpe_batch_eval(fpe_batch_t B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
+                          void *cuda_stream) {
+  if (!B || (B->ntotal > 0 && (!z_re || !out))) {
+    set_error("fpe_batch_eval: NULL batch, point or output pointer");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(B->device);
+  return launch_batch(B, z_re, z_im, out, nterms, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_batch_sync(fpe_batch_t B, void *cuda_stream) {
+  if (!B) {
+    set_error("NULL batch");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(B->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int32_t h = 0;
+  if ((e = cudaMemcpy(&h, B->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy(status)");
+  if (h) {
+    cudaMemset(B->d_status, 0, sizeof(int32_t));
+    set_error("non-finite evaluation point");
+    return FPE_ERR_NONFINITE;
   }
   return FPE_OK;
+}
+
+void fpe_batch_destroy(fpe_batch_t B) {
+  if (!B) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(B->device);
+  void *ptrs[] = {B->d_table, B->d_pid, B->d_offsets, B->d_hist, B->d_cursor, B->d_cnt, B->d_status};
+  for (void *a : ptrs)
+    if (a) cudaFree(a);
+  free_workspace(B->ws);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete B;
+}
+
+fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,
+                          const double *z_im, fpe_xc64 *out, void *cuda_stream) {
+  if (npoly == 0) return FPE_OK;
+  fpe_batch_t B = nullptr;
+  fpe_status s = fpe_batch_create(P, npoly, pt_offsets, &B);
+  if (s != FPE_OK) return s;
+  s = fpe_batch_eval(B, z_re, z_im, out, nullptr, cuda_stream);
+  if (s == FPE_OK) s = fpe_batch_sync(B, cuda_stream);
+  fpe_batch_destroy(B);
+  return s;
 }
 
 fpe_status fpe_horner(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,

@@ -188,6 +188,33 @@ __global__ void k_scan_bins(uint32_t *bins) {
   if (t < kNumCounters) bins[2 * kNumBins + t] = 0;
 }
 
+// Lists a long-window point and reserves its warp groups: group 0 lives in
+// slot i (its list index), groups 1.. in extra slots; when the extra slots run
+// out the window gets one group and the slots of its failed reservation that
+// exist are marked unused (-1).
+__device__ __forceinline__ void list_long_window(long long L, uint32_t pos, uint32_t *cnt, int32_t *long_list,
+                                                 int32_t *long_ngroups, int32_t *long_gbase, int32_t *extra_owner,
+                                                 int32_t *extra_group, int extra_cap) {
+  uint32_t i = atomicAdd(&cnt[kCntLong], 1u);
+  long_list[i] = (int32_t)pos;
+  int ng = (int)((L + kGroupSpan - 1) / kGroupSpan);
+  int gb = 0;
+  if (ng > 1) {
+    gb = (int)atomicAdd(&cnt[kCntExtra], (uint32_t)(ng - 1));
+    if (gb + ng - 1 > extra_cap) {
+      for (int g = 1; g < ng && gb + g - 1 < extra_cap; ++g) extra_owner[gb + g - 1] = -1;
+      ng = 1;
+    } else {
+      for (int g = 1; g < ng; ++g) {
+        extra_owner[gb + g - 1] = (int32_t)i;
+        extra_group[gb + g - 1] = g;
+      }
+    }
+  }
+  long_ngroups[i] = ng;
+  long_gbase[i] = gb;
+}
+
 template <bool CZ>
 __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, const double *__restrict__ zim,
                           const long long *__restrict__ lo, const long long *__restrict__ hi,
@@ -216,30 +243,12 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
   r.kl = kl[p];
   r.N = N[p];
   r.orig = p;
+  r.pid = 0;
+  r.pad = 0;
   rec[pos] = r;
-  const long long L = r.hi - r.lo + 1;
-  if (!r.flags && L > kLongWindow) {
-    // group 0 lives in slot i; groups 1.. in reserved extra slots (one group if none are left)
-    uint32_t i = atomicAdd(&bins[2 * kNumBins + kCntLong], 1u);
-    long_list[i] = (int32_t)pos;
-    int ng = (int)((L + kGroupSpan - 1) / kGroupSpan);
-    int gb = 0;
-    if (ng > 1) {
-      gb = (int)atomicAdd(&bins[2 * kNumBins + kCntExtra], (uint32_t)(ng - 1));
-      if (gb + ng - 1 > extra_cap) {
-        // no room: one group; mark the slots of this reservation that exist as unused
-        for (int g = 1; g < ng && gb + g - 1 < extra_cap; ++g) extra_owner[gb + g - 1] = -1;
-        ng = 1;
-      } else {
-        for (int g = 1; g < ng; ++g) {
-          extra_owner[gb + g - 1] = (int32_t)i;
-          extra_group[gb + g - 1] = g;
-        }
-      }
-    }
-    long_ngroups[i] = ng;
-    long_gbase[i] = gb;
-  }
+  if (!r.flags && r.hi - r.lo + 1 > kLongWindow)
+    list_long_window(r.hi - r.lo + 1, pos, bins + 2 * kNumBins, long_list, long_ngroups, long_gbase, extra_owner,
+                     extra_group, extra_cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,13 +586,14 @@ __device__ __forceinline__ xdd range_sum_comp(const DevPoly &P, double zr, doubl
   return xdd_norm(x);
 }
 
-template <bool CC, bool CZ, bool ACC, bool F32>
-__global__ void __launch_bounds__(128) k_sum_short(DevPoly P, int n, const PointRec *__restrict__ rec,
-                                                   fpe_xc64 *__restrict__ out, int32_t *nterms,
-                                                   int32_t *bits_lost) {
+template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
+__global__ void __launch_bounds__(128) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table, int n,
+                                                   const PointRec *__restrict__ rec, fpe_xc64 *__restrict__ out,
+                                                   int32_t *nterms, int32_t *bits_lost) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   PointRec r = rec[q];
+  const DevPoly &P = BATCH ? table[r.pid] : P0;
   fpe_xc64 o;
   if (r.flags) {
     o = special_value(P, r.flags);
@@ -641,21 +651,22 @@ __device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
   return g == 0 ? i : cap + gbase + g - 1;
 }
 
-template <bool CC, bool CZ, bool ACC, bool F32>
-__global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *__restrict__ rec,
+template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
+__global__ void __launch_bounds__(128) k_sum_groups(DevPoly P0, const DevPoly *__restrict__ table,
+                                                    const PointRec *__restrict__ rec,
                                                     const int32_t *__restrict__ long_list,
                                                     const int32_t *__restrict__ long_ngroups,
                                                     const int32_t *__restrict__ long_gbase,
                                                     const int32_t *__restrict__ extra_owner,
-                                                    const int32_t *__restrict__ extra_group, uint32_t *bins, int cap,
+                                                    const int32_t *__restrict__ extra_group, uint32_t *cnt, int cap,
                                                     int extra_cap, xdd *__restrict__ gval, xdd *__restrict__ gcarry) {
   const int lane = threadIdx.x & 31;
-  const uint32_t nlong = *(volatile uint32_t *)&bins[2 * kNumBins + kCntLong];
-  const uint32_t nextra = min(*(volatile uint32_t *)&bins[2 * kNumBins + kCntExtra], (uint32_t)extra_cap);
+  const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
+  const uint32_t nextra = min(*(volatile uint32_t *)&cnt[kCntExtra], (uint32_t)extra_cap);
   // every extra slot below min(reserved, extra_cap) is written by k_scatter: an owner, or -1
   while (true) {
     uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(&bins[2 * kNumBins + kCntGroupWork], 1u);
+    if (lane == 0) t = atomicAdd(&cnt[kCntGroupWork], 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= nlong + nextra) break;
     int i, g;
@@ -669,6 +680,7 @@ __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *_
     }
     const int ng = long_ngroups[i];
     const PointRec r = rec[long_list[i]];
+    const DevPoly &P = BATCH ? table[r.pid] : P0;
     const long long L = r.hi - r.lo + 1;
     const long long C = (L + 32LL * ng - 1) / (32LL * ng);
     const long long clo = r.lo + (long long)g * 32 * C + lane * C;
@@ -712,16 +724,19 @@ __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P, const PointRec *_
 
 // One thread per long-window point: sum_g (z^S)^g (val_g + carry_{g-1}) by
 // Horner from the top group, then times z^(l + v).
-__global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec *__restrict__ rec,
+template <bool BATCH>
+__global__ void __launch_bounds__(128) k_finalize_long(DevPoly P0, const DevPoly *__restrict__ table,
+                                                       const PointRec *__restrict__ rec,
                                                        const int32_t *__restrict__ long_list,
                                                        const int32_t *__restrict__ long_ngroups,
-                                                       const int32_t *__restrict__ long_gbase, uint32_t *bins,
+                                                       const int32_t *__restrict__ long_gbase, uint32_t *cnt,
                                                        int cap, const xdd *__restrict__ gval,
                                                        const xdd *__restrict__ gcarry, fpe_xc64 *__restrict__ out,
                                                        int32_t *nterms, int32_t *bits_lost) {
-  const uint32_t nlong = *(volatile uint32_t *)&bins[2 * kNumBins + kCntLong];
+  const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nlong; i += gridDim.x * blockDim.x) {
     const PointRec r = rec[long_list[i]];
+    const DevPoly &P = BATCH ? table[r.pid] : P0;
     const int ng = long_ngroups[i], gb = long_gbase[i];
     xdd acc = gval[group_slot(i, ng - 1, gb, cap)];
     if (ng > 1) {
@@ -764,19 +779,21 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
   const int cap = (int)w.cap, xcap = (int)w.extra_cap;
   {
     ProfScope ps("k_sum_short", st);
-    k_sum_short<CC, CZ, ACC, F32><<<(n + 127) / 128, 128, 0, st>>>(P->dev, n, w.rec, out, nterms, bits_lost);
+    k_sum_short<CC, CZ, ACC, F32, false>
+        <<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms, bits_lost);
   }
   {
     ProfScope ps("k_sum_groups", st);
-    k_sum_groups<CC, CZ, ACC, F32><<<num_sms() * 4, 128, 0, st>>>(
-        P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group, w.bins, cap, xcap,
-        (xdd *)w.group_val, (xdd *)w.group_carry);
+    k_sum_groups<CC, CZ, ACC, F32, false><<<num_sms() * 4, 128, 0, st>>>(
+        P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
+        w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
   }
   {
     ProfScope ps("k_finalize_long", st);
-    k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase,
-                                                   w.bins, cap, (const xdd *)w.group_val,
-                                                   (const xdd *)w.group_carry, out, nterms, bits_lost);
+    k_finalize_long<false><<<num_sms() * 2, 128, 0, st>>>(P->dev, nullptr, w.rec, w.long_list, w.long_ngroups,
+                                                          w.long_gbase, w.bins + 2 * kNumBins, cap,
+                                                          (const xdd *)w.group_val, (const xdd *)w.group_carry,
+                                                          out, nterms, bits_lost);
   }
 }
 
@@ -835,6 +852,170 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   P->last_n = n64;
+  return FPE_OK;
+}
+
+}  // namespace fpe
+
+namespace fpe {
+
+// ---------------------------------------------------------------------------
+// Batched evaluation: many polynomials, each at its own points, in one fixed
+// sequence of launches (§8.1: points are independent).  The polynomials'
+// descriptors live in a device table; every point carries its polynomial's
+// index.  Bucketing is a segmented counting sort: kBatchBins lambda bins per
+// polynomial, scanned per polynomial, so points stay inside their
+// polynomial's segment and a warp's lanes share one coefficient array.
+// ---------------------------------------------------------------------------
+template <bool CZ>
+__global__ void k_locate_batch(const DevPoly *__restrict__ table, const int32_t *__restrict__ pid, int n,
+                               const double *__restrict__ zre, const double *__restrict__ zim,
+                               long long *__restrict__ lo_out, long long *__restrict__ hi_out,
+                               long long *__restrict__ kl_out, double *__restrict__ N_out,
+                               uint32_t *__restrict__ key, uint32_t *__restrict__ hist) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int i = pid[p];
+  const DevPoly &P = table[i];
+  double zr = zre[p], zi = CZ ? zim[p] : 0.0;
+  Window w = locate_point<CZ>(P, zr, zi);
+  lo_out[p] = w.lo + (w.flags ? 0 : P.v);
+  hi_out[p] = w.hi + (w.flags ? 0 : P.v);
+  kl_out[p] = w.kl;
+  N_out[p] = w.flags ? 0.0 : w.N + w.lam * (double)P.v;
+  const uint32_t k = (uint32_t)i * kBatchBins + (bucket_of(w.lam, w.flags) * kBatchBins) / kNumBins;
+  key[p] = k;
+  atomicAdd(&hist[k], 1u);
+}
+
+// per polynomial: exclusive scan of its bins, starting at its first point; resets the counters
+__global__ void k_scan_batch(const int64_t *__restrict__ offsets, int npoly, const uint32_t *__restrict__ hist,
+                             uint32_t *__restrict__ cursor, uint32_t *__restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kNumCounters) cnt[i] = 0;
+  if (i >= npoly) return;
+  uint32_t run = (uint32_t)offsets[i];
+  for (int b = 0; b < kBatchBins; ++b) {
+    cursor[i * kBatchBins + b] = run;
+    run += hist[i * kBatchBins + b];
+  }
+}
+
+template <bool CZ>
+__global__ void k_scatter_batch(const DevPoly *__restrict__ table, const int32_t *__restrict__ pid, int n,
+                                const double *__restrict__ zre, const double *__restrict__ zim,
+                                const long long *__restrict__ lo, const long long *__restrict__ hi,
+                                const long long *__restrict__ kl, const double *__restrict__ N,
+                                const uint32_t *__restrict__ key, uint32_t *cursor, uint32_t *cnt,
+                                PointRec *__restrict__ rec, int32_t *__restrict__ long_list,
+                                int32_t *__restrict__ long_ngroups, int32_t *__restrict__ long_gbase,
+                                int32_t *__restrict__ extra_owner, int32_t *__restrict__ extra_group, int extra_cap,
+                                int32_t *status) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int i = pid[p];
+  const long long v = table[i].v;
+  uint32_t pos = atomicAdd(&cursor[key[p]], 1u);
+  PointRec r;
+  r.zr = zre[p];
+  r.zi = CZ ? zim[p] : 0.0;
+  r.flags = 0;
+  if (!isfinite(r.zr) || !isfinite(r.zi)) {
+    r.flags = kPointNonFinite;
+    atomicOr(status, kStatusNonFinite);
+  } else if (r.zr == 0.0 && r.zi == 0.0) {
+    r.flags = kPointZero;
+  }
+  r.lo = r.flags ? 1 : lo[p] - v;
+  r.hi = r.flags ? 0 : hi[p] - v;
+  r.kl = kl[p];
+  r.N = N[p];
+  r.orig = p;
+  r.pid = i;
+  r.pad = 0;
+  rec[pos] = r;
+  if (!r.flags && r.hi - r.lo + 1 > kLongWindow)
+    list_long_window(r.hi - r.lo + 1, pos, cnt, long_list, long_ngroups, long_gbase, extra_owner, extra_group,
+                     extra_cap);
+}
+
+template <bool CC, bool CZ, bool ACC, bool F32>
+static void launch_batch_sums(fpe_batch_s *B, fpe_xc64 *out, int32_t *nterms, cudaStream_t st) {
+  Workspace &w = B->ws;
+  const int n = (int)B->ntotal, cap = (int)w.cap, xcap = (int)w.extra_cap;
+  {
+    ProfScope ps("k_sum_short", st);
+    k_sum_short<CC, CZ, ACC, F32, true>
+        <<<(n + 127) / 128, 128, 0, st>>>(DevPoly{}, B->d_table, n, w.rec, out, nterms, nullptr);
+  }
+  {
+    ProfScope ps("k_sum_groups", st);
+    k_sum_groups<CC, CZ, ACC, F32, true><<<num_sms() * 4, 128, 0, st>>>(
+        DevPoly{}, B->d_table, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
+        B->d_cnt, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
+  }
+  {
+    ProfScope ps("k_finalize_long", st);
+    k_finalize_long<true><<<num_sms() * 2, 128, 0, st>>>(DevPoly{}, B->d_table, w.rec, w.long_list,
+                                                         w.long_ngroups, w.long_gbase, B->d_cnt, cap,
+                                                         (const xdd *)w.group_val, (const xdd *)w.group_carry, out,
+                                                         nterms, nullptr);
+  }
+}
+
+fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
+                        cudaStream_t st) {
+  if (B->ntotal == 0) return FPE_OK;
+  Workspace &w = B->ws;
+  const int n = (int)B->ntotal, nb = (n + 255) / 256;
+  const bool cz = z_im != nullptr;
+  cudaError_t e = cudaMemsetAsync(B->d_hist, 0, B->npoly * kBatchBins * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  {
+    ProfScope ps("k_locate_batch", st);
+    if (cz)
+      k_locate_batch<true><<<nb, 256, 0, st>>>(B->d_table, B->d_pid, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key,
+                                               B->d_hist);
+    else
+      k_locate_batch<false><<<nb, 256, 0, st>>>(B->d_table, B->d_pid, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key,
+                                                B->d_hist);
+  }
+  {
+    ProfScope ps("k_scan_batch", st);
+    const int np = (int)B->npoly;
+    k_scan_batch<<<(std::max(np, kNumCounters) + 127) / 128, 128, 0, st>>>(B->d_offsets, np, B->d_hist,
+                                                                           B->d_cursor, B->d_cnt);
+  }
+  {
+    ProfScope ps("k_scatter_batch", st);
+    if (cz)
+      k_scatter_batch<true><<<nb, 256, 0, st>>>(B->d_table, B->d_pid, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key,
+                                                B->d_cursor, B->d_cnt, w.rec, w.long_list, w.long_ngroups,
+                                                w.long_gbase, w.extra_owner, w.extra_group, (int)w.extra_cap,
+                                                B->d_status);
+    else
+      k_scatter_batch<false><<<nb, 256, 0, st>>>(B->d_table, B->d_pid, n, z_re, z_im, w.lo, w.hi, w.kl, w.N,
+                                                 w.key, B->d_cursor, B->d_cnt, w.rec, w.long_list, w.long_ngroups,
+                                                 w.long_gbase, w.extra_owner, w.extra_group, (int)w.extra_cap,
+                                                 B->d_status);
+  }
+  const bool cc = B->complex_coef;
+#define FPE_BATCH_SUMS(CCv, CZv)                                         \
+  do {                                                                   \
+    if (B->fp32)                                                         \
+      launch_batch_sums<CCv, CZv, false, true>(B, out, nterms, st);      \
+    else if (B->accurate)                                                \
+      launch_batch_sums<CCv, CZv, true, false>(B, out, nterms, st);      \
+    else                                                                 \
+      launch_batch_sums<CCv, CZv, false, false>(B, out, nterms, st);     \
+  } while (0)
+  if (cc && cz) FPE_BATCH_SUMS(true, true);
+  else if (cc) FPE_BATCH_SUMS(true, false);
+  else if (cz) FPE_BATCH_SUMS(false, true);
+  else FPE_BATCH_SUMS(false, false);
+#undef FPE_BATCH_SUMS
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return FPE_OK;
 }
 
@@ -964,16 +1145,16 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
                                              w.extra_group, (int)w.extra_cap, P->d_status);
       const int cap = (int)w.cap, xcap = (int)w.extra_cap;
       const bool acc = P->dev.accurate != 0;
-#define FPE_NOALLOC_SUMS(CCv, CZv, ACCv, F32v)                                                                       \
+#define FPE_NOALLOC_SUMS(CCv, CZv, ACCv, F32v)                                                                 \
   do {                                                                                                         \
-    k_sum_short<CCv, CZv, ACCv, F32v><<<(ni + 127) / 128, 128, 0, st>>>(P->dev, ni, w.rec, out, nterms,       \
-                                                                        bits_lost);                           \
-    k_sum_groups<CCv, CZv, ACCv, F32v><<<num_sms() * 4, 128, 0, st>>>(                                        \
-        P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group, w.bins, cap,   \
-        xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                                                       \
-    k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase,   \
-                                                   w.bins, cap, (const xdd *)w.group_val,                      \
-                                                   (const xdd *)w.group_carry, out, nterms, bits_lost);        \
+    k_sum_short<CCv, CZv, ACCv, F32v, false>                                                                   \
+        <<<(ni + 127) / 128, 128, 0, st>>>(P->dev, nullptr, ni, w.rec, out, nterms, bits_lost);                \
+    k_sum_groups<CCv, CZv, ACCv, F32v, false><<<num_sms() * 4, 128, 0, st>>>(                                 \
+        P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,       \
+        w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                          \
+    k_finalize_long<false><<<num_sms() * 2, 128, 0, st>>>(                                                     \
+        P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.bins + 2 * kNumBins, cap,         \
+        (const xdd *)w.group_val, (const xdd *)w.group_carry, out, nterms, bits_lost);                         \
   } while (0)
       const bool f32 = P->dev.fp32 != 0;
       if (cc && cz) {

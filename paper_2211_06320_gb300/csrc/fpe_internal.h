@@ -34,6 +34,9 @@ constexpr int64_t kLongWindow = 4096;
 constexpr int64_t kMaxLaneChunk = 1024;
 constexpr int64_t kGroupSpan = 32 * kMaxLaneChunk;
 
+// Batched evaluation: lambda bins per polynomial (segmented bucketing).
+constexpr int kBatchBins = 32;
+
 // Counters after the 2 * kNumBins histogram words.
 constexpr int kCntLong = 0;        // long-window points listed
 constexpr int kCntGroupWork = 1;   // group work cursor
@@ -77,6 +80,8 @@ struct PointRec {
   double N;          // max of cover(k) + lambda k, untrimmed (eq. defN)
   int32_t orig;      // index in the caller's order
   int32_t flags;     // kPointZero, kPointNonFinite
+  int32_t pid;       // polynomial of the point (batched evaluation; 0 otherwise)
+  int32_t pad;
 };
 constexpr int32_t kPointZero = 1;
 constexpr int32_t kPointNonFinite = 2;
@@ -128,8 +133,25 @@ struct fpe_poly_s {
   int64_t last_n = 0;                   // points of the last fpe_eval
 };
 
+struct fpe_batch_s {
+  int device = 0;
+  int64_t npoly = 0, ntotal = 0;
+  bool complex_coef = false, fp32 = false, accurate = false;
+  std::vector<fpe_poly_s *> polys;      // not owned
+  std::vector<int64_t> offsets;         // npoly + 1 point offsets
+  fpe::DevPoly *d_table = nullptr;      // npoly descriptors
+  int32_t *d_pid = nullptr;             // per point: polynomial index
+  int64_t *d_offsets = nullptr;
+  uint32_t *d_hist = nullptr, *d_cursor = nullptr;  // npoly * kBatchBins each
+  uint32_t *d_cnt = nullptr;            // kNumCounters
+  int32_t *d_status = nullptr;
+  fpe::Workspace ws;                    // sized for ntotal points
+};
+
 namespace fpe {
 // precondition.cpp
+fpe_status alloc_workspace(Workspace &w, int64_t n);
+void free_workspace(Workspace &w);
 fpe_status precondition_host(const double *re, const double *im, const int64_t *e2, int64_t n_coef, int p,
                              uint32_t flags, fpe_poly_s **out);
 void set_error(const std::string &msg);
@@ -140,6 +162,8 @@ fpe_status ensure_workspace(fpe_poly_s *P, int64_t n);
 // fpe_eval.cu
 fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                        int32_t *nterms, int32_t *bits_lost, cudaStream_t st);
+fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
+                        cudaStream_t st);
 // fpe_horner.cu
 fpe_status launch_horner(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                          int compensated, cudaStream_t st);

@@ -135,26 +135,25 @@ void free_handle(fpe_poly_s *P) {
   cudaGetDevice(&prev);
   cudaSetDevice(P->device);
   for (void *a : P->allocs) cudaFree(a);
-  Workspace &w = P->ws;
-  void *ws_ptrs[] = {w.lo,          w.hi,          w.kl,          w.N,          w.key,
-                     w.rec,         w.long_list,   w.long_ngroups, w.long_gbase, w.extra_owner,
-                     w.extra_group, w.group_val,   w.group_carry, w.bins,       w.dev_io};
-  for (void *a : ws_ptrs)
-    if (a) cudaFree(a);
-  if (w.host_pinned) cudaFreeHost(w.host_pinned);
+  free_workspace(P->ws);
   if (P->d_status) cudaFree(P->d_status);
   cudaSetDevice(prev);
   if (P->deriv) free_handle(P->deriv);
   delete P;
 }
 
-fpe_status ensure_workspace(fpe_poly_s *P, int64_t n) {
-  Workspace &w = P->ws;
-  if (w.bins == nullptr) {
-    cudaError_t e = cudaMalloc((void **)&w.bins, (2 * kNumBins + kNumCounters) * sizeof(uint32_t));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bins)");
-  }
-  if (n <= w.cap) return FPE_OK;
+void free_workspace(Workspace &w) {
+  void *ptrs[] = {w.lo,          w.hi,          w.kl,           w.N,          w.key,
+                  w.rec,         w.long_list,   w.long_ngroups, w.long_gbase, w.extra_owner,
+                  w.extra_group, w.group_val,   w.group_carry,  w.bins,       w.dev_io};
+  for (void *a : ptrs)
+    if (a) cudaFree(a);
+  if (w.host_pinned) cudaFreeHost(w.host_pinned);
+  w = Workspace();
+}
+
+// per-point scratch for n points (the bins are allocated separately)
+fpe_status alloc_workspace(Workspace &w, int64_t n) {
   const int64_t cap = std::max<int64_t>(n, 1024);
   const int64_t xcap = cap + 1024;  // extra group slots for very long windows
   void **slots[] = {(void **)&w.lo,          (void **)&w.hi,          (void **)&w.kl,
@@ -181,6 +180,16 @@ fpe_status ensure_workspace(fpe_poly_s *P, int64_t n) {
   w.cap = cap;
   w.extra_cap = xcap;
   return FPE_OK;
+}
+
+fpe_status ensure_workspace(fpe_poly_s *P, int64_t n) {
+  Workspace &w = P->ws;
+  if (w.bins == nullptr) {
+    cudaError_t e = cudaMalloc((void **)&w.bins, (2 * kNumBins + kNumCounters) * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bins)");
+  }
+  if (n <= w.cap) return FPE_OK;
+  return alloc_workspace(w, n);
 }
 
 // ---------------------------------------------------------------------------
