@@ -166,6 +166,40 @@ def batched_leg(F, torch, st):
     return res
 
 
+def differentiation_leg(F, torch, st):
+    """d = 2^18 unit-disk coefficients (+1e-3 noise), 2^20 sphere points: forward
+    P, P', one Newton step, and the backward kernels (dL/dz, dL/da_k)."""
+    import workloads as W
+    wl, _, _ = W.differentiation_d2pow18()
+    n = wl.points.n
+    P = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, None, 53, F.FPE_WITH_DERIV)
+    zr = torch.from_numpy(wl.points.re).cuda()
+    zi = torch.from_numpy(wl.points.im).cuda()
+    g = torch.ones(n, dtype=torch.float64, device="cuda")
+    ga_re = torch.zeros(wl.coeffs.n_coef, dtype=torch.float64, device="cuda")
+    ga_im = torch.zeros_like(ga_re)
+    out = F.empty_out(n)
+    steps = {
+        "forward_P": lambda: F.fpe_eval(P, zr, zi, out),
+        "derivative_P1": lambda: F.fpe_eval_deriv(P, zr, zi, out),
+        "newton_step": lambda: F.fpe_newton(P, zr, zi, out),
+        "grad_points": lambda: F.fpe_grad_points(P, zr, zi, g, g),
+        "grad_coeffs": lambda: F.fpe_grad_coeffs(P, zr, zi, g, g, ga_re, ga_im),
+    }
+    res = {"degree": wl.coeffs.n_coef - 1, "points": n}
+    for name, fn in steps.items():
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        res[f"{name}_evals_per_s"] = n / (a.elapsed_time(b) * 1e-3)
+    F.fpe_sync(P)
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -357,6 +391,7 @@ def main():
             extras["fpe_fp32_p24_avg_kept_terms"] = float(nt32.double().mean().item())
             extras["cpu_baseline"] = oracle_cpu_baseline(wl, 4096)
             extras["batched"] = batched_leg(F, torch, st)
+            extras["differentiation"] = differentiation_leg(F, torch, st)
 
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,

@@ -210,6 +210,44 @@ fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_
                           const double *z_im, fpe_xc64 *out, void *cuda_stream);
 
 /*
+ * fpe_newton -- one Newton step N_P(z) = z - P(z)/P'(z) (§7.2, eq. newton) at n
+ * points.  P(z) and P'(z) are evaluated by the FPE path as extended-exponent
+ * values, so the increment P/P' never overflows where P and P' do (the
+ * paper's cancellation of the valuation monomial z^m, m = min(l, l'), gives
+ * the same protection).  Requires FPE_WITH_DERIV.
+ *   inc         device fpe_xc64[n]: P(z)/P'(z) (0 where P(z) = 0; NaN where only P' vanishes).
+ *   z_next_re/im device double[n] or NULL: z - inc as FP64 (inf where inc overflows FP64).
+ * Asynchronous; the first call allocates scratch on the handle.
+ */
+fpe_status fpe_newton(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *inc,
+                      double *z_next_re, double *z_next_im, void *cuda_stream);
+
+/*
+ * fpe_grad_points -- the gradient with respect to the points of a real loss L
+ * of the values P(z_j): dL/dz_j = g_j conj(P'(z_j)) with g_j = dL/dP(z_j) (the
+ * conjugate Wirtinger convention; P is holomorphic in z).  P' is evaluated by
+ * the FPE path (§7.2).  Requires FPE_WITH_DERIV.  g_re/g_im (g_im NULL = real)
+ * and gz_re/gz_im (gz_im may be NULL) are device double[n].  Asynchronous.
+ */
+fpe_status fpe_grad_points(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, const double *g_re,
+                           const double *g_im, double *gz_re, double *gz_im, void *cuda_stream);
+
+/*
+ * fpe_grad_coeffs -- ADDS to ga the gradient with respect to the coefficients:
+ * dL/da_k += sum_j g_j conj(z_j)^k over the terms the evaluation kept,
+ * k in G_p cap [l_j, r_j] (eq. reducedQlambda): the FPE value at z_j depends on
+ * no other coefficient.  ga_re/ga_im are device double[n_coef] (untrimmed
+ * index; ga_im may be NULL for a real polynomial).  Atomic accumulation:
+ * the summation order, hence the last bits, vary between runs.  Asynchronous.
+ */
+fpe_status fpe_grad_coeffs(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, const double *g_re,
+                           const double *g_im, double *ga_re, double *ga_im, void *cuda_stream);
+
+/* fpe_to_complex -- (re, im) 2^e of n device fpe_xc64 values as device FP64
+ * (inf or 0 where the value leaves the FP64 range); im may be NULL.  Async. */
+fpe_status fpe_to_complex(const fpe_xc64 *v, int64_t n, double *re, double *im, void *cuda_stream);
+
+/*
  * fpe_horner -- the plain form beside FPE: Horner's scheme over all d+1
  * coefficients (§1, "Horner's scheme") on the GPU, with exact power-of-two
  * renormalisation so that no intermediate overflows.

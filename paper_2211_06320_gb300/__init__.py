@@ -38,7 +38,7 @@ EXPORTED = [
     "fpe_info", "fpe_get_hull", "fpe_get_good", "fpe_get_windows", "fpe_sync", "fpe_destroy",
     "fpe_status_string", "fpe_last_error", "fpe_profile_enable", "fpe_profile_reset", "fpe_profile_read",
     "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
-    "fpe_batch_destroy",
+    "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex",
 ]
 
 
@@ -90,6 +90,10 @@ def _load():
         "fpe_batch_eval": ([P, P, P, P, P, P], I32),
         "fpe_batch_sync": ([P, P], I32),
         "fpe_batch_destroy": ([P], None),
+        "fpe_newton": ([P, P, P, I64, P, P, P, P], I32),
+        "fpe_grad_points": ([P, P, P, I64, P, P, P, P, P], I32),
+        "fpe_grad_coeffs": ([P, P, P, I64, P, P, P, P, P], I32),
+        "fpe_to_complex": ([P, I64, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -360,3 +364,50 @@ def fpe_batch_eval(B: Batch, z_re, z_im=None, out=None, nterms=None, stream=None
 
 def fpe_batch_sync(B: Batch, stream=None):
     _check(_load().fpe_batch_sync(B._h, _stream(stream)), "fpe_batch_sync")
+
+
+def fpe_newton(P: Poly, z_re, z_im=None, inc=None, z_next_re=None, z_next_im=None, stream=None):
+    """One Newton step: returns (inc as (n, 3) fpe_xc64, z_next_re, z_next_im)."""
+    import torch
+    lib = _load()
+    n = int(z_re.shape[0])
+    if inc is None:
+        inc = empty_out(n, z_re.device)
+    if z_next_re is None:
+        z_next_re = torch.empty_like(z_re)
+    if z_next_im is None and z_im is not None:
+        z_next_im = torch.empty_like(z_im)
+    _check(lib.fpe_newton(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(inc), _dptr(z_next_re), _dptr(z_next_im),
+                          _stream(stream)), "fpe_newton")
+    return inc, z_next_re, z_next_im
+
+
+def fpe_grad_points(P: Poly, z_re, z_im, g_re, g_im, stream=None):
+    import torch
+    lib = _load()
+    n = int(z_re.shape[0])
+    gz_re = torch.empty_like(z_re)
+    gz_im = torch.empty_like(z_re)
+    _check(lib.fpe_grad_points(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(g_re), _dptr(g_im), _dptr(gz_re),
+                               _dptr(gz_im), _stream(stream)), "fpe_grad_points")
+    return gz_re, gz_im
+
+
+def fpe_grad_coeffs(P: Poly, z_re, z_im, g_re, g_im, ga_re, ga_im=None, stream=None):
+    """Adds dL/da_k into ga_re/ga_im (device float64, n_coef entries)."""
+    lib = _load()
+    n = int(z_re.shape[0])
+    _check(lib.fpe_grad_coeffs(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(g_re), _dptr(g_im), _dptr(ga_re),
+                               _dptr(ga_im), _stream(stream)), "fpe_grad_coeffs")
+    return ga_re, ga_im
+
+
+def fpe_to_complex(v, stream=None):
+    """(re, im) 2^e of an (n, 3) fpe_xc64 tensor as two float64 tensors."""
+    import torch
+    lib = _load()
+    n = int(v.shape[0])
+    re = torch.empty(n, dtype=torch.float64, device=v.device)
+    im = torch.empty(n, dtype=torch.float64, device=v.device)
+    _check(lib.fpe_to_complex(_dptr(v), n, _dptr(re), _dptr(im), _stream(stream)), "fpe_to_complex")
+    return re, im

@@ -267,6 +267,50 @@ fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_
   return s;
 }
 
+fpe_status fpe_newton(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *inc,
+                      double *z_next_re, double *z_next_im, void *cuda_stream) {
+  fpe_status s = check_eval_args(P, z_re, n, inc);
+  if (s != FPE_OK) return s;
+  if (!(P->flags & FPE_WITH_DERIV)) {
+    set_error("fpe_newton: handle was preconditioned without FPE_WITH_DERIV");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  return launch_newton(P, z_re, z_im, n, inc, z_next_re, z_next_im, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_grad_points(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, const double *g_re,
+                           const double *g_im, double *gz_re, double *gz_im, void *cuda_stream) {
+  fpe_status s = check_eval_args(P, z_re, n, gz_re);
+  if (s != FPE_OK) return s;
+  if (!(P->flags & FPE_WITH_DERIV) || (n > 0 && !g_re)) {
+    set_error("fpe_grad_points: needs FPE_WITH_DERIV and a non-NULL g_re");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  return launch_grad_points(P, z_re, z_im, n, g_re, g_im, gz_re, gz_im, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_grad_coeffs(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, const double *g_re,
+                           const double *g_im, double *ga_re, double *ga_im, void *cuda_stream) {
+  fpe_status s = check_eval_args(P, z_re, n, ga_re);
+  if (s != FPE_OK) return s;
+  if (n > 0 && !g_re) {
+    set_error("fpe_grad_coeffs: g_re is NULL");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  return launch_grad_coeffs(P, z_re, z_im, n, g_re, g_im, ga_re, ga_im, (cudaStream_t)cuda_stream);
+}
+
+fpe_status fpe_to_complex(const fpe_xc64 *v, int64_t n, double *re, double *im, void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!v || !re))) {
+    set_error("fpe_to_complex: bad arguments");
+    return FPE_ERR_INVALID_ARG;
+  }
+  return launch_to_complex(v, n, re, im, (cudaStream_t)cuda_stream);
+}
+
 fpe_status fpe_horner(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                       int compensated, void *cuda_stream) {
   fpe_status s = check_eval_args(P, z_re, n, out);

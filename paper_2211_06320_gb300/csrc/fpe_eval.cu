@@ -807,15 +807,13 @@ static void launch_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, in
     launch_sums4<CC, CZ, false, false>(P, n, out, nterms, bits_lost, st);
 }
 
-fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, fpe_xc64 *out,
-                       int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
-  if (n64 == 0) return FPE_OK;
+// locate, bucket and scatter the points into P->ws.rec (the front of fpe_eval)
+fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, cudaStream_t st) {
   fpe_status s = ensure_workspace(P, n64);
   if (s != FPE_OK) return s;
   const int n = (int)n64;
   Workspace &w = P->ws;
   const bool cz = z_im != nullptr;
-  const bool cc = P->complex_coef;
   cudaError_t e = cudaMemsetAsync(w.bins, 0, kNumBins * sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   const int nb = (n + 255) / 256;
@@ -841,6 +839,19 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
                                            w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                            w.extra_group, (int)w.extra_cap, P->d_status);
   }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return FPE_OK;
+}
+
+fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, fpe_xc64 *out,
+                       int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
+  if (n64 == 0) return FPE_OK;
+  fpe_status s = launch_front(P, z_re, z_im, n64, st);
+  if (s != FPE_OK) return s;
+  const int n = (int)n64;
+  const bool cz = z_im != nullptr;
+  const bool cc = P->complex_coef;
   if (cc && cz)
     launch_sums<true, true>(P, n, out, nterms, bits_lost, st);
   else if (cc)
@@ -849,7 +860,7 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
     launch_sums<false, true>(P, n, out, nterms, bits_lost, st);
   else
     launch_sums<false, false>(P, n, out, nterms, bits_lost, st);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   P->last_n = n64;
   return FPE_OK;

@@ -131,6 +131,8 @@ struct fpe_poly_s {
   fpe_poly_s *deriv = nullptr;          // P' (FPE_WITH_DERIV), nullptr if P' = 0
   bool deriv_zero = false;
   int64_t last_n = 0;                   // points of the last fpe_eval
+  void *aux = nullptr;                  // scratch of fpe_newton / fpe_grad_points (grown on demand)
+  size_t aux_bytes = 0;
 };
 
 struct fpe_batch_s {
@@ -160,10 +162,21 @@ void free_handle(fpe_poly_s *P);
 fpe_status ensure_workspace(fpe_poly_s *P, int64_t n);
 
 // fpe_eval.cu
+fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, cudaStream_t st);
 fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                        int32_t *nterms, int32_t *bits_lost, cudaStream_t st);
 fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
                         cudaStream_t st);
+// fpe_grad.cu
+fpe_status launch_newton(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *inc,
+                         double *znr, double *zni, cudaStream_t st);
+fpe_status launch_grad_points(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n,
+                              const double *g_re, const double *g_im, double *gz_re, double *gz_im,
+                              cudaStream_t st);
+fpe_status launch_grad_coeffs(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n,
+                              const double *g_re, const double *g_im, double *ga_re, double *ga_im,
+                              cudaStream_t st);
+fpe_status launch_to_complex(const fpe_xc64 *v, int64_t n, double *re, double *im, cudaStream_t st);
 // fpe_horner.cu
 fpe_status launch_horner(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                          int compensated, cudaStream_t st);

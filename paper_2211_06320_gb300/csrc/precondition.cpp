@@ -136,6 +136,7 @@ void free_handle(fpe_poly_s *P) {
   cudaSetDevice(P->device);
   for (void *a : P->allocs) cudaFree(a);
   free_workspace(P->ws);
+  if (P->aux) cudaFree(P->aux);
   if (P->d_status) cudaFree(P->d_status);
   cudaSetDevice(prev);
   if (P->deriv) free_handle(P->deriv);
