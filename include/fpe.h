@@ -276,6 +276,17 @@ fpe_status fpe_get_good(fpe_poly_t P, uint8_t *mask, int64_t n_coef);
  * device arrays of n entries in the caller's point order.  Asynchronous. */
 fpe_status fpe_get_windows(fpe_poly_t P, int64_t n, int64_t *l, int64_t *r, double *N, void *cuda_stream);
 
+/*
+ * fpe_analyse -- the |z|-ranges on which each coefficient is used (the
+ * -analyse task of §8.1): a good coefficient k is kept, k in [l, r] (def. LRN),
+ * exactly when lam_lo[k] <= log2|z| <= lam_hi[k] (the set is an interval
+ * because cover(k) + lambda k - N(lambda) is concave in lambda; the ends are
+ * +-inf when unbounded).  Bad coefficients (not in G_p) get NaN.  Host arrays
+ * of n_coef doubles, untrimmed indices; FP64 endpoints (ties at an endpoint
+ * may go either way, as in fpe_eval).  Works on FPE_HOST_ONLY handles.
+ */
+fpe_status fpe_analyse(fpe_poly_t P, double *lam_lo, double *lam_hi, int64_t n_coef);
+
 /* fpe_sync -- wait for the stream and return the first device-side status
  * recorded on the handle since the last fpe_sync (then clear it). */
 fpe_status fpe_sync(fpe_poly_t P, void *cuda_stream);

@@ -38,7 +38,7 @@ EXPORTED = [
     "fpe_info", "fpe_get_hull", "fpe_get_good", "fpe_get_windows", "fpe_sync", "fpe_destroy",
     "fpe_status_string", "fpe_last_error", "fpe_profile_enable", "fpe_profile_reset", "fpe_profile_read",
     "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
-    "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex",
+    "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex", "fpe_analyse",
 ]
 
 
@@ -94,6 +94,7 @@ def _load():
         "fpe_grad_points": ([P, P, P, I64, P, P, P, P, P], I32),
         "fpe_grad_coeffs": ([P, P, P, I64, P, P, P, P, P], I32),
         "fpe_to_complex": ([P, I64, P, P, P], I32),
+        "fpe_analyse": ([P, P, P, I64], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -411,3 +412,12 @@ def fpe_to_complex(v, stream=None):
     im = torch.empty(n, dtype=torch.float64, device=v.device)
     _check(lib.fpe_to_complex(_dptr(v), n, _dptr(re), _dptr(im), _stream(stream)), "fpe_to_complex")
     return re, im
+
+
+def fpe_analyse(P: Poly):
+    """Per coefficient, the log2|z| interval [lam_lo, lam_hi] where it is kept (NaN if never)."""
+    lib = _load()
+    lo = np.zeros(P.n_coef)
+    hi = np.zeros(P.n_coef)
+    _check(lib.fpe_analyse(P.handle, _np_ptr(lo), _np_ptr(hi), P.n_coef), "fpe_analyse")
+    return lo, hi

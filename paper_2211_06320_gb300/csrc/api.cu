@@ -2,6 +2,7 @@
 // host-buffer staging, and kernel timing.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -363,6 +364,39 @@ fpe_status fpe_get_windows(fpe_poly_t P, int64_t n, int64_t *l, int64_t *r, doub
   if (r && e == cudaSuccess) e = cudaMemcpyAsync(r, P->ws.hi, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
   if (N && e == cudaSuccess) e = cudaMemcpyAsync(N, P->ws.N, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "cudaMemcpyAsync");
+}
+
+fpe_status fpe_analyse(fpe_poly_t P, double *lam_lo, double *lam_hi, int64_t n_coef) {
+  if (!P || !lam_lo || !lam_hi || n_coef != P->n_coef) {
+    set_error("fpe_analyse: bad arguments");
+    return FPE_ERR_INVALID_ARG;
+  }
+  const std::vector<int64_t> &hk = P->hull_k, &hs = P->hull_s;
+  const int nh = (int)hk.size();
+  const double T = (double)P->T;
+  const double nan = std::nan("");
+  // cover(k) + lambda k >= max_i (s_i + lambda k_i) - T  <=>  for every vertex i:
+  //   lambda (k - k_i) >= s_i - cover(k) - T
+  for (int64_t k = 0; k < n_coef; ++k) {
+    if (!P->good[k]) {
+      lam_lo[k] = lam_hi[k] = nan;
+      continue;
+    }
+    // cover(k) exactly as a rational on its segment, evaluated in FP64
+    int seg = 0;
+    while (seg + 1 < nh - 1 && hk[seg + 1] <= k) ++seg;
+    double cov = (double)hs[seg];
+    if (nh > 1 && k != hk[seg])
+      cov = (double)hs[seg] + (double)(hs[seg + 1] - hs[seg]) * (double)(k - hk[seg]) / (double)(hk[seg + 1] - hk[seg]);
+    double lo = -INFINITY, hi = INFINITY;
+    for (int i = 0; i < nh; ++i) {
+      if (hk[i] < k) lo = fmax(lo, ((double)hs[i] - cov - T) / (double)(k - hk[i]));
+      else if (hk[i] > k) hi = fmin(hi, (cov + T - (double)hs[i]) / (double)(hk[i] - k));
+    }
+    lam_lo[k] = lo;
+    lam_hi[k] = hi;
+  }
+  return FPE_OK;
 }
 
 fpe_status fpe_sync(fpe_poly_t P, void *cuda_stream) {

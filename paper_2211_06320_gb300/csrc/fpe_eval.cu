@@ -627,6 +627,15 @@ __device__ __forceinline__ xdd shfl_down_xdd(xdd x, int s) {
   y.e = __shfl_down_sync(0xffffffffu, x.e, s);
   return y;
 }
+__device__ __forceinline__ xdd shfl_xor_xdd(xdd x, int s) {
+  xdd y;
+  y.rh = __shfl_xor_sync(0xffffffffu, x.rh, s);
+  y.rl = __shfl_xor_sync(0xffffffffu, x.rl, s);
+  y.ih = __shfl_xor_sync(0xffffffffu, x.ih, s);
+  y.il = __shfl_xor_sync(0xffffffffu, x.il, s);
+  y.e = __shfl_xor_sync(0xffffffffu, x.e, s);
+  return y;
+}
 __device__ __forceinline__ xdd shfl_up_xdd(xdd x, int s) {
   xdd y;
   y.rh = __shfl_up_sync(0xffffffffu, x.rh, s);
@@ -644,8 +653,9 @@ __device__ __forceinline__ xdd shfl_up_xdd(xdd x, int s) {
 //   chunk above the peak:     s_i = sum a_k z^(k - c_i) (top-down);
 //   chunk below the peak:     its sum z^(c_{i+1} - 1) R goes to slot i+1 as R / z;
 //   chunk holding the peak:   both parts, times z^(base - c_i).
-// A group's value is combined by a shuffle tree with w, w^2, w^4, ... (w = z^C);
-// lane 31's carry goes to the next group.  k_finalize_long combines the groups
+// A group's value is sum_i (z^C)^i s_i: each lane multiplies its slot by its
+// own power, then a butterfly adds the slots; lane 31's carry goes to the
+// next group.  k_finalize_long combines the groups
 // and applies z^(l + v), one point per thread.
 __device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
   return g == 0 ? i : cap + gbase + g - 1;
@@ -708,12 +718,10 @@ __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P0, const DevPoly *_
       if (lane > 0) sv = xdd_add(sv, inc);
       gout = shfl_down_xdd(carry, 31);  // lane 31's carry, read by lane 0
     }
-    xdd w = xdd_pow_int(r.zr, r.zi, C);
-    for (int s = 1; s < 32; s <<= 1) {
-      xdd other = shfl_down_xdd(sv, s);
-      if ((lane & (2 * s - 1)) == 0) sv = xdd_add(sv, xdd_mul(w, other));
-      if (s < 16) w = xdd_sqr(w);
-    }
+    // sum_i (z^C)^i s_i: each lane scales its slot by its own power (integer
+    // pipe), then a butterfly adds the 32 slots with every lane busy
+    if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
+    for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
     if (lane == 0) {
       const int slot = group_slot(i, g, long_gbase[i], cap);
       gval[slot] = sv;

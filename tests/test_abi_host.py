@@ -141,3 +141,30 @@ def test_derivative_handle_host(F):
     c = W.unit_square_complex(200, np.random.default_rng(9))
     P = F.fpe_precondition(c.re, c.im, None, 53, F.FPE_HOST_ONLY | F.FPE_WITH_DERIV)
     assert F.fpe_info(P)["d"] == 200
+
+
+@pytest.mark.parametrize("family", ["half_circle", "lognormal", "worked"])
+def test_analyse_intervals_match_oracle_windows(F, family):
+    """fpe_analyse: coefficient k is kept at lambda exactly when
+    lam_lo[k] <= lambda <= lam_hi[k]; checked against the oracle's windows on a
+    grid of lambda (away from the endpoints, where FP64 ties may differ)."""
+    rng = np.random.default_rng(3)
+    if family == "half_circle":
+        coef = W.half_circle(300)
+    elif family == "lognormal":
+        coef = W.lognormal_profile(400, 0.02, rng)
+    else:
+        coef = W.worked_example_coeffs(rng)
+    p = 12
+    P = F.fpe_precondition(coef.re, coef.im, coef.e2, p, F.FPE_HOST_ONLY)
+    lo, hi = F.fpe_analyse(P)
+    pre = oracle.precondition(coef, p)
+    lam = np.linspace(-40, 40, 801) + 0.0137
+    kl, N, L, R = oracle.windows(pre.hk, pre.hs, pre.T, lam)
+    k = np.arange(coef.n_coef)
+    for i, lm in enumerate(lam):
+        kept = (k >= L[i]) & (k <= R[i]) & pre.good.astype(bool)
+        pred = (lo <= lm) & (lm <= hi)
+        clear = np.isnan(lo) | ((np.abs(lm - lo) > 1e-9) & (np.abs(lm - hi) > 1e-9))
+        assert np.array_equal(kept[clear], pred[clear]), (family, lm)
+    assert np.all(np.isnan(lo) == ~pre.good.astype(bool))

@@ -410,3 +410,36 @@ def test_fp32_flags(env):
     with pytest.raises(F.FpeError) as e:
         F.fpe_precondition(c.re, c.im, None, 53, F.FPE_FP32)
     assert e.value.status == F.FPE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["unit_square_d1000", "inverse_factorial"])
+def test_bits_lost_diagnostic(env, name):
+    """bits_lost = max(0, ceil(N) - e) estimates the leading bits cancelled in
+    the computed value (the confidence estimator of §4.1; the remark on
+    cancellations in §2.5).  Where the cancellation c = log2(max_k |a_k z^k|)
+    - log2|P(z)| is moderate the output carries |P| to a few bits, so
+    bits_lost is within 2 of c (N within 1 of the largest term's log2, e
+    within 1 of log2|P|).  Past about 50 bits the FP64 output sits at the
+    error floor 2^-50 sum |a_k z^k|, so bits_lost saturates near 50 minus
+    log2 of the window length, and only its lower bound is checked."""
+    torch, F = env
+    if name == "unit_square_d1000":
+        wl = W.unit_square_d1000(n_points=2000)
+    else:
+        wl = W.inverse_factorial_d1e5(n_points=2000, d=3000)
+    P, out, nt, l, r, N = run_gpu(env, wl.coeffs, wl.points.re, wl.points.im)
+    zr = torch.from_numpy(wl.points.re).cuda()
+    zi = None if wl.points.im is None else torch.from_numpy(wl.points.im).cuda()
+    bl = torch.empty(wl.points.n, dtype=torch.int32, device="cuda")
+    F.fpe_eval(P, zr, zi, bits_lost=bl)
+    F.fpe_sync(P)
+    bl = bl.cpu().numpy()
+    ref, S, l2M = oracle.horner_ref(wl.coeffs, wl.points.re, wl.points.im)
+    mag = np.hypot(ref.re_hi + ref.re_lo, ref.im_hi + ref.im_lo)
+    l2P = np.log2(mag) + ref.e
+    want = np.maximum(0.0, l2M - l2P)
+    floor_bits = 50 - np.log2(np.maximum(nt, 1))
+    moderate = want <= floor_bits - 6
+    assert np.all(np.abs(bl[moderate] - want[moderate]) <= 2.0)
+    assert np.all(bl[~moderate] >= floor_bits[~moderate] - 8)
+        assert bl.max() > 50  # e^x at x ~ -50 cancels ~144 bits in the sum
