@@ -72,8 +72,10 @@ enum {
   FPE_HOST_ONLY = 8,   /* host analysis only (scales, cover, G_p; the -analyse
                           task of §8.1): no device memory is touched and the
                           handle cannot be evaluated                           */
-  FPE_ACCURATE = 16    /* compensated window sums: error <= u|P| + gamma^2 S
-                          for every input, at ~10x the FP64 work (see fpe_eval) */
+  FPE_ACCURATE = 16    /* window sums on the integer pipe in 128-bit fixed
+                          point: error <= u|P| + (2^-84 + L 2^-100) S for
+                          every input (L = window length), at ~1.7x the time
+                          of the default summation (see fpe_eval)              */
 };
 
 /*
@@ -122,9 +124,12 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
  * keeps |P_gpu - P| within 2^-50 sum |a_k||z|^k for coefficients of random
  * phase; long runs of aligned terms (e.g. all a_k = 1 near z = 1) or of
  * negligible terms after a dominant one can exceed it by a small factor.
- * With FPE_ACCURATE the window is summed by compensated Horner (error-free
- * transformations), which bounds the error by u|P| + gamma_2n^2 S for every
- * input.
+ * With FPE_ACCURATE the window is summed top-down by Horner's scheme on
+ * the integer pipe: the partial sum is a complex 128-bit fixed-point value
+ * with a 64-bit exponent, the point is used exactly, and each step truncates
+ * at 2^-104 or less of the partial sum, so the error is at most
+ * u|P| + (2^-84 + L 2^-100) S for every input (u|P| from rounding the
+ * output to FP64, 2^-84 S from the power z^l).
  * Asynchronous on cuda_stream.  The first call (and any call with a larger n
  * than before) allocates scratch memory on the handle.  Non-finite points
  * give NaN outputs and FPE_ERR_NONFINITE from the next fpe_sync().

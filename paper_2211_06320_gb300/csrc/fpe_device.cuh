@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -410,6 +411,204 @@ __device__ __forceinline__ xdd xdd_pow_int(double zr, double zi, long long n) {
   xdd x = xdd_from_xint(r);
   x.e += (long long)f * n;
   return x;
+}
+
+// ---------------------------------------------------------------------------
+// Horner steps on the integer pipe.  A partial sum is a complex fixed-point
+// value (xr + i xi) 2^G with xr, xi two's-complement 128-bit integers; after
+// isum_normalise the larger magnitude has its top bit at position 121.  A
+// step h <- h w + b truncates at the frame's unit: 2^-121 of the partial sum
+// after a normalisation and at most 16 bits more before the next one (a
+// product can lose 2 bits of magnitude, and normalising happens every 8
+// steps), so a window of L terms summed top-down has an error of order
+// L 2^-104 times the sum of the term magnitudes: the summation order no
+// longer matters.  The multiplier w = 2^beta z is used exactly: each
+// component is its 53-bit mantissa as a signed 63-bit word; when the two
+// exponents are within 10 of each other (more for subnormals) both words
+// share one exponent exactly, otherwise each keeps its own and the smaller
+// product is shifted into the larger's frame (the SPLIT form).  G
+// is a 64-bit exponent, so nothing overflows.
+//
+// Magnitude budget: a product (x w) >> 64 with |w| < 2^63 has at most half
+// the magnitude of x, so each component of h w is at most max(|xr|, |xi|),
+// and a coefficient adds less than 2^121 (larger ones move the frame up).
+// From < 2^122 after normalising, eight steps stay below 2^125 (mulhi_s
+// needs < 2^127): callers normalise at least every eight steps.  No FP64
+// instruction is used.
+// ---------------------------------------------------------------------------
+typedef __int128 i128;
+
+constexpr int kIsumTop = 121;        // top bit after normalising
+constexpr int kIsumMaxSteps = 8;     // steps between normalisations
+constexpr int kIsumCoefShift = 68;   // a coefficient 53-bit mantissa sits at most this far up
+
+struct isum {
+  i128 xr, xi;
+  long long G;
+};
+
+// frame of a zero sum: far below any coefficient, so the next nonzero
+// coefficient sets the frame (and steps of a zero sum cannot overflow G)
+constexpr long long kIsumZeroFrame = -(1LL << 60);
+
+// w = wr 2^(E - dr) + i wi 2^(E - di), |wr|, |wi| < 2^63; split == 0 means
+// dr == di == 0 (one shared exponent)
+struct iw {
+  long long wr, wi;
+  int dr, di, split;
+  long long E;
+};
+
+// x = (-1)^s m 2^e with m < 2^53 (m = 0 for x = 0)
+__host__ __device__ __forceinline__ void decode_dbl(double x, unsigned long long &m, int &e, int &s) {
+  const unsigned long long bits = dbl_bits(x);
+  s = (int)(bits >> 63);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  m = bits & 0xfffffffffffffull;
+  if (ex == 0) {
+    e = -1074;
+  } else {
+    m |= 0x10000000000000ull;
+    e = ex - 1075;
+  }
+}
+
+__host__ __device__ __forceinline__ int bitlen64(unsigned long long m) {
+#ifdef __CUDA_ARCH__
+  return m ? 64 - __clzll(m) : 0;
+#else
+  return m ? 64 - __builtin_clzll(m) : 0;
+#endif
+}
+
+__host__ __device__ __forceinline__ iw iw_from(double zr, double zi) {
+  unsigned long long mr, mi;
+  int er, ei, sr, si;
+  decode_dbl(zr, mr, er, sr);
+  decode_dbl(zi, mi, ei, si);
+  iw w;
+  // each mantissa with its top bit at 62, exponents Er, Ei of the word's unit
+  const int shr = mr ? 63 - bitlen64(mr) : 0, shi = mi ? 63 - bitlen64(mi) : 0;
+  const long long Er = (long long)er - shr, Ei = (long long)ei - shi;
+  w.E = mr ? (mi ? (Er > Ei ? Er : Ei) : Er) : Ei;
+  long long dr = mr ? w.E - Er : 0, di = mi ? w.E - Ei : 0;
+  // when the smaller word has at least that many trailing zeros (10 for a
+  // normal double) it moves down to the larger's unit exactly: one exponent
+  const int sdr = (dr > 0 && dr <= shr) ? (int)dr : 0;
+  const int sdi = (di > 0 && di <= shi) ? (int)di : 0;
+  const unsigned long long ur = (mr << shr) >> sdr, ui = (mi << shi) >> sdi;
+  dr -= sdr;
+  di -= sdi;
+  w.wr = sr ? -(long long)ur : (long long)ur;
+  w.wi = si ? -(long long)ui : (long long)ui;
+  w.dr = (int)(dr < 127 ? dr : 127);
+  w.di = (int)(di < 127 ? di : 127);
+  w.split = (w.dr | w.di) != 0;
+  return w;
+}
+
+// (x w) / 2^64 for |x| < 2^127, |w| < 2^63, within 1 of the exact quotient
+// (the low partial product is truncated)
+__host__ __device__ __forceinline__ i128 mulhi_s(i128 x, long long w) {
+  const long long x1 = (long long)(x >> 64);
+  const unsigned long long x0 = (unsigned long long)x;
+  const unsigned long long h0 = umulhi64(x0, (unsigned long long)w) - (w < 0 ? x0 : 0ull);
+  return (i128)x1 * w + (i128)(long long)h0;
+}
+
+// (-1)^s m 2^sh as a signed 128-bit value, sh <= kIsumCoefShift (truncated below 2^0)
+__host__ __device__ __forceinline__ i128 place53(unsigned long long m, int s, long long sh) {
+  const long long v = s ? -(long long)m : (long long)m;
+  if (sh >= 0) return (i128)((u128)(i128)v << sh);
+  return sh > -64 ? (i128)(v >> (-sh)) : (i128)(v >> 63);
+}
+
+__host__ __device__ __forceinline__ void isum_normalise(isum &h) {
+  const u128 m = (u128)(h.xr ^ (h.xr >> 127)) | (u128)(h.xi ^ (h.xi >> 127));
+  if (!m) {  // 0 or -1 (below the frame's unit): a zero sum
+    h.xr = h.xi = 0;
+    h.G = kIsumZeroFrame;
+    return;
+  }
+  const int d = clz128(m) - (127 - kIsumTop);
+  if (d > 0) {
+    h.xr = (i128)((u128)h.xr << d);
+    h.xi = (i128)((u128)h.xi << d);
+  } else if (d < 0) {
+    h.xr >>= -d;
+    h.xi >>= -d;
+  }
+  h.G -= d;
+}
+
+// fixed-point copy of the complex double hr + i hm, normalised (exact unless
+// the two parts are more than 68 binary orders apart)
+__host__ __device__ __forceinline__ isum isum_from(double hr, double hm) {
+  unsigned long long mr, mi;
+  int er, ei, sr, si;
+  decode_dbl(hr, mr, er, sr);
+  decode_dbl(hm, mi, ei, si);
+  isum h;
+  if (!mr && !mi) {
+    h.xr = h.xi = 0;
+    h.G = kIsumZeroFrame;
+    return h;
+  }
+  const long long tr = mr ? (long long)er + bitlen64(mr) - 1 : LLONG_MIN;
+  const long long ti = mi ? (long long)ei + bitlen64(mi) - 1 : LLONG_MIN;
+  h.G = (tr > ti ? tr : ti) - kIsumTop;
+  h.xr = mr ? place53(mr, sr, er - h.G) : (i128)0;
+  h.xi = mi ? place53(mi, si, ei - h.G) : (i128)0;
+  return h;
+}
+
+// h <- h w 2^shift + (br + i bi) without normalising; CZ: complex w, CC:
+// complex coefficient (h is complex when either is), SPLIT: w with two
+// exponents.  we64 = w.E + shift + 64.
+template <bool CC, bool CZ, bool SPLIT>
+__host__ __device__ __forceinline__ void isum_step(isum &h, const iw &w, long long we64, double br, double bi) {
+  constexpr bool CH = CC || CZ;
+  i128 re, im = 0;
+  if (CZ) {
+    if (SPLIT) {
+      re = (mulhi_s(h.xr, w.wr) >> w.dr) - (mulhi_s(h.xi, w.wi) >> w.di);
+      im = (mulhi_s(h.xr, w.wi) >> w.di) + (mulhi_s(h.xi, w.wr) >> w.dr);
+    } else {
+      re = mulhi_s(h.xr, w.wr) - mulhi_s(h.xi, w.wi);
+      im = mulhi_s(h.xr, w.wi) + mulhi_s(h.xi, w.wr);
+    }
+  } else {
+    re = mulhi_s(h.xr, w.wr);
+    if (CH) im = mulhi_s(h.xi, w.wr);
+  }
+  long long G = h.G + we64;
+  unsigned long long mr, mi = 0;
+  int er, ei = 0, s_r, s_i = 0;
+  decode_dbl(br, mr, er, s_r);
+  if (CC) decode_dbl(bi, mi, ei, s_i);
+  // a coefficient of 2^121 or more in this frame moves the frame up first
+  long long need = G;
+  if (mr && (long long)er - need > kIsumCoefShift) need = (long long)er - kIsumCoefShift;
+  if (CC && mi && (long long)ei - need > kIsumCoefShift) need = (long long)ei - kIsumCoefShift;
+  if (need > G) {
+    const int d = (int)(need - G < 127 ? need - G : 127);
+    re >>= d;
+    im >>= d;
+    G = need;
+  }
+  if (mr) re += place53(mr, s_r, (long long)er - G);
+  if (CC && mi) im += place53(mi, s_i, (long long)ei - G);
+  h.xr = re;
+  h.xi = im;
+  h.G = G;
+}
+
+// extended double-double of a fixed-point sum
+__device__ __forceinline__ xdd xdd_from_isum(const isum &h) {
+  const int sr = h.xr < 0, si = h.xi < 0;
+  const u128 ar = sr ? (u128)(-h.xr) : (u128)h.xr, ai = si ? (u128)(-h.xi) : (u128)h.xi;
+  if (!ar && !ai) return xdd_zero();
+  return xdd_from_xint(xint_norm(ar, sr, ai, si, h.G + 126));
 }
 
 // Normalised FP64 output (fpe_xc64) from an extended double-double value.

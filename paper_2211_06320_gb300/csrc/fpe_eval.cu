@@ -575,15 +575,68 @@ __device__ __forceinline__ xdd range_sum_any(const DevPoly &P, double zr, double
     return range_sum<CC, CZ>(P, zr, zi, mr, mi, f, u, lo, hi, kl, base);
 }
 
-// Compensated top-down sum over [lo, hi] relative to z^lo (FPE_ACCURATE).
+// Integer-pipe Horner continued from h (scaled at index k + 1, which lies in
+// piece j) down to lo: h <- h 2^(rho(k+1) - rho(k)) z + b_k.  Returns the
+// piece holding lo.
+template <bool CC, bool CZ, bool SPLIT>
+__device__ __forceinline__ int int_horner(const DevPoly &P, isum &h, const iw &w, long long k, int j, long long lo) {
+  while (k >= lo) {
+    if (k < P.piece_k0[j]) {
+      --j;  // k == piece_k0[j + 1] - 1: enter piece j
+      h.G += P.piece_delta[j];
+    }
+    const long long we64 = w.E + P.piece_beta[j] + 64;
+    const long long k0 = max((long long)P.piece_k0[j], lo);
+    if (CC) {
+      const double2 *b2 = reinterpret_cast<const double2 *>(P.b);
+      for (; k - (kIsumMaxSteps - 1) >= k0; k -= kIsumMaxSteps) {
+#pragma unroll
+        for (int t = 0; t < kIsumMaxSteps; ++t) {
+          const double2 c = __ldg(&b2[k - t]);
+          isum_step<CC, CZ, SPLIT>(h, w, we64, c.x, c.y);
+        }
+        isum_normalise(h);
+      }
+      for (; k >= k0; --k) {
+        const double2 c = __ldg(&b2[k]);
+        isum_step<CC, CZ, SPLIT>(h, w, we64, c.x, c.y);
+      }
+    } else {
+      for (; k - (kIsumMaxSteps - 1) >= k0; k -= kIsumMaxSteps) {
+#pragma unroll
+        for (int t = 0; t < kIsumMaxSteps; ++t) isum_step<CC, CZ, SPLIT>(h, w, we64, __ldg(&P.b[k - t]), 0.0);
+        isum_normalise(h);
+      }
+      for (; k >= k0; --k) isum_step<CC, CZ, SPLIT>(h, w, we64, __ldg(&P.b[k]), 0.0);
+    }
+    isum_normalise(h);  // at most kIsumMaxSteps - 1 steps since the last one
+  }
+  return j;
+}
+
+// sum_{k=lo}^{hi} a_k z^(k - lo) in extended double-double by Horner taken
+// top-down on the integer pipe (FPE_ACCURATE): every step rounds at 2^-104
+// or less of the partial sum, so the order that makes FP64 accurate (toward
+// the peak term) is not needed and no FP64 instruction is spent.
 template <bool CC, bool CZ>
-__device__ __forceinline__ xdd range_sum_comp(const DevPoly &P, double zr, double zi, long long lo, long long hi) {
-  double hr, hm, cr, cm;
-  long long rho;
-  window_horner<CC, CZ, true>(P, P.b, zr, zi, lo, hi, hr, hm, cr, cm, rho);
-  dd re = two_sum(hr, cr), im = two_sum(hm, cm);
-  xdd x = {re.hi, re.lo, im.hi, im.lo, rho};
-  return xdd_norm(x);
+__device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, double zi, long long lo, long long hi) {
+  isum h;
+  if (CC) {
+    const double2 c = reinterpret_cast<const double2 *>(P.b)[hi];
+    h = isum_from(c.x, c.y);
+  } else {
+    h = isum_from(P.b[hi], 0.0);
+  }
+  int j = P.piece_first[hi >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= hi) ++j;
+  const iw w = iw_from(zr, CZ ? zi : 0.0);
+  if (CZ && w.split)
+    j = int_horner<CC, CZ, true>(P, h, w, hi - 1, j, lo);
+  else
+    j = int_horner<CC, CZ, false>(P, h, w, hi - 1, j, lo);
+  xdd X = xdd_from_isum(h);
+  if (X.rh != 0.0 || X.ih != 0.0) X.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
+  return X;
 }
 
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
@@ -600,10 +653,9 @@ __global__ void __launch_bounds__(128) k_sum_short(DevPoly P0, const DevPoly *__
   } else {
     if (r.hi - r.lo + 1 > kLongWindow) return;  // summed by k_sum_groups
     xdd X;
-    long long base;
+    long long base = r.lo;
     if (ACC) {
-      X = range_sum_comp<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
-      base = r.lo;
+      X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
     } else {
       const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
       const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
@@ -697,7 +749,7 @@ __global__ void __launch_bounds__(128) k_sum_groups(DevPoly P0, const DevPoly *_
     const long long chi = min(clo + C - 1, r.hi);
     xdd sv = xdd_zero(), carry = xdd_zero();
     if (ACC) {
-      if (clo <= chi) sv = range_sum_comp<CC, CZ>(P, r.zr, r.zi, clo, chi);
+      if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
     } else if (clo <= chi) {
       const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
       const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);

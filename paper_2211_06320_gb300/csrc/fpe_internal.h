@@ -66,7 +66,7 @@ struct DevPoly {
   int32_t npieces;
   int32_t complex_coef;
   int32_t fp32;
-  int32_t accurate;    // FPE_ACCURATE: compensated window sums
+  int32_t accurate;    // FPE_ACCURATE: window sums on the integer pipe
   int32_t log2_piece;  // kLog2PieceLen or kLog2PieceLenF32
   double a0_re, a0_im;  // a_0 as a normalised mantissa (0 when v > 0)
   int64_t a0_e;
