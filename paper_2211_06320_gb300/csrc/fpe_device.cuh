@@ -242,6 +242,26 @@ __device__ __forceinline__ cdd recip_dd(double mr, double mi) {
   return {ur.hi, ur.lo, ui.hi, ui.lo};
 }
 
+// complex double-double product (relative error about 2^-104 of |a||b|)
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+  dd p = two_prod(x.hi, y.hi);
+  p.lo = fma(x.hi, y.lo, fma(x.lo, y.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+  dd s = two_sum(x.hi, y.hi);
+  s.lo += x.lo + y.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ cdd cdd_mul(const cdd &a, const cdd &b) {
+  const dd ar = {a.rh, a.rl}, ai = {a.ih, a.il}, br = {b.rh, b.rl}, bi = {b.ih, b.il};
+  dd t = dd_mul(ai, bi);
+  t.hi = -t.hi;
+  t.lo = -t.lo;
+  const dd re = dd_add(dd_mul(ar, br), t), im = dd_add(dd_mul(ar, bi), dd_mul(ai, br));
+  return {re.hi, re.lo, im.hi, im.lo};
+}
+
 // ---------------------------------------------------------------------------
 // z^n on the integer pipe.  On this GPU a 64-bit integer multiply-high issues
 // about four times as fast as an FP64 FMA and 32-bit multiply-adds about 37
@@ -422,47 +442,60 @@ __device__ __forceinline__ xdd xdd_pow_int(double zr, double zi, long long n) {
 // product can lose 2 bits of magnitude, and normalising happens every 8
 // steps), so a window of L terms summed top-down has an error of order
 // L 2^-104 times the sum of the term magnitudes: the summation order no
-// longer matters.  The multiplier w = 2^beta z is used exactly: each
-// component is its 53-bit mantissa as a signed 63-bit word; when the two
-// exponents are within 10 of each other (more for subnormals) both words
-// share one exponent exactly, otherwise each keeps its own and the smaller
-// product is shifted into the larger's frame (the SPLIT form).  G
-// is a 64-bit exponent, so nothing overflows.
+// longer matters.  No FP64 instruction is used.
 //
-// Magnitude budget: a product (x w) >> 64 with |w| < 2^63 has at most half
-// the magnitude of x, so each component of h w is at most max(|xr|, |xi|),
+// The multiplier.  w = 2^beta z is used exactly, as w = i^q w' with w' in
+// the closed first quadrant (a swap and sign changes of z's parts): each
+// component of w' is its 53-bit mantissa as an unsigned 63-bit word.  When
+// the two exponents are within 10 of each other (more for subnormals) both
+// words share one exponent exactly; otherwise each keeps its own and the
+// smaller component's products are shifted into the larger's frame (SPLIT).
+// Horner with w = i^q w' runs as g_k = g_{k+1} w' + i^(-q m) b_k with
+// m = top - k, and h = i^(q m) g at the end: rotating a coefficient by a
+// power of i is a swap and sign changes, so no product carries a sign of w.
+//
+// The coefficients come packed (qpack): a 54-bit two's-complement mantissa
+// and an exponent, placed into the frame with one variable shift.
+//
+// Magnitude budget: a product (x w) >> 64 with w < 2^63 has at most half
+// the magnitude of x, so each component of h w' is at most max(|xr|, |xi|),
 // and a coefficient adds less than 2^121 (larger ones move the frame up).
-// From < 2^122 after normalising, eight steps stay below 2^125 (mulhi_s
-// needs < 2^127): callers normalise at least every eight steps.  No FP64
-// instruction is used.
+// From < 2^122 after normalising, eight steps stay below 2^125: callers
+// normalise at least every eight steps.
 // ---------------------------------------------------------------------------
 typedef __int128 i128;
 
 constexpr int kIsumTop = 121;        // top bit after normalising
 constexpr int kIsumMaxSteps = 8;     // steps between normalisations
-constexpr int kIsumCoefShift = 68;   // a coefficient 53-bit mantissa sits at most this far up
+constexpr int kIsumCoefShift = 68;   // a coefficient 54-bit mantissa sits at most this far up
 
 struct isum {
   i128 xr, xi;
-  long long G;
+  int G;
 };
 
 // frame of a zero sum: far below any coefficient, so the next nonzero
-// coefficient sets the frame (and steps of a zero sum cannot overflow G)
-constexpr long long kIsumZeroFrame = -(1LL << 60);
+// coefficient sets the frame (and eight steps of a zero sum cannot wrap G)
+constexpr int kIsumZeroFrame = -(1 << 29);
 
-// w = wr 2^(E - dr) + i wi 2^(E - di), |wr|, |wi| < 2^63; split == 0 means
-// dr == di == 0 (one shared exponent)
+// w = i^q (w'r + i w'i), w'r = r 2^(E - dr), w'i = m 2^(E - di), r, m < 2^63
 struct iw {
-  long long wr, wi;
-  int dr, di, split;
-  long long E;
+  uint32_t r0, r1, m0, m1;  // 32-bit limbs of the two words
+  int dr, di, split, q;
+  int E;
 };
 
-// x = (-1)^s m 2^e with m < 2^53 (m = 0 for x = 0)
-__host__ __device__ __forceinline__ void decode_dbl(double x, unsigned long long &m, int &e, int &s) {
+__host__ __device__ __forceinline__ int bitlen64(unsigned long long m) {
+#ifdef __CUDA_ARCH__
+  return m ? 64 - __clzll(m) : 0;
+#else
+  return m ? 64 - __builtin_clzll(m) : 0;
+#endif
+}
+
+// |x| = m 2^e with m < 2^53 (m = 0 for x = 0)
+__host__ __device__ __forceinline__ void decode_abs(double x, unsigned long long &m, int &e) {
   const unsigned long long bits = dbl_bits(x);
-  s = (int)(bits >> 63);
   const int ex = (int)((bits >> 52) & 0x7ff);
   m = bits & 0xfffffffffffffull;
   if (ex == 0) {
@@ -473,52 +506,101 @@ __host__ __device__ __forceinline__ void decode_dbl(double x, unsigned long long
   }
 }
 
-__host__ __device__ __forceinline__ int bitlen64(unsigned long long m) {
-#ifdef __CUDA_ARCH__
-  return m ? 64 - __clzll(m) : 0;
-#else
-  return m ? 64 - __builtin_clzll(m) : 0;
-#endif
-}
-
 __host__ __device__ __forceinline__ iw iw_from(double zr, double zi) {
+  // z = i^q w' with Re w' > 0, Im w' >= 0 (z != 0)
+  int q;
+  double ar, ai;  // |parts| of w' in order (re, im)
+  if (zr > 0.0 && zi >= 0.0) {
+    q = 0, ar = zr, ai = zi;
+  } else if (zr <= 0.0 && zi > 0.0) {
+    q = 1, ar = zi, ai = -zr;
+  } else if (zr < 0.0 && zi <= 0.0) {
+    q = 2, ar = -zr, ai = -zi;
+  } else {
+    q = 3, ar = -zi, ai = zr;
+  }
   unsigned long long mr, mi;
-  int er, ei, sr, si;
-  decode_dbl(zr, mr, er, sr);
-  decode_dbl(zi, mi, ei, si);
+  int er, ei;
+  decode_abs(ar, mr, er);
+  decode_abs(ai, mi, ei);
   iw w;
-  // each mantissa with its top bit at 62, exponents Er, Ei of the word's unit
+  w.q = q;
+  // each mantissa with its top bit at 62; exponents Er, Ei of the word's unit
   const int shr = mr ? 63 - bitlen64(mr) : 0, shi = mi ? 63 - bitlen64(mi) : 0;
-  const long long Er = (long long)er - shr, Ei = (long long)ei - shi;
+  const int Er = er - shr, Ei = ei - shi;
   w.E = mr ? (mi ? (Er > Ei ? Er : Ei) : Er) : Ei;
-  long long dr = mr ? w.E - Er : 0, di = mi ? w.E - Ei : 0;
-  // when the smaller word has at least that many trailing zeros (10 for a
-  // normal double) it moves down to the larger's unit exactly: one exponent
-  const int sdr = (dr > 0 && dr <= shr) ? (int)dr : 0;
-  const int sdi = (di > 0 && di <= shi) ? (int)di : 0;
+  int dr = mr ? w.E - Er : 0, di = mi ? w.E - Ei : 0;
+  // when the smaller word has that many trailing zeros it moves down exactly
+  const int sdr = (dr > 0 && dr <= shr) ? dr : 0;
+  const int sdi = (di > 0 && di <= shi) ? di : 0;
   const unsigned long long ur = (mr << shr) >> sdr, ui = (mi << shi) >> sdi;
   dr -= sdr;
   di -= sdi;
-  w.wr = sr ? -(long long)ur : (long long)ur;
-  w.wi = si ? -(long long)ui : (long long)ui;
-  w.dr = (int)(dr < 127 ? dr : 127);
-  w.di = (int)(di < 127 ? di : 127);
+  w.r0 = (uint32_t)ur;
+  w.r1 = (uint32_t)(ur >> 32);
+  w.m0 = (uint32_t)ui;
+  w.m1 = (uint32_t)(ui >> 32);
+  w.dr = dr < 127 ? dr : 127;
+  w.di = di < 127 ? di : 127;
   w.split = (w.dr | w.di) != 0;
   return w;
 }
 
-// (x w) / 2^64 for |x| < 2^127, |w| < 2^63, within 1 of the exact quotient
-// (the low partial product is truncated)
-__host__ __device__ __forceinline__ i128 mulhi_s(i128 x, long long w) {
-  const long long x1 = (long long)(x >> 64);
-  const unsigned long long x0 = (unsigned long long)x;
-  const unsigned long long h0 = umulhi64(x0, (unsigned long long)w) - (w < 0 ? x0 : 0ull);
-  return (i128)x1 * w + (i128)(long long)h0;
+// x w / 2^64 for a two's-complement x (|x| < 2^127) and w = (w1:w0) < 2^63:
+// the partial products of the two lowest 32-bit columns are dropped, so the
+// result is within 3 of the exact quotient.  Computed on the unsigned bit
+// pattern of x, then w 2^64 is subtracted when x < 0.
+__host__ __device__ __forceinline__ i128 mulhi_limb(i128 xs, uint32_t w0, uint32_t w1) {
+  const u128 x = (u128)xs;
+  const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32), x2 = (uint32_t)(x >> 64), x3 = (uint32_t)(x >> 96);
+  const uint32_t m = (uint32_t)((int32_t)x3 >> 31);
+#ifdef __CUDA_ARCH__
+  uint32_t r0, r1, r2, r3;
+  asm("{\n\t"
+      ".reg .u32 t0, t1;\n\t"
+      "mul.hi.u32      %0, %5, %8;\n\t"        // col 2: hi(x1 w0)
+      "mul.lo.u32      %1, %7, %8;\n\t"        // col 3: lo(x3 w0)
+      "mul.hi.u32      %2, %7, %8;\n\t"        // col 4: hi(x3 w0)
+      "mad.lo.cc.u32   %0, %6, %8, %0;\n\t"    // col 2 += lo(x2 w0)
+      "madc.hi.cc.u32  %1, %6, %8, %1;\n\t"    // col 3 += hi(x2 w0)
+      "addc.u32        %2, %2, 0;\n\t"
+      "mad.lo.cc.u32   %0, %5, %9, %0;\n\t"    // col 2 += lo(x1 w1)
+      "madc.lo.cc.u32  %1, %6, %9, %1;\n\t"    // col 3 += lo(x2 w1)
+      "madc.lo.cc.u32  %2, %7, %9, %2;\n\t"    // col 4 += lo(x3 w1)
+      "addc.u32        %3, 0, 0;\n\t"
+      "mad.hi.cc.u32   %0, %4, %9, %0;\n\t"    // col 2 += hi(x0 w1)
+      "madc.hi.cc.u32  %1, %5, %9, %1;\n\t"    // col 3 += hi(x1 w1)
+      "madc.hi.cc.u32  %2, %6, %9, %2;\n\t"    // col 4 += hi(x2 w1)
+      "madc.hi.u32     %3, %7, %9, %3;\n\t"    // col 5 += hi(x3 w1)
+      "and.b32         t0, %8, %10;\n\t"       // x < 0: subtract w 2^64
+      "and.b32         t1, %9, %10;\n\t"
+      "sub.cc.u32      %2, %2, t0;\n\t"
+      "subc.u32        %3, %3, t1;\n\t"
+      "}"
+      : "=&r"(r0), "=&r"(r1), "=&r"(r2), "=&r"(r3)
+      : "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(w0), "r"(w1), "r"(m));
+  return (i128)(((u128)r3 << 96) | ((u128)r2 << 64) | ((u128)r1 << 32) | (u128)r0);
+#else
+  // the same column sums, modulo 2^128
+  auto lo = [](uint32_t a, uint32_t b) -> u128 { return (u128)(uint32_t)((uint64_t)a * b); };
+  auto hi = [](uint32_t a, uint32_t b) -> u128 { return (u128)(uint32_t)(((uint64_t)a * b) >> 32); };
+  u128 r = hi(x1, w0) + hi(x0, w1) + lo(x2, w0) + lo(x1, w1);
+  r += (hi(x2, w0) + hi(x1, w1) + lo(x3, w0) + lo(x2, w1)) << 32;
+  r += (hi(x3, w0) + hi(x2, w1) + lo(x3, w1)) << 64;
+  r += hi(x3, w1) << 96;
+  r -= ((u128)(((uint64_t)(w1 & m) << 32) | (w0 & m))) << 64;
+  return (i128)r;
+#endif
 }
 
-// (-1)^s m 2^sh as a signed 128-bit value, sh <= kIsumCoefShift (truncated below 2^0)
-__host__ __device__ __forceinline__ i128 place53(unsigned long long m, int s, long long sh) {
-  const long long v = s ? -(long long)m : (long long)m;
+// a packed coefficient component: value = v 2^e
+__host__ __device__ __forceinline__ void qdecode(unsigned long long q, long long &v, int &e) {
+  v = (long long)(q << 10) >> 10;
+  e = (int)(q >> 54) - kQBias;
+}
+
+// v 2^sh as a signed 128-bit value, sh <= kIsumCoefShift (truncated below 2^0)
+__host__ __device__ __forceinline__ i128 place_q(long long v, int sh) {
   if (sh >= 0) return (i128)((u128)(i128)v << sh);
   return sh > -64 ? (i128)(v >> (-sh)) : (i128)(v >> 63);
 }
@@ -545,59 +627,86 @@ __host__ __device__ __forceinline__ void isum_normalise(isum &h) {
 // the two parts are more than 68 binary orders apart)
 __host__ __device__ __forceinline__ isum isum_from(double hr, double hm) {
   unsigned long long mr, mi;
-  int er, ei, sr, si;
-  decode_dbl(hr, mr, er, sr);
-  decode_dbl(hm, mi, ei, si);
+  int er, ei;
+  decode_abs(hr, mr, er);
+  decode_abs(hm, mi, ei);
   isum h;
   if (!mr && !mi) {
     h.xr = h.xi = 0;
     h.G = kIsumZeroFrame;
     return h;
   }
-  const long long tr = mr ? (long long)er + bitlen64(mr) - 1 : LLONG_MIN;
-  const long long ti = mi ? (long long)ei + bitlen64(mi) - 1 : LLONG_MIN;
+  const int tr = mr ? er + bitlen64(mr) - 1 : -100000;
+  const int ti = mi ? ei + bitlen64(mi) - 1 : -100000;
   h.G = (tr > ti ? tr : ti) - kIsumTop;
-  h.xr = mr ? place53(mr, sr, er - h.G) : (i128)0;
-  h.xi = mi ? place53(mi, si, ei - h.G) : (i128)0;
+  const long long vr = hr < 0.0 ? -(long long)mr : (long long)mr;
+  const long long vi = hm < 0.0 ? -(long long)mi : (long long)mi;
+  h.xr = mr ? place_q(vr, er - h.G) : (i128)0;
+  h.xi = mi ? place_q(vi, ei - h.G) : (i128)0;
   return h;
 }
 
-// h <- h w 2^shift + (br + i bi) without normalising; CZ: complex w, CC:
-// complex coefficient (h is complex when either is), SPLIT: w with two
-// exponents.  we64 = w.E + shift + 64.
+// multiply the fixed-point sum by i^t (exact)
+__host__ __device__ __forceinline__ void isum_rotate(isum &h, int t) {
+  const i128 r = h.xr, m = h.xi;
+  switch (t & 3) {
+    case 1: h.xr = -m, h.xi = r; break;
+    case 2: h.xr = -r, h.xi = -m; break;
+    case 3: h.xr = m, h.xi = -r; break;
+    default: break;
+  }
+}
+
+// g <- g w' 2^shift + i^t (br + i bi) from packed coefficient words, without
+// normalising; CZ: complex w, CC: complex coefficient, SPLIT: w with two
+// exponents.  we64 = w.E + shift + 64.  Returns nothing; t is the caller's.
 template <bool CC, bool CZ, bool SPLIT>
-__host__ __device__ __forceinline__ void isum_step(isum &h, const iw &w, long long we64, double br, double bi) {
+__host__ __device__ __forceinline__ void isum_step(isum &h, const iw &w, int we64, unsigned long long qr,
+                                                   unsigned long long qi, int t) {
   constexpr bool CH = CC || CZ;
   i128 re, im = 0;
   if (CZ) {
+    i128 prr = mulhi_limb(h.xr, w.r0, w.r1), pir = mulhi_limb(h.xi, w.r0, w.r1);
+    i128 pii = mulhi_limb(h.xi, w.m0, w.m1), pri = mulhi_limb(h.xr, w.m0, w.m1);
     if (SPLIT) {
-      re = (mulhi_s(h.xr, w.wr) >> w.dr) - (mulhi_s(h.xi, w.wi) >> w.di);
-      im = (mulhi_s(h.xr, w.wi) >> w.di) + (mulhi_s(h.xi, w.wr) >> w.dr);
-    } else {
-      re = mulhi_s(h.xr, w.wr) - mulhi_s(h.xi, w.wi);
-      im = mulhi_s(h.xr, w.wi) + mulhi_s(h.xi, w.wr);
+      prr >>= w.dr, pir >>= w.dr;
+      pii >>= w.di, pri >>= w.di;
     }
+    re = prr - pii;
+    im = pri + pir;
   } else {
-    re = mulhi_s(h.xr, w.wr);
-    if (CH) im = mulhi_s(h.xi, w.wr);
+    re = mulhi_limb(h.xr, w.r0, w.r1);
+    if (CH) im = mulhi_limb(h.xi, w.r0, w.r1);
   }
-  long long G = h.G + we64;
-  unsigned long long mr, mi = 0;
-  int er, ei = 0, s_r, s_i = 0;
-  decode_dbl(br, mr, er, s_r);
-  if (CC) decode_dbl(bi, mi, ei, s_i);
+  int G = h.G + we64;
+  long long vr, vi = 0;
+  int er, ei = -kQBias;
+  qdecode(qr, vr, er);
+  if (CC) qdecode(qi, vi, ei);
+  if (CZ) {  // i^t (vr + i vi)
+    if (t & 1) {
+      const long long tv = vr;
+      const int te = er;
+      vr = vi, er = ei;
+      vi = tv, ei = te;
+    }
+    if (t == 1 || t == 2) vr = -vr;
+    if (t >= 2) vi = -vi;
+  } else if (t & 2) {  // real w: t in {0, 2}
+    vr = -vr;
+    vi = -vi;
+  }
   // a coefficient of 2^121 or more in this frame moves the frame up first
-  long long need = G;
-  if (mr && (long long)er - need > kIsumCoefShift) need = (long long)er - kIsumCoefShift;
-  if (CC && mi && (long long)ei - need > kIsumCoefShift) need = (long long)ei - kIsumCoefShift;
+  const int etop = (er > ei ? er : ei) - kIsumCoefShift;
+  const int need = etop > G ? etop : G;
   if (need > G) {
-    const int d = (int)(need - G < 127 ? need - G : 127);
+    const int d = need - G < 127 ? need - G : 127;
     re >>= d;
     im >>= d;
     G = need;
   }
-  if (mr) re += place53(mr, s_r, (long long)er - G);
-  if (CC && mi) im += place53(mi, s_i, (long long)ei - G);
+  re += place_q(vr, er - G);
+  if (CH) im += place_q(vi, ei - G);
   h.xr = re;
   h.xi = im;
   h.G = G;
@@ -608,7 +717,7 @@ __device__ __forceinline__ xdd xdd_from_isum(const isum &h) {
   const int sr = h.xr < 0, si = h.xi < 0;
   const u128 ar = sr ? (u128)(-h.xr) : (u128)h.xr, ai = si ? (u128)(-h.xi) : (u128)h.xi;
   if (!ar && !ai) return xdd_zero();
-  return xdd_from_xint(xint_norm(ar, sr, ai, si, h.G + 126));
+  return xdd_from_xint(xint_norm(ar, sr, ai, si, (long long)h.G + 126));
 }
 
 // Normalised FP64 output (fpe_xc64) from an extended double-double value.

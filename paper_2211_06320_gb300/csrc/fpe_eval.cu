@@ -342,60 +342,115 @@ __device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, 
 // returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-hi) = h * 2^rho(hi).
 // 1/z = u 2^ue with u in double-double.  Within piece j the step from k-1 to
 // k multiplies by v_j = 2^-beta_j / z; crossing from piece j to j+1 first
-// scales h by 2^-delta_j.  Each step is 8 FMA for complex z and coefficients.
+// scales h by 2^-delta_j.  A single step is 8 FMA for complex z and
+// coefficients (v in double-double).
+//
+// Blocks of four.  With w = 1/v = 2^beta_j z (exact in FP64), four steps
+// from K to K+4 inside a piece are
+//   h_{K+4} = v^4 h_K + v^3 s_K,  s_K = b_{K+1} + w (b_{K+2} + w (b_{K+3} + w b_{K+4})),
+// so G = w^3 h obeys G_{K+4} = v^4 G_K + s_K (the first block of a run
+// starts from G = v h_K + s_K, and h = v^3 G at its end).  s_K is a top-down
+// FP64 Horner with the exact multiplier (3 complex FMA, rounding within
+// 3u of the block's term magnitudes) and the block step multiplies by v^4 in
+// double-double: 20 FMA per four terms instead of 32.  u3 = u^3, u4 = u^4.
 template <bool CC, bool CZ>
 __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b, const cdd &u,
-                                                  int ue, long long lo, long long hi, double &hr, double &hm,
+                                                  const cdd &u3, const cdd &u4, bool blocks, int ue, double zr,
+                                                  double zi, long long lo, long long hi, double &hr, double &hm,
                                                   long long &rho_hi) {
   int j = P.piece_first[lo >> P.log2_piece];
   while (P.piece_k0[j + 1] <= lo) ++j;
-  if (CC) {
-    double2 c = reinterpret_cast<const double2 *>(b)[lo];
-    hr = c.x;
-    hm = c.y;
-  } else {
-    hr = b[lo];
-    hm = 0.0;
-  }
+  auto load = [&](long long k, double &br, double &bi) {
+    if (CC) {
+      const double2 c = __ldg(reinterpret_cast<const double2 *>(b) + k);
+      br = c.x;
+      bi = c.y;
+    } else {
+      br = __ldg(b + k);
+      bi = 0.0;
+    }
+  };
+  load(lo, hr, hm);
   long long k = lo + 1;
   while (k <= hi) {
-    const int sh = ue - P.piece_beta[j];
+    const int beta = P.piece_beta[j];
+    const int sh = ue - beta;
     const double vhr = scale2(u.rh, sh), vlr = scale2(u.rl, sh);
     const double vhi = CZ ? scale2(u.ih, sh) : 0.0, vli = CZ ? scale2(u.il, sh) : 0.0;
     const long long kend = min((long long)P.piece_k0[j + 1] - 1, hi);
-    bool cross = false;
-    for (;;) {
-      if (k > kend) {
-        if (k > hi) break;
-        // k is the first index of piece j + 1: rescale, one step with v_j, move on
-        const double s2 = pow2i(-P.piece_delta[j]);
-        hr *= s2;
-        hm *= s2;
-        cross = true;
-      }
-      double br, bi;
-      if (CC) {
-        double2 c = __ldg(reinterpret_cast<const double2 *>(b) + k);
-        br = c.x;
-        bi = c.y;
-      } else {
-        br = __ldg(b + k);
-        bi = 0.0;
-      }
+    // h <- h v + (br + i bi), v in double-double
+    auto step_v = [&](double &xr, double &xm, double br, double bi) {
       double nr, ni;
       if (CZ) {
-        nr = fma(hr, vhr, fma(-hm, vhi, fma(hr, vlr, fma(-hm, vli, br))));
-        ni = fma(hr, vhi, fma(hm, vhr, fma(hr, vli, fma(hm, vlr, bi))));
+        nr = fma(xr, vhr, fma(-xm, vhi, fma(xr, vlr, fma(-xm, vli, br))));
+        ni = fma(xr, vhi, fma(xm, vhr, fma(xr, vli, fma(xm, vlr, bi))));
       } else {
-        nr = fma(hr, vhr, fma(hr, vlr, br));
-        ni = CC ? fma(hm, vhr, fma(hm, vlr, bi)) : 0.0;
+        nr = fma(xr, vhr, fma(xr, vlr, br));
+        ni = (CC || CZ) ? fma(xm, vhr, fma(xm, vlr, bi)) : 0.0;
+      }
+      xr = nr;
+      xm = ni;
+    };
+    if (blocks && kend - k + 1 >= 8 && sh > -200 && sh < 200) {  // v^4 and its low part stay normal
+      const double wr = scale2(zr, beta), wi = CZ ? scale2(zi, beta) : 0.0;
+      const double ahr = scale2(u4.rh, 4 * sh), alr = scale2(u4.rl, 4 * sh);
+      const double ahi = CZ ? scale2(u4.ih, 4 * sh) : 0.0, ali = CZ ? scale2(u4.il, 4 * sh) : 0.0;
+      // s over [k, k + 3] by top-down Horner with w
+      auto block_sum = [&](long long k0, double &sr, double &si) {
+        double cr, ci, dr = 0.0, dm = 0.0;
+        load(k0 + 3, sr, si);
+#pragma unroll
+        for (int t = 2; t >= 0; --t) {
+          load(k0 + t, cr, ci);
+          horner_step<CC, CZ, false>(sr, si, dr, dm, wr, wi, cr, ci);
+        }
+      };
+      double sr, si;
+      block_sum(k, sr, si);
+      step_v(hr, hm, sr, si);  // G = v h + s
+      k += 4;
+      for (; k + 3 <= kend; k += 4) {
+        block_sum(k, sr, si);
+        double nr, ni;  // G <- v^4 G + s
+        if (CZ) {
+          nr = fma(hr, ahr, fma(-hm, ahi, fma(hr, alr, fma(-hm, ali, sr))));
+          ni = fma(hr, ahi, fma(hm, ahr, fma(hr, ali, fma(hm, alr, si))));
+        } else {
+          nr = fma(hr, ahr, fma(hr, alr, sr));
+          ni = (CC || CZ) ? fma(hm, ahr, fma(hm, alr, si)) : 0.0;
+        }
+        hr = nr;
+        hm = ni;
+      }
+      // h = v^3 G
+      const double chr = scale2(u3.rh, 3 * sh), clr = scale2(u3.rl, 3 * sh);
+      const double chi = CZ ? scale2(u3.ih, 3 * sh) : 0.0, cli = CZ ? scale2(u3.il, 3 * sh) : 0.0;
+      double nr, ni;
+      if (CZ) {
+        nr = fma(hr, chr, fma(-hm, chi, fma(hr, clr, -hm * cli)));
+        ni = fma(hr, chi, fma(hm, chr, fma(hr, cli, hm * clr)));
+      } else {
+        nr = fma(hr, chr, hr * clr);
+        ni = (CC || CZ) ? fma(hm, chr, hm * clr) : 0.0;
       }
       hr = nr;
       hm = ni;
-      ++k;
-      if (cross) break;
     }
-    if (cross) ++j;
+    for (; k <= kend; ++k) {
+      double br, bi;
+      load(k, br, bi);
+      step_v(hr, hm, br, bi);
+    }
+    if (k > hi) break;
+    // k is the first index of piece j + 1: rescale, one step with v_j, move on
+    const double s2 = pow2i(-P.piece_delta[j]);
+    hr *= s2;
+    hm *= s2;
+    double br, bi;
+    load(k, br, bi);
+    step_v(hr, hm, br, bi);
+    ++k;
+    ++j;
   }
   rho_hi = P.piece_rho0[j] + (long long)P.piece_beta[j] * (hi - P.piece_k0[j]);
 }
@@ -412,6 +467,7 @@ __device__ __forceinline__ xdd xdd_from_cdd(const cdd &u, int ue) {
 template <bool CC, bool CZ>
 __device__ __forceinline__ xdd range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
                                          const cdd &u, long long lo, long long hi, long long kl, long long &base) {
+  constexpr long long kBlockMin = 16;  // below-peak terms from which the blocked pass pays for u^3, u^4
   xdd X = xdd_zero();
   const long long top_lo = max(kl, lo);
   const long long low_hi = min(top_lo - 1, hi);
@@ -426,7 +482,14 @@ __device__ __forceinline__ xdd range_sum(const DevPoly &P, double zr, double zi,
   if (has_low) {
     double hr, hm;
     long long rho;
-    window_horner_rev<CC, CZ>(P, P.b, u, -f, lo, low_hi, hr, hm, rho);
+    const bool blocks = low_hi - lo + 1 >= kBlockMin;
+    cdd u3 = u, u4 = u;
+    if (blocks) {
+      const cdd u2 = cdd_mul(u, u);
+      u3 = cdd_mul(u2, u);
+      u4 = cdd_mul(u2, u2);
+    }
+    window_horner_rev<CC, CZ>(P, P.b, u, u3, u4, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho);
     if (has_up && (X.rh != 0.0 || X.ih != 0.0)) X = xdd_mul_d(X, mr, mi, f);  // z^top_lo = z * z^low_hi
     if (hr != 0.0 || hm != 0.0) X = xdd_add(X, xdd_from(hr, hm, rho));
     base = low_hi;
@@ -575,43 +638,75 @@ __device__ __forceinline__ xdd range_sum_any(const DevPoly &P, double zr, double
     return range_sum<CC, CZ>(P, zr, zi, mr, mi, f, u, lo, hi, kl, base);
 }
 
-// Integer-pipe Horner continued from h (scaled at index k + 1, which lies in
-// piece j) down to lo: h <- h 2^(rho(k+1) - rho(k)) z + b_k.  Returns the
+// Integer-pipe Horner continued from g (scaled at index k + 1, which lies in
+// piece j) down to lo: g <- g 2^(rho(k+1) - rho(k)) w' + i^t b_k with the
+// packed coefficients, t advancing by -q (mod 4) per step (w = i^q w').
+// t on entry is the rotation of the first step's coefficient.  Returns the
 // piece holding lo.
 template <bool CC, bool CZ, bool SPLIT>
-__device__ __forceinline__ int int_horner(const DevPoly &P, isum &h, const iw &w, long long k, int j, long long lo) {
+__device__ __forceinline__ int int_horner(const DevPoly &P, isum &h, const iw &w, long long k, int j, long long lo,
+                                          int t) {
+  const int dq = (4 - w.q) & 3;
   while (k >= lo) {
     if (k < P.piece_k0[j]) {
       --j;  // k == piece_k0[j + 1] - 1: enter piece j
       h.G += P.piece_delta[j];
     }
-    const long long we64 = w.E + P.piece_beta[j] + 64;
+    const int we64 = w.E + P.piece_beta[j] + 64;
     const long long k0 = max((long long)P.piece_k0[j], lo);
     if (CC) {
-      const double2 *b2 = reinterpret_cast<const double2 *>(P.b);
+      const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(P.bq);
       for (; k - (kIsumMaxSteps - 1) >= k0; k -= kIsumMaxSteps) {
 #pragma unroll
-        for (int t = 0; t < kIsumMaxSteps; ++t) {
-          const double2 c = __ldg(&b2[k - t]);
-          isum_step<CC, CZ, SPLIT>(h, w, we64, c.x, c.y);
+        for (int u = 0; u < kIsumMaxSteps; ++u) {
+          const ulonglong2 c = __ldg(&b2[k - u]);
+          isum_step<CC, CZ, SPLIT>(h, w, we64, c.x, c.y, t);
+          t = (t + dq) & 3;
         }
         isum_normalise(h);
       }
       for (; k >= k0; --k) {
-        const double2 c = __ldg(&b2[k]);
-        isum_step<CC, CZ, SPLIT>(h, w, we64, c.x, c.y);
+        const ulonglong2 c = __ldg(&b2[k]);
+        isum_step<CC, CZ, SPLIT>(h, w, we64, c.x, c.y, t);
+        t = (t + dq) & 3;
       }
     } else {
+      const unsigned long long *b1 = reinterpret_cast<const unsigned long long *>(P.bq);
       for (; k - (kIsumMaxSteps - 1) >= k0; k -= kIsumMaxSteps) {
 #pragma unroll
-        for (int t = 0; t < kIsumMaxSteps; ++t) isum_step<CC, CZ, SPLIT>(h, w, we64, __ldg(&P.b[k - t]), 0.0);
+        for (int u = 0; u < kIsumMaxSteps; ++u) {
+          isum_step<CC, CZ, SPLIT>(h, w, we64, __ldg(&b1[k - u]), 0ull, t);
+          t = (t + dq) & 3;
+        }
         isum_normalise(h);
       }
-      for (; k >= k0; --k) isum_step<CC, CZ, SPLIT>(h, w, we64, __ldg(&P.b[k]), 0.0);
+      for (; k >= k0; --k) {
+        isum_step<CC, CZ, SPLIT>(h, w, we64, __ldg(&b1[k]), 0ull, t);
+        t = (t + dq) & 3;
+      }
     }
     isum_normalise(h);  // at most kIsumMaxSteps - 1 steps since the last one
   }
   return j;
+}
+
+// Continue the Horner sum g = h (the value at index top, scaled by
+// 2^rho(top)) on the integer pipe down to lo; returns sum_{k=lo}^{..}
+// a_k z^(k - lo) as extended double-double.
+template <bool CC, bool CZ>
+__device__ __forceinline__ xdd int_tail(const DevPoly &P, isum h, double zr, double zi, long long top, long long lo) {
+  int j = P.piece_first[top >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= top) ++j;
+  const iw w = iw_from(zr, CZ ? zi : 0.0);
+  const int t0 = (4 - w.q) & 3;
+  if (CZ && w.split)
+    j = int_horner<CC, CZ, true>(P, h, w, top - 1, j, lo, t0);
+  else
+    j = int_horner<CC, CZ, false>(P, h, w, top - 1, j, lo, t0);
+  isum_rotate(h, (int)((w.q * ((top - lo) & 3)) & 3));  // h = i^(q (top - lo)) g
+  xdd X = xdd_from_isum(h);
+  if (X.rh != 0.0 || X.ih != 0.0) X.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
+  return X;
 }
 
 // sum_{k=lo}^{hi} a_k z^(k - lo) in extended double-double by Horner taken
@@ -627,16 +722,7 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
   } else {
     h = isum_from(P.b[hi], 0.0);
   }
-  int j = P.piece_first[hi >> P.log2_piece];
-  while (P.piece_k0[j + 1] <= hi) ++j;
-  const iw w = iw_from(zr, CZ ? zi : 0.0);
-  if (CZ && w.split)
-    j = int_horner<CC, CZ, true>(P, h, w, hi - 1, j, lo);
-  else
-    j = int_horner<CC, CZ, false>(P, h, w, hi - 1, j, lo);
-  xdd X = xdd_from_isum(h);
-  if (X.rh != 0.0 || X.ih != 0.0) X.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
-  return X;
+  return int_tail<CC, CZ>(P, h, zr, zi, hi, lo);
 }
 
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>

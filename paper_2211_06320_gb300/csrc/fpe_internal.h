@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -21,6 +22,27 @@ namespace fpe {
 // j runs at the exactly rescaled point w_j = 2^beta[j] * z.
 constexpr int kLog2PieceLen = 7;       // FP64 coefficients
 constexpr int kLog2PieceLenF32 = 5;    // FP32 coefficients: keeps b_k and partial sums inside FP32 range
+
+// Packed integer copy of the FPE coefficients, read by the integer-pipe
+// window sums: each component (-1)^s m 2^e (m < 2^53) is a 54-bit
+// two's-complement mantissa in bits 0..53 and e + kQBias in bits 54..63, so
+// the device gets (mantissa, exponent) with two shifts.  Kept coefficients
+// have e in [-(T + 67) - 52, 14] (the bounds above), well inside the field;
+// a component with e < -kQBias (below 2^-459, negligible beside the other
+// component of a kept coefficient) or a zero is stored as 0.
+constexpr int kQBias = 512;
+
+// the packed word of x, or ~0 when x's exponent does not fit the field
+inline uint64_t qpack(double x) {
+  if (x == 0.0) return 0;
+  int ex;
+  const double f = std::frexp(x, &ex);  // x = f 2^ex, 0.5 <= |f| < 1
+  const long long m = (long long)std::ldexp(f, 53);  // exact
+  const int e = ex - 53;
+  if (e < -kQBias) return 0;
+  if (e >= kQBias) return ~(uint64_t)0;
+  return ((uint64_t)(e + kQBias) << 54) | ((uint64_t)m & ((1ull << 54) - 1));
+}
 
 // Bucketing of points by log2|z| before summation (points of similar modulus
 // get similar windows; §8.1 suggests grouping evaluations of similar size).
@@ -50,6 +72,7 @@ struct DevPoly {
                                // complex: interleaved (re, im); real: one double
   const double *b_full;        // every coefficient, same layout (Horner baselines)
   const float *bf;             // FPE_FP32: the FPE coefficients rounded to FP32 (same layout)
+  const uint64_t *bq;          // the FPE coefficients packed by qpack (same layout; FP64 modes)
   const int32_t *piece_k0;     // npieces + 1 entries, last = D + 1
   const int32_t *piece_beta;   // integer slope of rho on the piece
   const int32_t *piece_delta;  // exponent shift applied to h when entering piece j from j + 1

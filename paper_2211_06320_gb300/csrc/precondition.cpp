@@ -394,9 +394,20 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
     }
   }
 
+  std::vector<uint64_t> bq;
   if (fp32) {  // the p-bit representation of the kept coefficients (Thm. equivAlgo's tilde a_k)
     bf.resize(b.size());
     for (size_t i = 0; i < b.size(); ++i) bf[i] = (float)b[i];
+  } else {  // integer-pipe copy for the window sums
+    bq.resize(b.size());
+    for (size_t i = 0; i < b.size(); ++i) {
+      bq[i] = qpack(b[i]);
+      if (bq[i] == ~(uint64_t)0) {
+        set_error("fpe_precondition: a rescaled coefficient is outside the packed exponent range");
+        free_handle(P);
+        return FPE_ERR_UNSUPPORTED;
+      }
+    }
   }
 
   // a_0 for z = 0 (§4.2: P(0) = a_0), normalised
@@ -420,6 +431,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   DevPoly &dp = P->dev;
   if (!host_only) {
     if ((st = upload(P, b, &dp.b)) != FPE_OK || (st = upload(P, bf, &dp.bf)) != FPE_OK ||
+        (st = upload(P, bq, &dp.bq)) != FPE_OK ||
         (st = upload(P, bfull, &dp.b_full)) != FPE_OK ||
         (st = upload(P, pk0, &dp.piece_k0)) != FPE_OK ||
         (st = upload(P, pbeta, &dp.piece_beta)) != FPE_OK ||
