@@ -32,6 +32,37 @@ METRIC = "polynomial evaluations/s at d=2^20 (FPE vs GPU Horner, same accuracy),
 UNIT = "evals/s"
 
 
+# DRAM bytes per launch of the window-sum kernels from one ncu capture of this
+# workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel sources it was taken on: the file records their SHA-256.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_unit_disk_d2pow20.txt")
+KERNEL_SOURCES = ["fpe_eval.cu", "fpe_device.cuh", "fpe_internal.h"]
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2211_06320_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str):
+    """(bytes per launch, note) from the ncu record, or (None, why not)."""
+    try:
+        lines = [ln.split() for ln in open(TRAFFIC_FILE) if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None, "no ncu traffic record"
+    sha = kernel_sources_sha()
+    for parts in lines:
+        if len(parts) >= 3 and parts[0] == kernel:
+            if parts[2] != sha:
+                return None, "ncu traffic record predates the current kernel sources"
+            return float(parts[1]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one full-size launch"
+    return None, "no ncu traffic record for " + kernel
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,8 +341,10 @@ def main():
         dom = max(kern, key=lambda k: kern[k][0])
         ms, fl = kern[dom]
         achieved = fl / (ms * 1e-3) / 1e12
+        traffic, traffic_note = measured_traffic(dom)
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                    "traffic_source": traffic_note,
                     "peak_source": "measured: fpe_measure_fma_peak(64) on this GPU in this run (FP64 FMA x2)",
                     "share": {k: (v[0] * args.steps) / max(k_all, 1e-9) for k, v in kern.items()},
                     "all_window_kernels_frac": ((fl_short + fl_long) / ((k_short + k_long + k_fin) / args.steps

@@ -726,7 +726,7 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
 }
 
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
-__global__ void __launch_bounds__(128) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table, int n,
+__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table, int n,
                                                    const PointRec *__restrict__ rec, fpe_xc64 *__restrict__ out,
                                                    int32_t *nterms, int32_t *bits_lost) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,7 +800,7 @@ __device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
 }
 
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
-__global__ void __launch_bounds__(128) k_sum_groups(DevPoly P0, const DevPoly *__restrict__ table,
+__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(DevPoly P0, const DevPoly *__restrict__ table,
                                                     const PointRec *__restrict__ rec,
                                                     const int32_t *__restrict__ long_list,
                                                     const int32_t *__restrict__ long_ngroups,
@@ -930,7 +930,7 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
   }
   {
     ProfScope ps("k_sum_groups", st);
-    k_sum_groups<CC, CZ, ACC, F32, false><<<num_sms() * 4, 128, 0, st>>>(
+    k_sum_groups<CC, CZ, ACC, F32, false><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
         P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
         w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
   }
@@ -1107,7 +1107,7 @@ static void launch_batch_sums(fpe_batch_s *B, fpe_xc64 *out, int32_t *nterms, cu
   }
   {
     ProfScope ps("k_sum_groups", st);
-    k_sum_groups<CC, CZ, ACC, F32, true><<<num_sms() * 4, 128, 0, st>>>(
+    k_sum_groups<CC, CZ, ACC, F32, true><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
         DevPoly{}, B->d_table, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
         B->d_cnt, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
   }
@@ -1306,7 +1306,7 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
   do {                                                                                                         \
     k_sum_short<CCv, CZv, ACCv, F32v, false>                                                                   \
         <<<(ni + 127) / 128, 128, 0, st>>>(P->dev, nullptr, ni, w.rec, out, nterms, bits_lost);                \
-    k_sum_groups<CCv, CZv, ACCv, F32v, false><<<num_sms() * 4, 128, 0, st>>>(                                 \
+    k_sum_groups<CCv, CZv, ACCv, F32v, false><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(                                 \
         P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,       \
         w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                          \
     k_finalize_long<false><<<num_sms() * 2, 128, 0, st>>>(                                                     \

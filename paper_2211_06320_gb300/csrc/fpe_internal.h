@@ -44,6 +44,14 @@ inline uint64_t qpack(double x) {
   return ((uint64_t)(e + kQBias) << 54) | ((uint64_t)m & ((1ull << 54) - 1));
 }
 
+// Resident 128-thread blocks per SM asked of the window-sum kernels (caps
+// their registers at 65536 / (128 * this)); k_sum_groups is launched with
+// exactly this many blocks per SM.
+#ifndef FPE_SUM_BLOCKS_PER_SM
+#define FPE_SUM_BLOCKS_PER_SM 4
+#endif
+constexpr int kSumBlocksPerSm = FPE_SUM_BLOCKS_PER_SM;
+
 // Bucketing of points by log2|z| before summation (points of similar modulus
 // get similar windows; §8.1 suggests grouping evaluations of similar size).
 constexpr int kNumBins = 4096;

@@ -359,15 +359,40 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
       int64_t len = pk0[j + 1] - pk0[j];
       pdelta[j] = (j + 1 < np) ? (int32_t)(prho0[j + 1] - prho0[j] - (int64_t)pbeta[j] * len) : 0;
     }
+    // Merge a piece into its predecessor when the cut changes nothing: same
+    // slope and no exponent jump, so rho continues as the same integer line
+    // (an integer cover slope, e.g. a flat cover, never drifts from it).
+    // The stored b_k are unchanged; the summation loops see fewer crossings.
+    {
+      int m = 0;
+      for (int j = 1; j < np; ++j) {
+        if (pbeta[j] == pbeta[m] && pdelta[m] == 0) {
+          pdelta[m] = pdelta[j];  // the merged piece ends where piece j ended
+        } else {
+          ++m;
+          pk0[m] = pk0[j];
+          pbeta[m] = pbeta[j];
+          prho0[m] = prho0[j];
+          pdelta[m] = pdelta[j];
+        }
+      }
+      const int nm = np > 0 ? m + 1 : 0;
+      pk0[nm] = (int32_t)(D + 1);
+      pk0.resize(nm + 1);
+      pbeta.resize(nm);
+      prho0.resize(nm);
+      pdelta.resize(nm);
+    }
+    const int npm = (int)pbeta.size();
     int64_t nblk = D / kPieceLen + 1;
     pfirst.resize(nblk + 1);
     int j = 0;
     for (int64_t g = 0; g <= nblk; ++g) {
       int64_t start = g * kPieceLen;
-      while (j + 1 < np && pk0[j + 1] <= start) ++j;
+      while (j + 1 < npm && pk0[j + 1] <= start) ++j;
       pfirst[g] = j;
     }
-    P->dev.npieces = np;
+    P->dev.npieces = npm;
   }
 
   // coefficients b_k = a_k 2^-rho(k), trimmed; bad ones zeroed in b
