@@ -352,7 +352,8 @@ def main():
                     "whole_step_frac": (fl_short + fl_long) / (float(step_ms.mean()) * 1e-3) / 1e12 / peak_tflops,
                     "flops_per_launch": fl, "launch_ms": ms,
                     "algorithmic_flops": "8 per kept complex term (4 FMA: one complex multiply-add of "
-                                         "Horner's scheme on G_p cap [l, r])"}
+                                         "Horner's scheme on G_p cap [l, r])",
+                    "fma_issued_per_term": "4 at or above the peak term, 5 below it (blocks of four)"}
         extras["roofline"] = roofline
         extras["gpu_launches"] = int(launches)
         extras["avg_kept_terms"] = float(nt.mean())

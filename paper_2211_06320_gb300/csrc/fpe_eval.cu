@@ -9,22 +9,22 @@
 //   k_scatter   points to bucketed order (points of similar |z| together, so a
 //               warp's lanes get windows of similar length and position);
 //               long windows listed separately.
-//   k_sum_short one thread per point: the window's sum on the rescaled
-//               coefficients b_k, then the power z^(k_lambda - 1 + v) in
-//               extended double-double (§8.2).
-//   k_sum_groups   windows longer than kLongWindow: warp groups of 32 lane
-//               chunks, combined by a shuffle tree with powers of z^chunk.
-//   k_finalize_long  one thread per long window: combines its groups and
-//               applies the power z^(l + v).
+//   k_sums      all window sums in one persistent launch: warps take work
+//               items from a counter, first the warp groups of long windows
+//               (32 lane chunks of one window), then 32 bucketed points each
+//               (one thread per short window); the last group of a long
+//               window combines its groups and applies z^(l + v).
 //
 // Summation order.  The terms of a window peak at k_lambda.  Horner's scheme
 // is accurate when each step adds a term no smaller than the ones already
 // summed, so the window is summed in two parts that both move toward the
 // peak: [k_lambda, r] top-down with multiplier z (4 FMA per complex term),
-// and [l, k_lambda - 1] bottom-up with multiplier 1/z held in double-double
-// (8 FMA per term).  Top-down over the whole window (the paper's z^l times
-// Horner) rounds a partial sum already as large as P(z) at every one of the
-// ~T/lambda steps below the peak, which in FP64 exceeds 2^-50 S(z).
+// and [l, k_lambda - 1] bottom-up with multiplier 1/z held in double-double,
+// in blocks of four (20 FMA per four terms, see window_horner_rev).
+// Top-down over the whole window (the paper's z^l times Horner) rounds a
+// partial sum already as large as P(z) at every one of the ~T/lambda steps
+// below the peak, which in FP64 exceeds 2^-50 S(z).  FPE_ACCURATE sums
+// top-down on the integer pipe in 128-bit fixed point instead.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -725,19 +725,17 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
   return int_tail<CC, CZ>(P, h, zr, zi, hi, lo);
 }
 
+// One point of a short window (L <= kLongWindow), or a special point: its
+// window's sum, then the power z^(base + v) in extended double-double.
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
-__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table, int n,
-                                                   const PointRec *__restrict__ rec, fpe_xc64 *__restrict__ out,
-                                                   int32_t *nterms, int32_t *bits_lost) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  PointRec r = rec[q];
+__device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__restrict__ table,
+                                          const PointRec &r, fpe_xc64 *__restrict__ out, int32_t *nterms,
+                                          int32_t *bits_lost) {
   const DevPoly &P = BATCH ? table[r.pid] : P0;
   fpe_xc64 o;
   if (r.flags) {
     o = special_value(P, r.flags);
   } else {
-    if (r.hi - r.lo + 1 > kLongWindow) return;  // summed by k_sum_groups
     xdd X;
     long long base = r.lo;
     if (ACC) {
@@ -793,25 +791,113 @@ __device__ __forceinline__ xdd shfl_up_xdd(xdd x, int s) {
 //   chunk holding the peak:   both parts, times z^(base - c_i).
 // A group's value is sum_i (z^C)^i s_i: each lane multiplies its slot by its
 // own power, then a butterfly adds the slots; lane 31's carry goes to the
-// next group.  k_finalize_long combines the groups
-// and applies z^(l + v), one point per thread.
+// next group.  The warp that finishes a window's last group combines them
+// and applies z^(l + v).
 __device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
   return g == 0 ? i : cap + gbase + g - 1;
 }
 
+// One thread per bucketed point with a short window (static blocks).
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
-__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(DevPoly P0, const DevPoly *__restrict__ table,
-                                                    const PointRec *__restrict__ rec,
-                                                    const int32_t *__restrict__ long_list,
-                                                    const int32_t *__restrict__ long_ngroups,
-                                                    const int32_t *__restrict__ long_gbase,
-                                                    const int32_t *__restrict__ extra_owner,
-                                                    const int32_t *__restrict__ extra_group, uint32_t *cnt, int cap,
-                                                    int extra_cap, xdd *__restrict__ gval, xdd *__restrict__ gcarry) {
+__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table,
+                                                                    int n, const PointRec *__restrict__ rec,
+                                                                    fpe_xc64 *__restrict__ out, int32_t *nterms,
+                                                                    int32_t *bits_lost) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const PointRec r = rec[q];
+  if (r.flags || r.hi - r.lo + 1 <= kLongWindow) sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
+}
+
+// Group g of a long window (ng groups): lane i sums its chunk, the 32 slots
+// are combined; lane 0 returns the group's value sv and carry gout.
+template <bool CC, bool CZ, bool ACC, bool F32>
+__device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, int ng, int g, int lane, xdd &sv_out,
+                                          xdd &gout_out) {
+  const long long L = r.hi - r.lo + 1;
+  const long long C = (L + 32LL * ng - 1) / (32LL * ng);
+  const long long clo = r.lo + (long long)g * 32 * C + lane * C;
+  const long long chi = min(clo + C - 1, r.hi);
+  xdd sv = xdd_zero(), carry = xdd_zero();
+  if (ACC) {
+    if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
+  } else if (clo <= chi) {
+    const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+    const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
+    const cdd u = recip_dd(mr, mi);
+    long long base;
+    xdd X = range_sum_any<CC, CZ, F32>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
+    if (chi < r.kl) {
+      carry = xdd_mul(X, xdd_from_cdd(u, -f));  // below the peak: X / z to the next slot
+    } else if (base > clo) {
+      sv = xdd_mul(X, xdd_pow_int(r.zr, r.zi, base - clo));
+    } else {
+      sv = X;
+    }
+  }
+  xdd gout = xdd_zero();
+  if (!ACC) {
+    xdd inc = shfl_up_xdd(carry, 1);
+    if (lane > 0) sv = xdd_add(sv, inc);
+    gout = shfl_down_xdd(carry, 31);  // lane 31's carry, read by lane 0
+  }
+  // sum_i (z^C)^i s_i: each lane scales its slot by its own power (integer
+  // pipe), then a butterfly adds the 32 slots with every lane busy
+  if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
+  for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
+  sv_out = sv;
+  gout_out = gout;
+}
+
+// Combine a long window's groups, sum_g (z^S)^g (val_g + carry_{g-1}) by
+// Horner from the top group, apply z^(l + v) and write the point (one lane).
+// Group values written by other SMs are read past L1 (__ldcg).
+template <bool BATCH>
+__device__ __forceinline__ void finalize_long(const DevPoly &P0, const DevPoly *__restrict__ table,
+                                              const PointRec &r, int i, int ng, int gb, int cap,
+                                              const xdd *gval, const xdd *gcarry, fpe_xc64 *__restrict__ out,
+                                              int32_t *nterms, int32_t *bits_lost) {
+  const DevPoly &P = BATCH ? table[r.pid] : P0;
+  auto ld = [](const xdd *p) {
+    xdd x;
+    x.rh = __ldcg(&p->rh);
+    x.rl = __ldcg(&p->rl);
+    x.ih = __ldcg(&p->ih);
+    x.il = __ldcg(&p->il);
+    x.e = __ldcg(&p->e);
+    return x;
+  };
+  xdd acc = ld(&gval[group_slot(i, ng - 1, gb, cap)]);
+  if (ng > 1) {
+    const long long L = r.hi - r.lo + 1;
+    const long long C = (L + 32LL * ng - 1) / (32LL * ng);
+    const xdd W = xdd_pow_int(r.zr, r.zi, 32 * C);
+    acc = xdd_add(acc, ld(&gcarry[group_slot(i, ng - 2, gb, cap)]));
+    for (int g = ng - 2; g >= 0; --g) {
+      xdd sg = ld(&gval[group_slot(i, g, gb, cap)]);
+      if (g > 0) sg = xdd_add(sg, ld(&gcarry[group_slot(i, g - 1, gb, cap)]));
+      acc = xdd_add(xdd_mul(acc, W), sg);
+    }
+  }
+  const xdd pw = xdd_pow_int(r.zr, r.zi, r.lo + P.v);
+  const fpe_xc64 o = xdd_out(xdd_mul(acc, pw));
+  out[r.orig] = o;
+  write_diag(P, r, o, nterms, bits_lost);
+}
+
+// Warp groups of the long windows, one evaluation of one polynomial:
+// persistent warps take group items from a counter and store each group's
+// value and carry; k_finalize_long combines them.
+template <bool CC, bool CZ, bool ACC, bool F32>
+__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(
+    DevPoly P, const PointRec *__restrict__ rec, const int32_t *__restrict__ long_list,
+    const int32_t *__restrict__ long_ngroups, const int32_t *__restrict__ long_gbase,
+    const int32_t *__restrict__ extra_owner, const int32_t *__restrict__ extra_group, uint32_t *cnt, int cap,
+    int extra_cap, xdd *__restrict__ gval, xdd *__restrict__ gcarry) {
   const int lane = threadIdx.x & 31;
   const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
+  // every extra slot below min(reserved, extra_cap) is written by the scatter: an owner, or -1
   const uint32_t nextra = min(*(volatile uint32_t *)&cnt[kCntExtra], (uint32_t)extra_cap);
-  // every extra slot below min(reserved, extra_cap) is written by k_scatter: an owner, or -1
   while (true) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(&cnt[kCntGroupWork], 1u);
@@ -826,40 +912,9 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(DevPoly P0,
       if (i < 0) continue;  // slot of a reservation that did not fit
       g = extra_group[t - nlong];
     }
-    const int ng = long_ngroups[i];
     const PointRec r = rec[long_list[i]];
-    const DevPoly &P = BATCH ? table[r.pid] : P0;
-    const long long L = r.hi - r.lo + 1;
-    const long long C = (L + 32LL * ng - 1) / (32LL * ng);
-    const long long clo = r.lo + (long long)g * 32 * C + lane * C;
-    const long long chi = min(clo + C - 1, r.hi);
-    xdd sv = xdd_zero(), carry = xdd_zero();
-    if (ACC) {
-      if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
-    } else if (clo <= chi) {
-      const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
-      const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
-      const cdd u = recip_dd(mr, mi);
-      long long base;
-      xdd X = range_sum_any<CC, CZ, F32>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
-      if (chi < r.kl) {
-        carry = xdd_mul(X, xdd_from_cdd(u, -f));  // below the peak: X / z to the next slot
-      } else if (base > clo) {
-        sv = xdd_mul(X, xdd_pow_int(r.zr, r.zi, base - clo));
-      } else {
-        sv = X;
-      }
-    }
-    xdd gout = xdd_zero();
-    if (!ACC) {
-      xdd inc = shfl_up_xdd(carry, 1);
-      if (lane > 0) sv = xdd_add(sv, inc);
-      gout = shfl_down_xdd(carry, 31);  // lane 31's carry, read by lane 0
-    }
-    // sum_i (z^C)^i s_i: each lane scales its slot by its own power (integer
-    // pipe), then a butterfly adds the 32 slots with every lane busy
-    if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
-    for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
+    xdd sv, gout;
+    sum_group<CC, CZ, ACC, F32>(P, r, long_ngroups[i] & 0xffff, g, lane, sv, gout);
     if (lane == 0) {
       const int slot = group_slot(i, g, long_gbase[i], cap);
       gval[slot] = sv;
@@ -868,38 +923,93 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(DevPoly P0,
   }
 }
 
-// One thread per long-window point: sum_g (z^S)^g (val_g + carry_{g-1}) by
-// Horner from the top group, then times z^(l + v).
-template <bool BATCH>
-__global__ void __launch_bounds__(128) k_finalize_long(DevPoly P0, const DevPoly *__restrict__ table,
-                                                       const PointRec *__restrict__ rec,
+// One thread per long window: combine its groups and write the point.
+__global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec *__restrict__ rec,
                                                        const int32_t *__restrict__ long_list,
                                                        const int32_t *__restrict__ long_ngroups,
-                                                       const int32_t *__restrict__ long_gbase, uint32_t *cnt,
+                                                       const int32_t *__restrict__ long_gbase, const uint32_t *cnt,
                                                        int cap, const xdd *__restrict__ gval,
                                                        const xdd *__restrict__ gcarry, fpe_xc64 *__restrict__ out,
                                                        int32_t *nterms, int32_t *bits_lost) {
-  const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
+  const uint32_t nlong = *(volatile const uint32_t *)&cnt[kCntLong];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nlong; i += gridDim.x * blockDim.x) {
     const PointRec r = rec[long_list[i]];
+    finalize_long<false>(P, nullptr, r, (int)i, long_ngroups[i] & 0xffff, long_gbase[i], cap, gval, gcarry, out,
+                         nterms, bits_lost);
+  }
+}
+
+// All window sums of one evaluation in one persistent launch.// All window sums of one batched evaluation in one persistent launch (the
+// single-polynomial path uses k_sum_short, k_sum_groups, k_finalize_long,
+// which measured faster there).  Each warp
+// takes work items from a counter:
+//   first the warp groups of the long windows (the largest items), a group
+//   being 32 lane chunks of one window (see above);
+//   then 32 consecutive bucketed points each, one per lane, whose short
+//   windows (or special values) fill the tail.
+// A window with one group is finished by the warp that sums it.  Otherwise
+// each group stores its value, fences, and counts itself done in the upper
+// 16 bits of long_ngroups[i]; the warp that completes the count combines the
+// groups and writes the point.  No warp ever waits for another.
+template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
+__global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
+    DevPoly P0, const DevPoly *__restrict__ table, int n, const PointRec *__restrict__ rec,
+    const int32_t *__restrict__ long_list, int32_t *long_ngroups, const int32_t *__restrict__ long_gbase,
+    const int32_t *__restrict__ extra_owner, const int32_t *__restrict__ extra_group, uint32_t *cnt, int cap,
+    int extra_cap, xdd *gval, xdd *gcarry, fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
+  // every extra slot below min(reserved, extra_cap) is written by the scatter: an owner, or -1
+  const uint32_t nextra = min(*(volatile uint32_t *)&cnt[kCntExtra], (uint32_t)extra_cap);
+  const uint32_t ngroup_items = nlong + nextra;
+  const uint32_t nitems = ngroup_items + (uint32_t)((n + 31) / 32);
+  while (true) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&cnt[kCntGroupWork], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= nitems) break;
+    if (t >= ngroup_items) {  // 32 short-window points
+      const long long q = (long long)(t - ngroup_items) * 32 + lane;
+      if (q < n) {
+        const PointRec r = rec[q];
+        if (r.flags || r.hi - r.lo + 1 <= kLongWindow)
+          sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
+      }
+      continue;
+    }
+    int i, g;
+    if (t < nlong) {
+      i = (int)t;
+      g = 0;
+    } else {
+      i = extra_owner[t - nlong];
+      if (i < 0) continue;  // slot of a reservation that did not fit
+      g = extra_group[t - nlong];
+    }
+    const int ng = *(volatile int32_t *)&long_ngroups[i] & 0xffff;
+    const PointRec r = rec[long_list[i]];
     const DevPoly &P = BATCH ? table[r.pid] : P0;
-    const int ng = long_ngroups[i], gb = long_gbase[i];
-    xdd acc = gval[group_slot(i, ng - 1, gb, cap)];
-    if (ng > 1) {
-      const long long L = r.hi - r.lo + 1;
-      const long long C = (L + 32LL * ng - 1) / (32LL * ng);
-      const xdd W = xdd_pow_int(r.zr, r.zi, 32 * C);
-      acc = xdd_add(acc, gcarry[group_slot(i, ng - 2, gb, cap)]);
-      for (int g = ng - 2; g >= 0; --g) {
-        xdd sg = gval[group_slot(i, g, gb, cap)];
-        if (g > 0) sg = xdd_add(sg, gcarry[group_slot(i, g - 1, gb, cap)]);
-        acc = xdd_add(xdd_mul(acc, W), sg);
+    xdd sv, gout;
+    sum_group<CC, CZ, ACC, F32>(P, r, ng, g, lane, sv, gout);
+    if (lane == 0) {
+      if (ng == 1) {  // the whole window: finish it here
+        const xdd pw = xdd_pow_int(r.zr, r.zi, r.lo + P.v);
+        const fpe_xc64 o = xdd_out(xdd_mul(sv, pw));
+        out[r.orig] = o;
+        write_diag(P, r, o, nterms, bits_lost);
+      } else {
+        const int gb = long_gbase[i];
+        const int slot = group_slot(i, g, gb, cap);
+        gval[slot] = sv;
+        gcarry[slot] = gout;
+        __threadfence();  // the group's value is visible before it is counted
+        const int done = atomicAdd(&long_ngroups[i], 1 << 16) >> 16;
+        if (done == ng - 1) {
+          __threadfence();
+          finalize_long<BATCH>(P0, table, r, i, ng, gb, cap, gval, gcarry, out, nterms, bits_lost);
+        }
       }
     }
-    const xdd pw = xdd_pow_int(r.zr, r.zi, r.lo + P.v);
-    const fpe_xc64 o = xdd_out(xdd_mul(acc, pw));
-    out[r.orig] = o;
-    write_diag(P, r, o, nterms, bits_lost);
   }
 }
 
@@ -923,23 +1033,23 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
                          cudaStream_t st) {
   Workspace &w = P->ws;
   const int cap = (int)w.cap, xcap = (int)w.extra_cap;
+  uint32_t *cnt = w.bins + 2 * kNumBins;
   {
     ProfScope ps("k_sum_short", st);
-    k_sum_short<CC, CZ, ACC, F32, false>
-        <<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms, bits_lost);
+    k_sum_short<CC, CZ, ACC, F32, false><<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms,
+                                                                          bits_lost);
   }
   {
     ProfScope ps("k_sum_groups", st);
-    k_sum_groups<CC, CZ, ACC, F32, false><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
-        P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
-        w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
+    k_sum_groups<CC, CZ, ACC, F32><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
+        P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group, cnt, cap, xcap,
+        (xdd *)w.group_val, (xdd *)w.group_carry);
   }
   {
     ProfScope ps("k_finalize_long", st);
-    k_finalize_long<false><<<num_sms() * 2, 128, 0, st>>>(P->dev, nullptr, w.rec, w.long_list, w.long_ngroups,
-                                                          w.long_gbase, w.bins + 2 * kNumBins, cap,
-                                                          (const xdd *)w.group_val, (const xdd *)w.group_carry,
-                                                          out, nterms, bits_lost);
+    k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, cnt,
+                                                   cap, (const xdd *)w.group_val, (const xdd *)w.group_carry, out,
+                                                   nterms, bits_lost);
   }
 }
 
@@ -1099,25 +1209,11 @@ __global__ void k_scatter_batch(const DevPoly *__restrict__ table, const int32_t
 template <bool CC, bool CZ, bool ACC, bool F32>
 static void launch_batch_sums(fpe_batch_s *B, fpe_xc64 *out, int32_t *nterms, cudaStream_t st) {
   Workspace &w = B->ws;
-  const int n = (int)B->ntotal, cap = (int)w.cap, xcap = (int)w.extra_cap;
-  {
-    ProfScope ps("k_sum_short", st);
-    k_sum_short<CC, CZ, ACC, F32, true>
-        <<<(n + 127) / 128, 128, 0, st>>>(DevPoly{}, B->d_table, n, w.rec, out, nterms, nullptr);
-  }
-  {
-    ProfScope ps("k_sum_groups", st);
-    k_sum_groups<CC, CZ, ACC, F32, true><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
-        DevPoly{}, B->d_table, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
-        B->d_cnt, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);
-  }
-  {
-    ProfScope ps("k_finalize_long", st);
-    k_finalize_long<true><<<num_sms() * 2, 128, 0, st>>>(DevPoly{}, B->d_table, w.rec, w.long_list,
-                                                         w.long_ngroups, w.long_gbase, B->d_cnt, cap,
-                                                         (const xdd *)w.group_val, (const xdd *)w.group_carry, out,
-                                                         nterms, nullptr);
-  }
+  ProfScope ps("k_sums", st);
+  k_sums<CC, CZ, ACC, F32, true><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
+      DevPoly{}, B->d_table, (int)B->ntotal, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
+      w.extra_group, B->d_cnt, (int)w.cap, (int)w.extra_cap, (xdd *)w.group_val, (xdd *)w.group_carry, out, nterms,
+      nullptr);
 }
 
 fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
@@ -1306,12 +1402,12 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
   do {                                                                                                         \
     k_sum_short<CCv, CZv, ACCv, F32v, false>                                                                   \
         <<<(ni + 127) / 128, 128, 0, st>>>(P->dev, nullptr, ni, w.rec, out, nterms, bits_lost);                \
-    k_sum_groups<CCv, CZv, ACCv, F32v, false><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(                                 \
-        P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,       \
+    k_sum_groups<CCv, CZv, ACCv, F32v><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(                           \
+        P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,                \
         w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                          \
-    k_finalize_long<false><<<num_sms() * 2, 128, 0, st>>>(                                                     \
-        P->dev, nullptr, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.bins + 2 * kNumBins, cap,         \
-        (const xdd *)w.group_val, (const xdd *)w.group_carry, out, nterms, bits_lost);                         \
+    k_finalize_long<<<num_sms() * 2, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase,   \
+                                                   w.bins + 2 * kNumBins, cap, (const xdd *)w.group_val,       \
+                                                   (const xdd *)w.group_carry, out, nterms, bits_lost);        \
   } while (0)
       const bool f32 = P->dev.fp32 != 0;
       if (cc && cz) {

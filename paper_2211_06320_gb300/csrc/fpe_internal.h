@@ -45,8 +45,8 @@ inline uint64_t qpack(double x) {
 }
 
 // Resident 128-thread blocks per SM asked of the window-sum kernels (caps
-// their registers at 65536 / (128 * this)); k_sum_groups is launched with
-// exactly this many blocks per SM.
+// their registers at 65536 / (128 * this)); the persistent ones
+// (k_sum_groups, k_sums) are launched with exactly this many blocks per SM.
 #ifndef FPE_SUM_BLOCKS_PER_SM
 #define FPE_SUM_BLOCKS_PER_SM 4
 #endif
