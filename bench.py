@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--points", type=int, default=1 << 20)
     ap.add_argument("--degree", type=int, default=1 << 20)
     ap.add_argument("--no-extras", action="store_true", help="skip Horner baselines, accuracy and CPU legs")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters (no autotuning)")
     return ap.parse_args()
 
 
@@ -170,6 +171,7 @@ def batched_leg(F, torch, st):
         polys = [F.fpe_precondition(w.coeffs.re, w.coeffs.im, None, p, flags) for w in wls]
         res[f"{name}_precondition_s"] = time.perf_counter() - t0
         B = F.fpe_batch_create(polys, offs)
+        res[f"{name}_tuning"] = F.fpe_batch_autotune(B, zr, zi)
         out = F.empty_out(B.n)
         F.fpe_batch_eval(B, zr, zi, out=out)
         F.fpe_batch_sync(B)
@@ -283,6 +285,11 @@ def main():
     nterms = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
+    # launch parameters of the window sums picked by the library's autotuner on
+    # this rank's points (before the timed region, like the preconditioning)
+    t0 = time.perf_counter()
+    tuning = F.fpe_autotune(P, zr, zi) if not args.no_tune else F.fpe_get_tuning(P)
+    t_tune = time.perf_counter() - t0
 
     def barrier():
         if world > 1:
@@ -331,7 +338,7 @@ def main():
     if rank == 0:
         # roofline of the dominant kernel: algorithmic FP64 flops of the kept terms
         # (8 per complex x complex term, eq. complexityAlgo's Horner part) / its event time
-        long_mask = L > 4096
+        long_mask = L > tuning["long_window"]
         fl_short = 8.0 * float(nt[~long_mask].sum())
         fl_long = 8.0 * float(nt[long_mask].sum())
         fma_peak = F.fpe_measure_fma_peak(64, 5)
@@ -359,6 +366,7 @@ def main():
         extras["avg_kept_terms"] = float(nt.mean())
         extras["avg_window"] = float(L.mean())
         extras["precondition_ms"] = t_pre * 1e3
+        extras["tuning"] = dict(tuning, autotune_s=t_tune, autotuned=not args.no_tune)
         extras["wall_s_timed_region"] = wall
 
         # end to end through the C ABI with host buffers (pinned), copies inside the timed region

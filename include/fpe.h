@@ -181,9 +181,10 @@ fpe_status fpe_eval_deriv(fpe_poly_t P, const double *z_re, const double *z_im, 
                           void *cuda_stream);
 
 /*
- * Batched evaluation -- many polynomials, each at its own points, in one fixed
- * sequence of kernel launches (§8.1: the algorithm is embarrassingly parallel
- * over points).
+ * Batched evaluation -- many polynomials, each at its own points (§8.1: the
+ * algorithm is embarrassingly parallel over points): three kernels locate,
+ * bucket and scatter the points, then one persistent launch does every
+ * window sum from a device work counter.
  *
  * fpe_batch_create builds a batch over npoly handles (all on one device, all
  * real or all complex, the same FPE_FP32 and FPE_ACCURATE flags; otherwise
@@ -213,6 +214,45 @@ fpe_status fpe_batch_sync(fpe_batch_t B, void *cuda_stream);
 void fpe_batch_destroy(fpe_batch_t B);
 fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,
                           const double *z_im, fpe_xc64 *out, void *cuda_stream);
+
+/*
+ * Launch parameters of the window sums, and an autotuner for them (the paper
+ * has no counterpart: they only schedule the same terms).
+ *
+ * A point whose window has more than long_window terms is summed by warp
+ * groups: 32 lane chunks of at most lane_chunk terms each, combined by
+ * shuffles, several groups per window when it is longer than 32 lane_chunk;
+ * shorter windows take one thread each (32 points per warp).  Every setting
+ * keeps the error bounds of fpe_eval; the order of the additions inside a
+ * window changes, so values may differ in the last bits.  Defaults: 4096 and
+ * 1024.
+ *
+ * fpe_set_tuning, fpe_batch_set_tuning: long_window in [32, 2^24],
+ *   lane_chunk in [16, 2^16], else FPE_ERR_INVALID_ARG; t->ms is ignored.
+ *   The setting applies to later evaluations of that handle or batch.
+ * fpe_get_tuning: the handle's current setting (ms = 0 unless it came from
+ *   fpe_autotune).
+ * fpe_autotune: times fpe_eval on the caller's n device points (z_re, z_im
+ *   as in fpe_eval) at every setting of the grid long_window in {1024, 2048,
+ *   4096, 8192} x lane_chunk in {256, 512, 1024, 2048}: one untimed call,
+ *   then two calls between CUDA events on cuda_stream.  Keeps the fastest in
+ *   the handle and returns it in *best (ms = its time per call).
+ *   Synchronous; allocates and frees a temporary output array.  Errors as
+ *   fpe_eval, FPE_ERR_INVALID_ARG for a NULL best.
+ * fpe_batch_autotune: the same for a batch over its own points.
+ */
+typedef struct {
+  int64_t long_window;
+  int64_t lane_chunk;
+  double ms;
+} fpe_tuning;
+fpe_status fpe_set_tuning(fpe_poly_t P, const fpe_tuning *t);
+fpe_status fpe_get_tuning(fpe_poly_t P, fpe_tuning *t);
+fpe_status fpe_autotune(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, void *cuda_stream,
+                        fpe_tuning *best);
+fpe_status fpe_batch_set_tuning(fpe_batch_t B, const fpe_tuning *t);
+fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z_im, void *cuda_stream,
+                              fpe_tuning *best);
 
 /*
  * fpe_newton -- one Newton step N_P(z) = z - P(z)/P'(z) (§7.2, eq. newton) at n

@@ -39,6 +39,7 @@ EXPORTED = [
     "fpe_status_string", "fpe_last_error", "fpe_profile_enable", "fpe_profile_reset", "fpe_profile_read",
     "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
     "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex", "fpe_analyse",
+    "fpe_set_tuning", "fpe_get_tuning", "fpe_autotune", "fpe_batch_set_tuning", "fpe_batch_autotune",
 ]
 
 
@@ -50,6 +51,14 @@ class FpeError(RuntimeError):
 
 class XC64(ctypes.Structure):
     _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double), ("e", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    """fpe_tuning: launch parameters of the window sums."""
+    _fields_ = [("long_window", ctypes.c_int64), ("lane_chunk", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"long_window": int(self.long_window), "lane_chunk": int(self.lane_chunk), "ms": float(self.ms)}
 
 
 _lib = None
@@ -95,6 +104,11 @@ def _load():
         "fpe_grad_coeffs": ([P, P, P, I64, P, P, P, P, P], I32),
         "fpe_to_complex": ([P, I64, P, P, P], I32),
         "fpe_analyse": ([P, P, P, I64], I32),
+        "fpe_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "fpe_get_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "fpe_autotune": ([P, P, P, I64, P, ctypes.POINTER(Tuning)], I32),
+        "fpe_batch_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "fpe_batch_autotune": ([P, P, P, P, ctypes.POINTER(Tuning)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -365,6 +379,38 @@ def fpe_batch_eval(B: Batch, z_re, z_im=None, out=None, nterms=None, stream=None
 
 def fpe_batch_sync(B: Batch, stream=None):
     _check(_load().fpe_batch_sync(B._h, _stream(stream)), "fpe_batch_sync")
+
+
+def fpe_set_tuning(P: Poly, long_window: int, lane_chunk: int):
+    t = Tuning(long_window, lane_chunk, 0.0)
+    _check(_load().fpe_set_tuning(P.handle, ctypes.byref(t)), "fpe_set_tuning")
+
+
+def fpe_get_tuning(P: Poly) -> dict:
+    t = Tuning()
+    _check(_load().fpe_get_tuning(P.handle, ctypes.byref(t)), "fpe_get_tuning")
+    return t.as_dict()
+
+
+def fpe_autotune(P: Poly, z_re, z_im=None, stream=None) -> dict:
+    """Time fpe_eval over the tuning grid on these device points; the fastest
+    setting stays in the handle and is returned."""
+    t = Tuning()
+    _check(_load().fpe_autotune(P.handle, _dptr(z_re), _dptr(z_im), int(z_re.shape[0]), _stream(stream),
+                                ctypes.byref(t)), "fpe_autotune")
+    return t.as_dict()
+
+
+def fpe_batch_set_tuning(B: Batch, long_window: int, lane_chunk: int):
+    t = Tuning(long_window, lane_chunk, 0.0)
+    _check(_load().fpe_batch_set_tuning(B._h, ctypes.byref(t)), "fpe_batch_set_tuning")
+
+
+def fpe_batch_autotune(B: Batch, z_re, z_im=None, stream=None) -> dict:
+    t = Tuning()
+    _check(_load().fpe_batch_autotune(B._h, _dptr(z_re), _dptr(z_im), _stream(stream), ctypes.byref(t)),
+           "fpe_batch_autotune")
+    return t.as_dict()
 
 
 def fpe_newton(P: Poly, z_re, z_im=None, inc=None, z_next_re=None, z_next_im=None, stream=None):

@@ -74,6 +74,66 @@ struct DeviceGuard {
 
 using namespace fpe;
 
+// ---------------------------------------------------------------------------
+// launch parameters and the autotuner
+// ---------------------------------------------------------------------------
+
+static fpe_status check_tuning(const fpe_tuning *t) {
+  if (!t || t->long_window < 32 || t->long_window > (1 << 24) || t->lane_chunk < 16 || t->lane_chunk > (1 << 16)) {
+    set_error("tuning: need long_window in [32, 2^24] and lane_chunk in [16, 2^16]");
+    return FPE_ERR_INVALID_ARG;
+  }
+  return FPE_OK;
+}
+
+// Time run() at every setting of the grid, keep the fastest in tune.
+template <class Run>
+static fpe_status autotune_grid(Tuning &tune, double &tune_ms, Run run, cudaStream_t st, fpe_tuning *best) {
+  static const int64_t kLW[] = {1024, 2048, 4096, 8192};
+  static const int64_t kLC[] = {256, 512, 1024, 2048};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  const Tuning keep = tune;
+  Tuning pick = keep;
+  double pick_ms = -1.0;
+  fpe_status s = FPE_OK;
+  for (int64_t lw : kLW) {
+    for (int64_t lc : kLC) {
+      tune.long_window = lw;
+      tune.lane_chunk = lc;
+      if ((s = run()) != FPE_OK) break;  // untimed
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+      if ((s = run()) != FPE_OK || (s = run()) != FPE_OK) break;
+      if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      if (pick_ms < 0.0 || ms / 2.0 < pick_ms) {
+        pick_ms = ms / 2.0;
+        pick = tune;
+      }
+    }
+    if (s != FPE_OK || e != cudaSuccess) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == FPE_OK && e != cudaSuccess) s = cuda_fail(e, "fpe_autotune timing");
+  if (s != FPE_OK) {
+    tune = keep;
+    return s;
+  }
+  tune = pick;
+  tune_ms = pick_ms;
+  best->long_window = pick.long_window;
+  best->lane_chunk = pick.lane_chunk;
+  best->ms = pick_ms;
+  return FPE_OK;
+}
+
 extern "C" {
 
 fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e2, int64_t n_coef, int p,
@@ -254,6 +314,82 @@ void fpe_batch_destroy(fpe_batch_t B) {
   free_workspace(B->ws);
   if (prev >= 0) cudaSetDevice(prev);
   delete B;
+}
+
+fpe_status fpe_set_tuning(fpe_poly_t P, const fpe_tuning *t) {
+  if (!P) {
+    set_error("fpe_set_tuning: NULL handle");
+    return FPE_ERR_INVALID_ARG;
+  }
+  fpe_status s = check_tuning(t);
+  if (s != FPE_OK) return s;
+  P->tune.long_window = t->long_window;
+  P->tune.lane_chunk = t->lane_chunk;
+  P->tune_ms = 0.0;
+  return FPE_OK;
+}
+
+fpe_status fpe_get_tuning(fpe_poly_t P, fpe_tuning *t) {
+  if (!P || !t) {
+    set_error("fpe_get_tuning: NULL handle or output");
+    return FPE_ERR_INVALID_ARG;
+  }
+  t->long_window = P->tune.long_window;
+  t->lane_chunk = P->tune.lane_chunk;
+  t->ms = P->tune_ms;
+  return FPE_OK;
+}
+
+fpe_status fpe_autotune(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, void *cuda_stream,
+                        fpe_tuning *best) {
+  fpe_tuning dummy;
+  fpe_status s = check_eval_args(P, z_re, n, &dummy);
+  if (s != FPE_OK) return s;
+  if (!best || n == 0) {
+    set_error("fpe_autotune: need best != NULL and n > 0");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(P->device);
+  fpe_xc64 *out = nullptr;
+  cudaError_t e = cudaMalloc((void **)&out, n * sizeof(fpe_xc64));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(autotune)");
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  s = autotune_grid(P->tune, P->tune_ms,
+                    [&]() { return launch_eval(P, z_re, z_im, n, out, nullptr, nullptr, st); }, st, best);
+  cudaStreamSynchronize(st);
+  cudaFree(out);
+  return s;
+}
+
+fpe_status fpe_batch_set_tuning(fpe_batch_t B, const fpe_tuning *t) {
+  if (!B) {
+    set_error("fpe_batch_set_tuning: NULL batch");
+    return FPE_ERR_INVALID_ARG;
+  }
+  fpe_status s = check_tuning(t);
+  if (s != FPE_OK) return s;
+  B->tune.long_window = t->long_window;
+  B->tune.lane_chunk = t->lane_chunk;
+  return FPE_OK;
+}
+
+fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z_im, void *cuda_stream,
+                              fpe_tuning *best) {
+  if (!B || !best || B->ntotal == 0 || !z_re) {
+    set_error("fpe_batch_autotune: NULL batch, points or output, or an empty batch");
+    return FPE_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(B->device);
+  fpe_xc64 *out = nullptr;
+  cudaError_t e = cudaMalloc((void **)&out, B->ntotal * sizeof(fpe_xc64));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(autotune)");
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  double ms = 0.0;
+  fpe_status s = autotune_grid(B->tune, ms, [&]() { return launch_batch(B, z_re, z_im, out, nullptr, st); }, st,
+                               best);
+  cudaStreamSynchronize(st);
+  cudaFree(out);
+  return s;
 }
 
 fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_offsets, const double *z_re,

@@ -192,12 +192,12 @@ __global__ void k_scan_bins(uint32_t *bins) {
 // slot i (its list index), groups 1.. in extra slots; when the extra slots run
 // out the window gets one group and the slots of its failed reservation that
 // exist are marked unused (-1).
-__device__ __forceinline__ void list_long_window(long long L, uint32_t pos, uint32_t *cnt, int32_t *long_list,
-                                                 int32_t *long_ngroups, int32_t *long_gbase, int32_t *extra_owner,
-                                                 int32_t *extra_group, int extra_cap) {
+__device__ __forceinline__ void list_long_window(long long L, long long span, uint32_t pos, uint32_t *cnt,
+                                                 int32_t *long_list, int32_t *long_ngroups, int32_t *long_gbase,
+                                                 int32_t *extra_owner, int32_t *extra_group, int extra_cap) {
   uint32_t i = atomicAdd(&cnt[kCntLong], 1u);
   long_list[i] = (int32_t)pos;
-  int ng = (int)((L + kGroupSpan - 1) / kGroupSpan);
+  int ng = (int)min((L + span - 1) / span, 0x7fffLL);  // the upper 16 bits count finished groups
   int gb = 0;
   if (ng > 1) {
     gb = (int)atomicAdd(&cnt[kCntExtra], (uint32_t)(ng - 1));
@@ -223,7 +223,7 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
                           PointRec *__restrict__ rec, int32_t *__restrict__ long_list,
                           int32_t *__restrict__ long_ngroups, int32_t *__restrict__ long_gbase,
                           int32_t *__restrict__ extra_owner, int32_t *__restrict__ extra_group, int extra_cap,
-                          int32_t *status) {
+                          int32_t *status, long long long_window, long long span) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   uint32_t pos = atomicAdd(&bins[kNumBins + key[p]], 1u);
@@ -246,9 +246,9 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
   r.pid = 0;
   r.pad = 0;
   rec[pos] = r;
-  if (!r.flags && r.hi - r.lo + 1 > kLongWindow)
-    list_long_window(r.hi - r.lo + 1, pos, bins + 2 * kNumBins, long_list, long_ngroups, long_gbase, extra_owner,
-                     extra_group, extra_cap);
+  if (!r.flags && r.hi - r.lo + 1 > long_window)
+    list_long_window(r.hi - r.lo + 1, span, pos, bins + 2 * kNumBins, long_list, long_ngroups, long_gbase,
+                     extra_owner, extra_group, extra_cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -725,7 +725,7 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
   return int_tail<CC, CZ>(P, h, zr, zi, hi, lo);
 }
 
-// One point of a short window (L <= kLongWindow), or a special point: its
+// One point of a short window (L <= the long-window threshold), or a special point: its
 // window's sum, then the power z^(base + v) in extended double-double.
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
 __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__restrict__ table,
@@ -782,7 +782,7 @@ __device__ __forceinline__ xdd shfl_up_xdd(xdd x, int s) {
   return y;
 }
 
-// Long windows: warp groups.  A window of length L gets ng = ceil(L / kGroupSpan)
+// Long windows: warp groups.  A window of length L gets ng = ceil(L / (32 lane_chunk))
 // groups of S = 32 C terms with C = ceil(L / (32 ng)); lane i of group g owns
 // the chunk [c_i, c_i + C - 1], c_i = l + g S + i C, and a slot value s_i with
 //   sum over the window = z^l sum_g (z^S)^g sum_i (z^C)^i s_i:
@@ -802,11 +802,11 @@ template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
 __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table,
                                                                     int n, const PointRec *__restrict__ rec,
                                                                     fpe_xc64 *__restrict__ out, int32_t *nterms,
-                                                                    int32_t *bits_lost) {
+                                                                    int32_t *bits_lost, long long long_window) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const PointRec r = rec[q];
-  if (r.flags || r.hi - r.lo + 1 <= kLongWindow) sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
+  if (r.flags || r.hi - r.lo + 1 <= long_window) sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
 }
 
 // Group g of a long window (ng groups): lane i sums its chunk, the 32 slots
@@ -956,7 +956,8 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
     DevPoly P0, const DevPoly *__restrict__ table, int n, const PointRec *__restrict__ rec,
     const int32_t *__restrict__ long_list, int32_t *long_ngroups, const int32_t *__restrict__ long_gbase,
     const int32_t *__restrict__ extra_owner, const int32_t *__restrict__ extra_group, uint32_t *cnt, int cap,
-    int extra_cap, xdd *gval, xdd *gcarry, fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
+    int extra_cap, xdd *gval, xdd *gcarry, fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost,
+    long long long_window) {
   const int lane = threadIdx.x & 31;
   const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
   // every extra slot below min(reserved, extra_cap) is written by the scatter: an owner, or -1
@@ -972,7 +973,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
       const long long q = (long long)(t - ngroup_items) * 32 + lane;
       if (q < n) {
         const PointRec r = rec[q];
-        if (r.flags || r.hi - r.lo + 1 <= kLongWindow)
+        if (r.flags || r.hi - r.lo + 1 <= long_window)
           sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
       }
       continue;
@@ -1003,7 +1004,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
         gval[slot] = sv;
         gcarry[slot] = gout;
         __threadfence();  // the group's value is visible before it is counted
-        const int done = atomicAdd(&long_ngroups[i], 1 << 16) >> 16;
+        const int done = (int)(atomicAdd(reinterpret_cast<unsigned int *>(&long_ngroups[i]), 1u << 16) >> 16);
         if (done == ng - 1) {
           __threadfence();
           finalize_long<BATCH>(P0, table, r, i, ng, gb, cap, gval, gcarry, out, nterms, bits_lost);
@@ -1037,7 +1038,7 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
   {
     ProfScope ps("k_sum_short", st);
     k_sum_short<CC, CZ, ACC, F32, false><<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms,
-                                                                          bits_lost);
+                                                                          bits_lost, P->tune.long_window);
   }
   {
     ProfScope ps("k_sum_groups", st);
@@ -1089,11 +1090,13 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
     if (cz)
       k_scatter<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                           w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
-                                          w.extra_group, (int)w.extra_cap, P->d_status);
+                                          w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
+                                          P->tune.group_span());
     else
       k_scatter<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                            w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
-                                           w.extra_group, (int)w.extra_cap, P->d_status);
+                                           w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
+                                           P->tune.group_span());
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -1177,7 +1180,7 @@ __global__ void k_scatter_batch(const DevPoly *__restrict__ table, const int32_t
                                 PointRec *__restrict__ rec, int32_t *__restrict__ long_list,
                                 int32_t *__restrict__ long_ngroups, int32_t *__restrict__ long_gbase,
                                 int32_t *__restrict__ extra_owner, int32_t *__restrict__ extra_group, int extra_cap,
-                                int32_t *status) {
+                                int32_t *status, long long long_window, long long span) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int i = pid[p];
@@ -1201,8 +1204,8 @@ __global__ void k_scatter_batch(const DevPoly *__restrict__ table, const int32_t
   r.pid = i;
   r.pad = 0;
   rec[pos] = r;
-  if (!r.flags && r.hi - r.lo + 1 > kLongWindow)
-    list_long_window(r.hi - r.lo + 1, pos, cnt, long_list, long_ngroups, long_gbase, extra_owner, extra_group,
+  if (!r.flags && r.hi - r.lo + 1 > long_window)
+    list_long_window(r.hi - r.lo + 1, span, pos, cnt, long_list, long_ngroups, long_gbase, extra_owner, extra_group,
                      extra_cap);
 }
 
@@ -1213,7 +1216,7 @@ static void launch_batch_sums(fpe_batch_s *B, fpe_xc64 *out, int32_t *nterms, cu
   k_sums<CC, CZ, ACC, F32, true><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
       DevPoly{}, B->d_table, (int)B->ntotal, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
       w.extra_group, B->d_cnt, (int)w.cap, (int)w.extra_cap, (xdd *)w.group_val, (xdd *)w.group_carry, out, nterms,
-      nullptr);
+      nullptr, B->tune.long_window);
 }
 
 fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
@@ -1245,12 +1248,12 @@ fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, 
       k_scatter_batch<true><<<nb, 256, 0, st>>>(B->d_table, B->d_pid, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key,
                                                 B->d_cursor, B->d_cnt, w.rec, w.long_list, w.long_ngroups,
                                                 w.long_gbase, w.extra_owner, w.extra_group, (int)w.extra_cap,
-                                                B->d_status);
+                                                B->d_status, B->tune.long_window, B->tune.group_span());
     else
       k_scatter_batch<false><<<nb, 256, 0, st>>>(B->d_table, B->d_pid, n, z_re, z_im, w.lo, w.hi, w.kl, w.N,
                                                  w.key, B->d_cursor, B->d_cnt, w.rec, w.long_list, w.long_ngroups,
                                                  w.long_gbase, w.extra_owner, w.extra_group, (int)w.extra_cap,
-                                                 B->d_status);
+                                                 B->d_status, B->tune.long_window, B->tune.group_span());
   }
   const bool cc = B->complex_coef;
 #define FPE_BATCH_SUMS(CCv, CZv)                                         \
@@ -1391,17 +1394,20 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
       if (cz)
         k_scatter<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                             w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
-                                            w.extra_group, (int)w.extra_cap, P->d_status);
+                                            w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
+                                            P->tune.group_span());
       else
         k_scatter<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                              w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
-                                             w.extra_group, (int)w.extra_cap, P->d_status);
+                                             w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
+                                             P->tune.group_span());
       const int cap = (int)w.cap, xcap = (int)w.extra_cap;
       const bool acc = P->dev.accurate != 0;
 #define FPE_NOALLOC_SUMS(CCv, CZv, ACCv, F32v)                                                                 \
   do {                                                                                                         \
     k_sum_short<CCv, CZv, ACCv, F32v, false>                                                                   \
-        <<<(ni + 127) / 128, 128, 0, st>>>(P->dev, nullptr, ni, w.rec, out, nterms, bits_lost);                \
+        <<<(ni + 127) / 128, 128, 0, st>>>(P->dev, nullptr, ni, w.rec, out, nterms, bits_lost,                 \
+                                           P->tune.long_window);                                               \
     k_sum_groups<CCv, CZv, ACCv, F32v><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(                           \
         P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,                \
         w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                          \

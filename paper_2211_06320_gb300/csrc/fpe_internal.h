@@ -56,13 +56,19 @@ constexpr int kSumBlocksPerSm = FPE_SUM_BLOCKS_PER_SM;
 // get similar windows; §8.1 suggests grouping evaluations of similar size).
 constexpr int kNumBins = 4096;
 
-// Points whose window is longer than kLongWindow are summed by warp groups:
-// a group is 32 lane chunks of at most kMaxLaneChunk terms, and a window gets
-// ceil(L / kGroupSpan) groups, so no warp's serial chain exceeds
-// kMaxLaneChunk terms however long the window is.
+// Points whose window is longer than the long-window threshold are summed
+// by warp groups: a group is 32 lane chunks of at most lane_chunk terms, and
+// a window gets ceil(L / (32 lane_chunk)) groups, so no warp's serial chain
+// exceeds lane_chunk terms however long the window is; shorter windows get
+// one thread each (32 points per warp).  Both are per-handle launch
+// parameters (fpe_set_tuning, fpe_autotune); these are the defaults.
 constexpr int64_t kLongWindow = 4096;
 constexpr int64_t kMaxLaneChunk = 1024;
-constexpr int64_t kGroupSpan = 32 * kMaxLaneChunk;
+struct Tuning {
+  int64_t long_window = kLongWindow;
+  int64_t lane_chunk = kMaxLaneChunk;
+  int64_t group_span() const { return 32 * lane_chunk; }
+};
 
 // Batched evaluation: lambda bins per polynomial (segmented bucketing).
 constexpr int kBatchBins = 32;
@@ -164,6 +170,8 @@ struct fpe_poly_s {
   int64_t last_n = 0;                   // points of the last fpe_eval
   void *aux = nullptr;                  // scratch of fpe_newton / fpe_grad_points (grown on demand)
   size_t aux_bytes = 0;
+  fpe::Tuning tune;                     // launch parameters of the window sums
+  double tune_ms = 0.0;                 // time per call of the setting fpe_autotune chose
 };
 
 struct fpe_batch_s {
@@ -179,6 +187,7 @@ struct fpe_batch_s {
   uint32_t *d_cnt = nullptr;            // kNumCounters
   int32_t *d_status = nullptr;
   fpe::Workspace ws;                    // sized for ntotal points
+  fpe::Tuning tune;                     // launch parameters of the window sums
 };
 
 namespace fpe {

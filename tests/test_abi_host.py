@@ -136,6 +136,30 @@ def test_null_handle_and_status_strings(F):
         assert F.fpe_status_string(s)
 
 
+def test_tuning_set_get_and_limits(F):
+    """Launch parameters of the window sums: defaults, a valid setting kept,
+    out-of-range settings and NULL arguments refused; the autotuner refuses a
+    host-only handle before touching any device memory."""
+    lib = F._load()
+    P = F.fpe_precondition(np.array([1.0, 2.0, 3.0]), None, None, 53, F.FPE_HOST_ONLY)
+    assert F.fpe_get_tuning(P) == {"long_window": 4096, "lane_chunk": 1024, "ms": 0.0}
+    F.fpe_set_tuning(P, 2048, 256)
+    assert F.fpe_get_tuning(P) == {"long_window": 2048, "lane_chunk": 256, "ms": 0.0}
+    for lw, lc in [(31, 256), (1 << 25, 256), (4096, 15), (4096, 1 << 17)]:
+        with pytest.raises(F.FpeError) as e:
+            F.fpe_set_tuning(P, lw, lc)
+        assert e.value.status == F.FPE_ERR_INVALID_ARG
+    assert F.fpe_get_tuning(P)["long_window"] == 2048
+    t = F.Tuning()
+    assert lib.fpe_set_tuning(None, ctypes.byref(t)) == F.FPE_ERR_INVALID_ARG
+    assert lib.fpe_set_tuning(P.handle, None) == F.FPE_ERR_INVALID_ARG
+    assert lib.fpe_get_tuning(P.handle, None) == F.FPE_ERR_INVALID_ARG
+    z = np.zeros(4)
+    assert lib.fpe_autotune(P.handle, F._np_ptr(z), None, 4, None, ctypes.byref(t)) == F.FPE_ERR_INVALID_ARG
+    assert lib.fpe_batch_set_tuning(None, ctypes.byref(t)) == F.FPE_ERR_INVALID_ARG
+    assert lib.fpe_batch_autotune(None, None, None, None, ctypes.byref(t)) == F.FPE_ERR_INVALID_ARG
+
+
 def test_derivative_handle_host(F):
     """P' coefficients (k+1) a_{k+1} are preconditioned separately (§7.2)."""
     c = W.unit_square_complex(200, np.random.default_rng(9))
