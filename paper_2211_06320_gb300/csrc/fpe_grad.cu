@@ -9,9 +9,15 @@
 //                    (conjugate Wirtinger convention: P is holomorphic in z).
 //   fpe_grad_coeffs  dL/da_k += sum_j g_j conj(z_j)^k over the kept terms
 //                    k in G_p cap [l_j, r_j] of each point: the FPE output
-//                    depends on no other coefficient.
+//                    depends on no other coefficient.  Short windows: a warp
+//                    sums its 32 points per coefficient in shared memory
+//                    before one atomic add; long windows: a warp per point,
+//                    lanes on consecutive coefficients.
 //   fpe_to_complex   (re, im) 2^e as plain FP64 (inf where it overflows).
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
 
 #include "fpe_device.cuh"
 #include "fpe_internal.h"
@@ -62,28 +68,14 @@ __global__ void k_grad_points(int n, const double *__restrict__ gre, const doubl
   if (ozi) ozi[j] = fma(gi, dr, -gr * di);
 }
 
-// One thread per point (bucketed order): walks the point's window upward,
-// c_k = g conj(z)^k kept as an FP64 mantissa pair and an exponent,
-// renormalised every 32 steps; adds c_k to dL/da_k for every good k.
+// One thread walks one point's window upward: c_k = g conj(z)^k kept as an
+// FP64 mantissa pair and an exponent, renormalised every 8 steps; adds c_k to
+// dL/da_k for every good k.  Used for warps whose points are far apart in
+// |z| (see k_grad_coeffs_short).
 template <bool CZ>
-__global__ void __launch_bounds__(128) k_grad_coeffs(DevPoly P, int n, const PointRec *__restrict__ rec,
-                                                     const double *__restrict__ gre,
-                                                     const double *__restrict__ gim, double *__restrict__ gar,
-                                                     double *__restrict__ gai) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const PointRec r = rec[q];
-  const double gr = gre[r.orig], gi = gim ? gim[r.orig] : 0.0;
-  if (r.flags) {
-    // z = 0: P(0) = a_0, so only a_0 moves it (when a_0 is a coefficient of the valuation-0 part)
-    if ((r.flags & kPointZero) && P.v == 0) {
-      atomicAdd(&gar[0], gr);
-      if (gai) atomicAdd(&gai[0], gi);
-    }
-    return;
-  }
+__device__ __forceinline__ void grad_point_atomic(const DevPoly &P, const PointRec &r, double gr, double gi,
+                                                  double *__restrict__ gar, double *__restrict__ gai) {
   const double cz_r = r.zr, cz_i = CZ ? -r.zi : 0.0;  // conj(z)
-  // c = g conj(z)^(v + lo) in extended form
   xdd pw = xdd_pow_int(cz_r, cz_i, P.v + r.lo);
   xdd c = xdd_mul_d(pw, gr, gi, 0);
   double cr = c.rh + c.rl, ci = c.ih + c.il;
@@ -97,13 +89,177 @@ __global__ void __launch_bounds__(128) k_grad_coeffs(DevPoly P, int n, const Poi
     const double nr = fma(cr, cz_r, -ci * cz_i), ni = fma(cr, cz_i, ci * cz_r);
     cr = nr;
     ci = ni;
-    if (((t - r.lo) & 31) == 31) {
+    if (((t - r.lo) & 7) == 7) {
       const double m = fmax(fabs(cr), fabs(ci));
       if (m != 0.0) {
         const int f = frexp_exp(m);
         cr = scale2(cr, -f);
         ci = scale2(ci, -f);
         ce += f;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_max_d(double x) {
+  for (int s = 16; s >= 1; s >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, s));
+  return x;
+}
+__device__ __forceinline__ long long warp_max_ll(long long x) {
+  for (int s = 16; s >= 1; s >>= 1) x = max(x, (long long)__shfl_xor_sync(0xffffffffu, x, s));
+  return x;
+}
+__device__ __forceinline__ long long warp_min_ll(long long x) {
+  for (int s = 16; s >= 1; s >>= 1) x = min(x, (long long)__shfl_xor_sync(0xffffffffu, x, s));
+  return x;
+}
+
+// Short windows, 32 bucketed points per warp (one per lane).  The warp walks
+// the union of its lanes' windows 8 coefficients at a time: each lane writes
+// its contributions g conj(z)^k (0 outside its window) into a shared tile,
+// then lane l < 16 sums row l (coefficient k0 + (l & 7), component l >> 3)
+// over the 32 points and makes the one atomic add for it: one atomic per
+// coefficient component per warp instead of one per point.  The lanes keep
+// one exponent E, renormalised after every tile; a warp whose points' |z|
+// differ too much for that (powers more than 2^400 apart over the union)
+// takes the one-thread-per-point loop instead.
+constexpr int kGradTile = 8;
+
+template <bool CZ>
+__global__ void __launch_bounds__(128) k_grad_coeffs_short(DevPoly P, int n, const PointRec *__restrict__ rec,
+                                                           const double *__restrict__ gre,
+                                                           const double *__restrict__ gim,
+                                                           double *__restrict__ gar, double *__restrict__ gai,
+                                                           long long long_window) {
+  __shared__ double tile[4][2][kGradTile][33];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  PointRec r;
+  bool act = false;
+  double gr = 0.0, gi = 0.0;
+  if (q < n) {
+    r = rec[q];
+    gr = gre[r.orig];
+    gi = gim ? gim[r.orig] : 0.0;
+    if (r.flags) {
+      // z = 0: P(0) = a_0, so only a_0 moves it (when a_0 is a coefficient of the valuation-0 part)
+      if ((r.flags & kPointZero) && P.v == 0) {
+        atomicAdd(&gar[0], gr);
+        if (gai) atomicAdd(&gai[0], gi);
+      }
+    } else {
+      act = r.hi - r.lo + 1 <= long_window;
+    }
+  }
+  const long long ulo = warp_min_ll(act ? r.lo : LLONG_MAX), uhi = warp_max_ll(act ? r.hi : LLONG_MIN);
+  if (ulo > uhi) return;  // no short window in this warp (warp-uniform)
+  // spread of |z| over the warp, in bits over the union window
+  const double lam = act ? log2(fmax(fabs(r.zr), fabs(r.zi))) : 0.0;
+  const double lmax = warp_max_d(act ? lam : -1e300), lmin = -warp_max_d(act ? -lam : -1e300);
+  if ((lmax - lmin) * (double)(uhi - ulo + 1) > 400.0) {
+    if (act) grad_point_atomic<CZ>(P, r, gr, gi, gar, gai);
+    return;
+  }
+  const double cz_r = act ? r.zr : 0.0, cz_i = (act && CZ) ? -r.zi : 0.0;  // conj(z)
+  double cr = 0.0, ci = 0.0;
+  long long ce = LLONG_MIN / 2;
+  if (act) {
+    const xdd c = xdd_mul_d(xdd_pow_int(cz_r, cz_i, P.v + ulo), gr, gi, 0);
+    cr = c.rh + c.rl;
+    ci = c.ih + c.il;
+    if (cr != 0.0 || ci != 0.0) ce = c.e;
+  }
+  long long E = warp_max_ll(ce);
+  if (E == LLONG_MIN / 2) return;  // every g is 0 (warp-uniform)
+  {
+    const int sh = (int)max(-3000LL, ce - E);  // <= 0
+    cr = scale2(cr, sh);
+    ci = scale2(ci, sh);
+  }
+  for (long long k0 = ulo; k0 <= uhi; k0 += kGradTile) {
+#pragma unroll
+    for (int kk = 0; kk < kGradTile; ++kk) {
+      const long long k = k0 + kk;
+      const bool in = act && k >= r.lo && k <= r.hi;
+      tile[wib][0][kk][lane] = in ? cr : 0.0;
+      tile[wib][1][kk][lane] = in ? ci : 0.0;
+      const double nr = fma(cr, cz_r, -ci * cz_i), ni = fma(cr, cz_i, ci * cz_r);
+      cr = nr;
+      ci = ni;
+    }
+    __syncwarp();
+    if (lane < 2 * kGradTile) {
+      const int kk = lane & (kGradTile - 1), comp = lane / kGradTile;
+      const long long k = k0 + kk;
+      if (k <= uhi && P.gcount[k + 1] != P.gcount[k] && (comp == 0 || gai)) {
+        double sum = 0.0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) sum += tile[wib][comp][kk][j];
+        if (sum != 0.0) atomicAdd(&(comp ? gai : gar)[P.v + k], scale2(sum, (int)max(-3000LL, min(3000LL, E))));
+      }
+    }
+    __syncwarp();
+    const double m = warp_max_d(fmax(fabs(cr), fabs(ci)));
+    if (m != 0.0 && isfinite(m)) {
+      const int f = frexp_exp(m);
+      cr = scale2(cr, -f);
+      ci = scale2(ci, -f);
+      E += f;
+    }
+  }
+}
+
+// Long windows, one warp per point: lane i takes k = l + i + 32 m, so the
+// 32 atomic adds of a step go to 32 different coefficients.  Each lane starts
+// from g conj(z)^(v + l + i) and multiplies by conj(z)^32 held in
+// double-double (8 FMA per step), with its own exponent renormalised every 8
+// steps; the drift is that of L/32 FP64 roundings.
+template <bool CZ>
+__global__ void __launch_bounds__(128) k_grad_coeffs_long(DevPoly P, const PointRec *__restrict__ rec,
+                                                          const int32_t *__restrict__ long_list,
+                                                          const uint32_t *cnt, const double *__restrict__ gre,
+                                                          const double *__restrict__ gim,
+                                                          double *__restrict__ gar, double *__restrict__ gai) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nlong = *(volatile const uint32_t *)&cnt[kCntLong];
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nlong; i += nwarps) {
+    const PointRec r = rec[long_list[i]];
+    const double gr = gre[r.orig], gi = gim ? gim[r.orig] : 0.0;
+    const double cz_r = r.zr, cz_i = CZ ? -r.zi : 0.0;  // conj(z)
+    const xdd c0 = xdd_mul_d(xdd_pow_int(cz_r, cz_i, P.v + r.lo + lane), gr, gi, 0);
+    double cr = c0.rh + c0.rl, ci = c0.ih + c0.il;
+    long long ce = c0.e;
+    const xdd M = xdd_pow_int(cz_r, cz_i, 32);  // conj(z)^32 = (mh + ml) 2^me
+    const double mhr = M.rh, mlr = M.rl, mhi = M.ih, mli = M.il;
+    const long long me = M.e;
+    int steps = 0;
+    for (long long k = r.lo + lane; k <= r.hi; k += 32) {
+      if (P.gcount[k + 1] != P.gcount[k]) {
+        const int sh = (int)max(-3000LL, min(3000LL, ce));
+        atomicAdd(&gar[P.v + k], scale2(cr, sh));
+        if (gai) atomicAdd(&gai[P.v + k], scale2(ci, sh));
+      }
+      double nr, ni;
+      if (CZ) {
+        nr = fma(cr, mhr, fma(-ci, mhi, fma(cr, mlr, -ci * mli)));
+        ni = fma(cr, mhi, fma(ci, mhr, fma(cr, mli, ci * mlr)));
+      } else {
+        nr = fma(cr, mhr, cr * mlr);
+        ni = fma(ci, mhr, ci * mlr);
+      }
+      cr = nr;
+      ci = ni;
+      ce += me;
+      if (++steps == 8) {
+        steps = 0;
+        const double m = fmax(fabs(cr), fabs(ci));
+        if (m != 0.0 && isfinite(m)) {
+          const int f = frexp_exp(m);
+          cr = scale2(cr, -f);
+          ci = scale2(ci, -f);
+          ce += f;
+        }
       }
     }
   }
@@ -182,14 +338,28 @@ fpe_status launch_grad_coeffs(fpe_poly_s *P, const double *z_re, const double *z
   if (n == 0) return FPE_OK;
   fpe_status s = launch_front(P, z_re, z_im, n, st);
   if (s != FPE_OK) return s;
+  Workspace &w = P->ws;
   {
-    ProfScope ps("k_grad_coeffs", st);
+    ProfScope ps("k_grad_coeffs_short", st);
     if (z_im)
-      k_grad_coeffs<true><<<(int)((n + 127) / 128), 128, 0, st>>>(P->dev, (int)n, P->ws.rec, g_re, g_im, ga_re,
-                                                                  ga_im);
+      k_grad_coeffs_short<true><<<(int)((n + 127) / 128), 128, 0, st>>>(P->dev, (int)n, w.rec, g_re, g_im, ga_re,
+                                                                        ga_im, P->tune.long_window);
     else
-      k_grad_coeffs<false><<<(int)((n + 127) / 128), 128, 0, st>>>(P->dev, (int)n, P->ws.rec, g_re, g_im, ga_re,
-                                                                   ga_im);
+      k_grad_coeffs_short<false><<<(int)((n + 127) / 128), 128, 0, st>>>(P->dev, (int)n, w.rec, g_re, g_im, ga_re,
+                                                                         ga_im, P->tune.long_window);
+  }
+  {
+    ProfScope ps("k_grad_coeffs_long", st);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = std::max(sms, 1) * 8;
+    if (z_im)
+      k_grad_coeffs_long<true><<<blocks, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.bins + 2 * kNumBins, g_re, g_im,
+                                                       ga_re, ga_im);
+    else
+      k_grad_coeffs_long<false><<<blocks, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.bins + 2 * kNumBins, g_re,
+                                                        g_im, ga_re, ga_im);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "k_grad_coeffs");

@@ -134,10 +134,13 @@ def _dense_coeff_grad_windowed(z, g, n_coef, L, R, good):
     return G, A
 
 
-def test_coefficient_gradient_vs_dense(env):
+@pytest.mark.parametrize("long_window", [4096, 32], ids=["short-windows", "long-windows"])
+def test_coefficient_gradient_vs_dense(env, long_window):
     """dL/da_k restricted to the kept terms equals the windowed dense sum; against
     the full (unrestricted) gradient the difference, scaled by |a_k|, is below
-    2^(-T+1) sum_j |g_j| M_j (every dropped term is below 2^(-T+1) M_j, §6)."""
+    2^(-T+1) sum_j |g_j| M_j (every dropped term is below 2^(-T+1) M_j, §6).
+    With the long-window threshold at 32 every window goes through the
+    warp-per-point kernel instead of the shared-memory tiles."""
     torch, F = env
     rng = np.random.default_rng(22)
     coef = W.unit_disk_complex(300, rng)
@@ -146,6 +149,7 @@ def test_coefficient_gradient_vs_dense(env):
     z = r * np.exp(1j * t)
     g = rng.normal(size=800) + 1j * rng.normal(size=800)
     P = F.fpe_precondition(coef.re, coef.im, None, 53, F.FPE_WITH_DERIV)
+    F.fpe_set_tuning(P, long_window, 1024)
     zr = torch.from_numpy(z.real.copy()).cuda()
     zi = torch.from_numpy(z.imag.copy()).cuda()
     ga_re = torch.zeros(coef.n_coef, dtype=torch.float64, device="cuda")
@@ -165,6 +169,33 @@ def test_coefficient_gradient_vs_dense(env):
     bound = 2.0 ** (-T + 1) * np.sum(np.abs(g) * np.exp2(l2M))
     a_abs = np.hypot(coef.re, coef.im)
     assert np.all(a_abs * np.abs(got - G) <= bound + 1e-12 * a_abs * A)
+
+
+@pytest.mark.parametrize("long_window", [4096, 32], ids=["short-windows", "long-windows"])
+def test_coefficient_gradient_real(env, long_window):
+    """Real coefficients at real points (ga_im NULL), including z = 0 (only
+    a_0 moves P(0)) and a warp mixing |z| far apart (the per-point fallback)."""
+    torch, F = env
+    rng = np.random.default_rng(24)
+    coef = W.Coeffs(rng.uniform(-1, 1, 401), None)
+    x = np.concatenate([rng.uniform(-1.2, 1.2, 700), [0.0], [1e-30, 3e20], rng.uniform(-1.05, 1.05, 97)])
+    g = rng.normal(size=x.size)
+    P = F.fpe_precondition(coef.re, None, None, 53)
+    F.fpe_set_tuning(P, long_window, 1024)
+    xr = torch.from_numpy(x.copy()).cuda()
+    ga = torch.zeros(coef.n_coef, dtype=torch.float64, device="cuda")
+    F.fpe_grad_coeffs(P, xr, None, torch.from_numpy(g.copy()).cuda(), None, ga, None)
+    F.fpe_eval(P, xr, None)
+    l, rr, _ = F.fpe_get_windows(P, x.size)
+    F.fpe_sync(P)
+    good = F.fpe_get_good(P)
+    L, R = l.cpu().numpy(), rr.cpu().numpy()
+    L[x == 0], R[x == 0] = 0, 0  # P(0) = a_0: the window of z = 0 is {0}
+    with np.errstate(over="ignore", invalid="ignore"):
+        Gw, Aw = _dense_coeff_grad_windowed(x.astype(complex), g.astype(complex), coef.n_coef, L, R, good)
+    got = ga.cpu().numpy()
+    fin = np.isfinite(Gw.real)
+    assert np.all((np.abs(got - Gw.real) <= 1e-12 * Aw + 1e-300)[fin])
 
 
 def test_autograd_finite_differences(env):
