@@ -102,18 +102,6 @@ __device__ __forceinline__ xdd xdd_from(double re, double im, long long e) {
   return xdd_norm(x);
 }
 
-// x * x
-__device__ __forceinline__ xdd xdd_sqr(xdd x) {
-  dd p1 = two_prod(x.rh, x.rh), p2 = two_prod(x.ih, x.ih), p3 = two_prod(x.rh, x.ih);
-  dd s = two_sum(p1.hi, -p2.hi);
-  double t = s.lo + (p1.lo - p2.lo) + 2.0 * (x.rh * x.rl - x.ih * x.il);
-  dd re = two_sum(s.hi, t);
-  double ti = p3.lo + x.rh * x.il + x.rl * x.ih;
-  dd im = fast_two_sum(2.0 * p3.hi, 2.0 * ti);
-  xdd r = {re.hi, re.lo, im.hi, im.lo, 2 * x.e};
-  return xdd_norm(r);
-}
-
 // x * (zr + i zi) with zr, zi plain doubles (scaled by 2^ze)
 __device__ __forceinline__ xdd xdd_mul_d(xdd x, double zr, double zi, long long ze) {
   dd p1 = two_prod(x.rh, zr), p2 = two_prod(x.ih, zi);
@@ -161,23 +149,6 @@ __device__ __forceinline__ xdd xdd_add(xdd x, xdd y) {
   dd r2 = two_sum(re.hi, re.lo), i2 = two_sum(im.hi, im.lo);
   xdd r = {r2.hi, r2.lo, i2.hi, i2.lo, x.e};
   return xdd_norm(r);
-}
-
-// (zr + i zi)^n for n >= 0, left-to-right binary powering (§8.2: z^l by
-// repeated squaring, at most 2 log2 l products), in extended double-double.
-__device__ __forceinline__ xdd xdd_pow(double zr, double zi, long long n) {
-  if (n <= 0) return {0.5, 0.0, 0.0, 0.0, 1};
-  // split z = m 2^f with max(|m|) in [0.5, 1) so that the running power stays normalised
-  int f = frexp_exp(fmax(fabs(zr), fabs(zi)));
-  double mr = scale2(zr, -f), mi = scale2(zi, -f);
-  xdd r = xdd_from(mr, mi, 0);
-  int top = 63 - __clzll(n);
-  for (int b = top - 1; b >= 0; --b) {
-    r = xdd_sqr(r);
-    if ((n >> b) & 1) r = xdd_mul_d(r, mr, mi, 0);
-  }
-  r.e += (long long)f * n;
-  return r;
 }
 
 // One Horner step h <- h w + b on complex (or real, CZ/CC false) values.
@@ -718,6 +689,52 @@ __device__ __forceinline__ xdd xdd_from_isum(const isum &h) {
   const u128 ar = sr ? (u128)(-h.xr) : (u128)h.xr, ai = si ? (u128)(-h.xi) : (u128)h.xi;
   if (!ar && !ai) return xdd_zero();
   return xdd_from_xint(xint_norm(ar, sr, ai, si, (long long)h.G + 126));
+}
+
+// ---------------------------------------------------------------------------
+// Extended values of the FP32 mode: an FP64 complex mantissa with an int64
+// exponent, max(|r|, |i|) in [0.5, 1) or both zero.  Each operation rounds
+// at a few 2^-53 relative, far below the mode's 2^-21 tolerance, and costs
+// a third of the FP64 instructions of the double-double forms above.
+// ---------------------------------------------------------------------------
+struct xd {
+  double r, i;
+  long long e;
+};
+
+__device__ __forceinline__ xd xd_norm(double r, double i, long long e) {
+  const double m = fmax(fabs(r), fabs(i));
+  if (m == 0.0) return {0.0, 0.0, 0};
+  const int f = frexp_exp(m);
+  return {scale2(r, -f), scale2(i, -f), e + f};
+}
+__device__ __forceinline__ xd xd_mul(const xd &a, const xd &b) {
+  return xd_norm(fma(a.r, b.r, -a.i * b.i), fma(a.r, b.i, a.i * b.r), a.e + b.e);
+}
+// a * (zr + i zi) 2^ze
+__device__ __forceinline__ xd xd_mul_d(const xd &a, double zr, double zi, long long ze) {
+  return xd_norm(fma(a.r, zr, -a.i * zi), fma(a.r, zi, a.i * zr), a.e + ze);
+}
+__device__ __forceinline__ xd xd_add(const xd &a, const xd &b) {
+  if (a.r == 0.0 && a.i == 0.0) return b;
+  if (b.r == 0.0 && b.i == 0.0) return a;
+  if (a.e >= b.e) {
+    const int d = (int)max(-2000LL, b.e - a.e);
+    return xd_norm(a.r + scale2(b.r, d), a.i + scale2(b.i, d), a.e);
+  }
+  const int d = (int)max(-2000LL, a.e - b.e);
+  return xd_norm(b.r + scale2(a.r, d), b.i + scale2(a.i, d), b.e);
+}
+__device__ __forceinline__ xdd xdd_from_xd(const xd &x) { return {x.r, 0.0, x.i, 0.0, x.e}; }
+
+// z^n (n >= 0) on the integer pipe, kept to its top 53 bits
+__device__ __forceinline__ xd xd_pow_int(double zr, double zi, long long n) {
+  if (n <= 0) return {0.5, 0.0, 1};
+  const int f = frexp_exp(fmax(fabs(zr), fabs(zi)));
+  const xint v = xint_pow_unit(scale2(zr, -f), scale2(zi, -f), n);
+  // component = X 2^(e - 126) with X < 2^127: its top bits H = X >> 74 times 2^(e - 52)
+  const double hr = (double)(unsigned long long)(v.x >> 74), hi = (double)(unsigned long long)(v.y >> 74);
+  return xd_norm(v.sx ? -hr : hr, v.sy ? -hi : hi, v.e - 52 + (long long)f * n);
 }
 
 // Normalised FP64 output (fpe_xc64) from an extended double-double value.

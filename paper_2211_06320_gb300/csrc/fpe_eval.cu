@@ -601,12 +601,14 @@ __device__ __forceinline__ void window_horner_rev_f32(const DevPoly &P, const cd
   rho_hi = P.piece_rho0[j] + (long long)P.piece_beta[j] * (hi - P.piece_k0[j]);
 }
 
-// FP32 counterpart of range_sum
+// FP32 counterpart of range_sum with xd values: u = 1/m in plain FP64
+// (u.rh, u.ih), which the float-float multiplier of the bottom-up part is
+// split from anyway.
 template <bool CC, bool CZ>
-__device__ __forceinline__ xdd range_sum_f32(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
+__device__ __forceinline__ xd range_sum_f32x(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
                                              const cdd &u, long long lo, long long hi, long long kl,
                                              long long &base) {
-  xdd X = xdd_zero();
+  xd X = {0.0, 0.0, 0};
   const long long top_lo = max(kl, lo);
   const long long low_hi = min(top_lo - 1, hi);
   const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
@@ -614,28 +616,24 @@ __device__ __forceinline__ xdd range_sum_f32(const DevPoly &P, double zr, double
     float hr, hm;
     long long rho;
     window_horner_f32<CC, CZ>(P, zr, zi, top_lo, hi, hr, hm, rho);
-    if (hr != 0.0f || hm != 0.0f) X = xdd_from((double)hr, (double)hm, rho);
+    X = xd_norm((double)hr, (double)hm, rho);
     base = top_lo;
   }
   if (has_low) {
     float hr, hm;
     long long rho;
     window_horner_rev_f32<CC, CZ>(P, u, -f, lo, low_hi, hr, hm, rho);
-    if (has_up && (X.rh != 0.0 || X.ih != 0.0)) X = xdd_mul_d(X, mr, mi, f);
-    if (hr != 0.0f || hm != 0.0f) X = xdd_add(X, xdd_from((double)hr, (double)hm, rho));
+    if (has_up && (X.r != 0.0 || X.i != 0.0)) X = xd_mul_d(X, mr, mi, f);
+    X = xd_add(X, xd_norm((double)hr, (double)hm, rho));
     base = low_hi;
   }
   return X;
 }
 
-template <bool CC, bool CZ, bool F32>
-__device__ __forceinline__ xdd range_sum_any(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
-                                             const cdd &u, long long lo, long long hi, long long kl,
-                                             long long &base) {
-  if constexpr (F32)
-    return range_sum_f32<CC, CZ>(P, zr, zi, mr, mi, f, u, lo, hi, kl, base);
-  else
-    return range_sum<CC, CZ>(P, zr, zi, mr, mi, f, u, lo, hi, kl, base);
+// 1/m for a unit-size complex m in plain FP64, as a cdd with zero low parts
+__device__ __forceinline__ cdd recip_d(double mr, double mi) {
+  const double inv = 1.0 / fma(mr, mr, mi * mi);
+  return {mr * inv, 0.0, -mi * inv, 0.0};
 }
 
 // Integer-pipe Horner continued from g (scaled at index k + 1, which lies in
@@ -736,19 +734,31 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
   if (r.flags) {
     o = special_value(P, r.flags);
   } else {
-    xdd X;
     long long base = r.lo;
-    if (ACC) {
-      X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
-    } else {
+    if (F32) {  // xd values: the mode's tolerance does not need double-double
       const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
       const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
       cdd u = {0.0, 0.0, 0.0, 0.0};
-      if (r.lo < r.kl) u = recip_dd(mr, mi);
-      X = range_sum_any<CC, CZ, F32>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+      if (r.lo < r.kl) u = recip_d(mr, mi);
+      const xd X = range_sum_f32x<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+      const xd v = xd_mul(X, xd_pow_int(r.zr, r.zi, base + P.v));
+      o.re = v.r;
+      o.im = v.i;
+      o.e = v.e;
+    } else {
+      xdd X;
+      if (ACC) {
+        X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
+      } else {
+        const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+        const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
+        cdd u = {0.0, 0.0, 0.0, 0.0};
+        if (r.lo < r.kl) u = recip_dd(mr, mi);
+        X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+      }
+      xdd pw = xdd_pow_int(r.zr, r.zi, base + P.v);
+      o = xdd_out(xdd_mul(X, pw));
     }
-    xdd pw = xdd_pow_int(r.zr, r.zi, base + P.v);
-    o = xdd_out(xdd_mul(X, pw));
   }
   out[r.orig] = o;
   write_diag(P, r, o, nterms, bits_lost);
@@ -818,6 +828,47 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
   const long long C = (L + 32LL * ng - 1) / (32LL * ng);
   const long long clo = r.lo + (long long)g * 32 * C + lane * C;
   const long long chi = min(clo + C - 1, r.hi);
+  if constexpr (F32) {  // the same steps in xd values
+    xd v = {0.0, 0.0, 0}, cy = {0.0, 0.0, 0};
+    if (clo <= chi) {
+      const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+      const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
+      const cdd u = recip_d(mr, mi);
+      long long base;
+      const xd X = range_sum_f32x<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
+      if (chi < r.kl)
+        cy = xd_mul_d(X, u.rh, u.ih, -f);
+      else if (base > clo)
+        v = xd_mul(X, xd_pow_int(r.zr, r.zi, base - clo));
+      else
+        v = X;
+    }
+    auto shfl = [](xd x, int sft, int mode) {
+      xd y;
+      if (mode == 0) {
+        y.r = __shfl_up_sync(0xffffffffu, x.r, sft);
+        y.i = __shfl_up_sync(0xffffffffu, x.i, sft);
+        y.e = __shfl_up_sync(0xffffffffu, x.e, sft);
+      } else if (mode == 1) {
+        y.r = __shfl_down_sync(0xffffffffu, x.r, sft);
+        y.i = __shfl_down_sync(0xffffffffu, x.i, sft);
+        y.e = __shfl_down_sync(0xffffffffu, x.e, sft);
+      } else {
+        y.r = __shfl_xor_sync(0xffffffffu, x.r, sft);
+        y.i = __shfl_xor_sync(0xffffffffu, x.i, sft);
+        y.e = __shfl_xor_sync(0xffffffffu, x.e, sft);
+      }
+      return y;
+    };
+    const xd inc = shfl(cy, 1, 0);
+    if (lane > 0) v = xd_add(v, inc);
+    const xd go = shfl(cy, 31, 1);  // lane 31's carry, read by lane 0
+    if (lane > 0 && (v.r != 0.0 || v.i != 0.0)) v = xd_mul(v, xd_pow_int(r.zr, r.zi, lane * C));
+    for (int sft = 16; sft >= 1; sft >>= 1) v = xd_add(v, shfl(v, sft, 2));
+    sv_out = xdd_from_xd(v);
+    gout_out = xdd_from_xd(go);
+    return;
+  }
   xdd sv = xdd_zero(), carry = xdd_zero();
   if (ACC) {
     if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
@@ -826,7 +877,7 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
     const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
     const cdd u = recip_dd(mr, mi);
     long long base;
-    xdd X = range_sum_any<CC, CZ, F32>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
+    xdd X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
     if (chi < r.kl) {
       carry = xdd_mul(X, xdd_from_cdd(u, -f));  // below the peak: X / z to the next slot
     } else if (base > clo) {
@@ -849,38 +900,11 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
   gout_out = gout;
 }
 
-// Combine a long window's groups, sum_g (z^S)^g (val_g + carry_{g-1}) by
-// Horner from the top group, apply z^(l + v) and write the point (one lane).
-// Group values written by other SMs are read past L1 (__ldcg).
-template <bool BATCH>
-__device__ __forceinline__ void finalize_long(const DevPoly &P0, const DevPoly *__restrict__ table,
-                                              const PointRec &r, int i, int ng, int gb, int cap,
-                                              const xdd *gval, const xdd *gcarry, fpe_xc64 *__restrict__ out,
-                                              int32_t *nterms, int32_t *bits_lost) {
-  const DevPoly &P = BATCH ? table[r.pid] : P0;
-  auto ld = [](const xdd *p) {
-    xdd x;
-    x.rh = __ldcg(&p->rh);
-    x.rl = __ldcg(&p->rl);
-    x.ih = __ldcg(&p->ih);
-    x.il = __ldcg(&p->il);
-    x.e = __ldcg(&p->e);
-    return x;
-  };
-  xdd acc = ld(&gval[group_slot(i, ng - 1, gb, cap)]);
-  if (ng > 1) {
-    const long long L = r.hi - r.lo + 1;
-    const long long C = (L + 32LL * ng - 1) / (32LL * ng);
-    const xdd W = xdd_pow_int(r.zr, r.zi, 32 * C);
-    acc = xdd_add(acc, ld(&gcarry[group_slot(i, ng - 2, gb, cap)]));
-    for (int g = ng - 2; g >= 0; --g) {
-      xdd sg = ld(&gval[group_slot(i, g, gb, cap)]);
-      if (g > 0) sg = xdd_add(sg, ld(&gcarry[group_slot(i, g - 1, gb, cap)]));
-      acc = xdd_add(xdd_mul(acc, W), sg);
-    }
-  }
+// A long window with one group: its value times z^(l + v), written by one thread.
+__device__ __forceinline__ void finalize_one(const DevPoly &P, const PointRec &r, const xdd &val,
+                                             fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
   const xdd pw = xdd_pow_int(r.zr, r.zi, r.lo + P.v);
-  const fpe_xc64 o = xdd_out(xdd_mul(acc, pw));
+  const fpe_xc64 o = xdd_out(xdd_mul(val, pw));
   out[r.orig] = o;
   write_diag(P, r, o, nterms, bits_lost);
 }
@@ -923,7 +947,59 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(
   }
 }
 
-// One thread per long window: combine its groups and write the point.
+// The warp-parallel combination of a long window's ng > 1 groups (all 32
+// lanes call it): lane g holds val_g + carry_{g-1} times W^g = z^(32 C g),
+// a butterfly adds the lanes, lane 0 applies z^(l + v) and writes the point.
+// Group values written by other SMs are read past L1.
+template <bool BATCH>
+__device__ __forceinline__ void finalize_warp(const DevPoly &P0, const DevPoly *__restrict__ table,
+                                              const PointRec &r, int i, int ng, int gb, int cap,
+                                              const xdd *gval, const xdd *gcarry, int lane,
+                                              fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
+  const DevPoly &P = BATCH ? table[r.pid] : P0;
+  auto ld = [](const xdd *p) {
+    xdd x;
+    x.rh = __ldcg(&p->rh);
+    x.rl = __ldcg(&p->rl);
+    x.ih = __ldcg(&p->ih);
+    x.il = __ldcg(&p->il);
+    x.e = __ldcg(&p->e);
+    return x;
+  };
+  const long long L = r.hi - r.lo + 1;
+  const long long C = (L + 32LL * ng - 1) / (32LL * ng);
+  auto slot_sum = [&](int g) {  // val_g + carry_{g-1}
+    xdd v = ld(&gval[group_slot(i, g, gb, cap)]);
+    if (g > 0) v = xdd_add(v, ld(&gcarry[group_slot(i, g - 1, gb, cap)]));
+    return v;
+  };
+  xdd t = xdd_zero();
+  if (ng <= 32) {
+    if (lane < ng) t = slot_sum(lane);
+  } else {  // the lane's groups lane + 32 m, by Horner in W^32 from the top m
+    const xdd W32 = xdd_pow_int(r.zr, r.zi, 32 * 32 * C);
+    for (int g = lane + 32 * ((ng - 1 - lane) / 32); g >= lane; g -= 32) t = xdd_add(xdd_mul(t, W32), slot_sum(g));
+  }
+  // lane 0: z^(l + v); lane g > 0: W^g
+  const xdd pw = xdd_pow_int(r.zr, r.zi, lane == 0 ? r.lo + P.v : 32 * C * lane);
+  if (lane > 0 && (t.rh != 0.0 || t.ih != 0.0)) t = xdd_mul(t, pw);
+  for (int sft = 16; sft >= 1; sft >>= 1) t = xdd_add(t, shfl_xor_xdd(t, sft));
+  if (lane == 0) {
+    const fpe_xc64 o = xdd_out(xdd_mul(t, pw));
+    out[r.orig] = o;
+    write_diag(P, r, o, nterms, bits_lost);
+  }
+}
+
+// Finish the long windows.  A window with one group takes one thread: its
+// power z^(l + v) and one product.  A window with ng > 1 groups takes a warp:
+// lane g holds group g's value plus the carry of group g - 1 and multiplies
+// it by its own power W^g = z^(32 C g) (integer pipe), a butterfly adds the
+// lanes, and lane 0, which meanwhile computed z^(l + v), writes the point.
+// (On this GPU a dependent FP64 instruction costs a warp tens of cycles, so
+// a one-thread Horner over 32 groups in double-double was the kernel's
+// whole duration.)  For ng > 32 lane g first sums its groups g + 32 m by
+// Horner in W^32.
 __global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec *__restrict__ rec,
                                                        const int32_t *__restrict__ long_list,
                                                        const int32_t *__restrict__ long_ngroups,
@@ -932,14 +1008,23 @@ __global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec
                                                        const xdd *__restrict__ gcarry, fpe_xc64 *__restrict__ out,
                                                        int32_t *nterms, int32_t *bits_lost) {
   const uint32_t nlong = *(volatile const uint32_t *)&cnt[kCntLong];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nlong; i += gridDim.x * blockDim.x) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  for (uint32_t i = tid; i < nlong; i += nthr) {
+    if ((long_ngroups[i] & 0xffff) != 1) continue;
     const PointRec r = rec[long_list[i]];
-    finalize_long<false>(P, nullptr, r, (int)i, long_ngroups[i] & 0xffff, long_gbase[i], cap, gval, gcarry, out,
+    finalize_one(P, r, gval[group_slot((int)i, 0, long_gbase[i], cap)], out, nterms, bits_lost);
+  }
+  const int lane = threadIdx.x & 31;
+  const uint32_t wid = tid >> 5, nwarps = nthr >> 5;
+  for (uint32_t i = wid; i < nlong; i += nwarps) {
+    const int ng = long_ngroups[i] & 0xffff;
+    if (ng == 1) continue;  // warp-uniform
+    finalize_warp<false>(P, nullptr, rec[long_list[i]], (int)i, ng, long_gbase[i], cap, gval, gcarry, lane, out,
                          nterms, bits_lost);
   }
 }
 
-// All window sums of one evaluation in one persistent launch.// All window sums of one batched evaluation in one persistent launch (the
+// All window sums of one batched evaluation in one persistent launch (the
 // single-polynomial path uses k_sum_short, k_sum_groups, k_finalize_long,
 // which measured faster there).  Each warp
 // takes work items from a counter:
@@ -950,7 +1035,8 @@ __global__ void __launch_bounds__(128) k_finalize_long(DevPoly P, const PointRec
 // A window with one group is finished by the warp that sums it.  Otherwise
 // each group stores its value, fences, and counts itself done in the upper
 // 16 bits of long_ngroups[i]; the warp that completes the count combines the
-// groups and writes the point.  No warp ever waits for another.
+// groups (all lanes, finalize_warp) and writes the point.  No warp ever
+// waits for another.
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
 __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
     DevPoly P0, const DevPoly *__restrict__ table, int n, const PointRec *__restrict__ rec,
@@ -992,23 +1078,22 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
     const DevPoly &P = BATCH ? table[r.pid] : P0;
     xdd sv, gout;
     sum_group<CC, CZ, ACC, F32>(P, r, ng, g, lane, sv, gout);
-    if (lane == 0) {
-      if (ng == 1) {  // the whole window: finish it here
-        const xdd pw = xdd_pow_int(r.zr, r.zi, r.lo + P.v);
-        const fpe_xc64 o = xdd_out(xdd_mul(sv, pw));
-        out[r.orig] = o;
-        write_diag(P, r, o, nterms, bits_lost);
-      } else {
-        const int gb = long_gbase[i];
+    if (ng == 1) {  // the whole window: finish it here
+      if (lane == 0) finalize_one(P, r, sv, out, nterms, bits_lost);
+    } else {
+      const int gb = long_gbase[i];
+      int last = 0;
+      if (lane == 0) {
         const int slot = group_slot(i, g, gb, cap);
         gval[slot] = sv;
         gcarry[slot] = gout;
         __threadfence();  // the group's value is visible before it is counted
         const int done = (int)(atomicAdd(reinterpret_cast<unsigned int *>(&long_ngroups[i]), 1u << 16) >> 16);
-        if (done == ng - 1) {
-          __threadfence();
-          finalize_long<BATCH>(P0, table, r, i, ng, gb, cap, gval, gcarry, out, nterms, bits_lost);
-        }
+        last = done == ng - 1;
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence();
+        finalize_warp<BATCH>(P0, table, r, i, ng, gb, cap, gval, gcarry, lane, out, nterms, bits_lost);
       }
     }
   }
