@@ -193,45 +193,10 @@ __device__ __forceinline__ void horner_step(double &hr, double &hm, double &cr, 
   }
 }
 
-// 1/m in double-double for a complex m with max(|mr|, |mi|) in [0.5, 1):
-// conj(m) / |m|^2, |m|^2 summed exactly from TwoProd terms, each quotient
-// refined by one FMA-based correction step.
+// A complex double-double (rh + rl) + i (ih + il).
 struct cdd {
   double rh, rl, ih, il;
 };
-__device__ __forceinline__ dd dd_div_d(double a, dd b) {
-  double q1 = a / b.hi;
-  double r = fma(-q1, b.hi, a) - q1 * b.lo;
-  double q2 = r / b.hi;
-  return fast_two_sum(q1, q2);
-}
-__device__ __forceinline__ cdd recip_dd(double mr, double mi) {
-  dd p1 = two_prod(mr, mr), p2 = two_prod(mi, mi);
-  dd s = two_sum(p1.hi, p2.hi);
-  dd n2 = fast_two_sum(s.hi, s.lo + p1.lo + p2.lo);
-  dd ur = dd_div_d(mr, n2), ui = dd_div_d(-mi, n2);
-  return {ur.hi, ur.lo, ui.hi, ui.lo};
-}
-
-// complex double-double product (relative error about 2^-104 of |a||b|)
-__device__ __forceinline__ dd dd_mul(dd x, dd y) {
-  dd p = two_prod(x.hi, y.hi);
-  p.lo = fma(x.hi, y.lo, fma(x.lo, y.hi, p.lo));
-  return fast_two_sum(p.hi, p.lo);
-}
-__device__ __forceinline__ dd dd_add(dd x, dd y) {
-  dd s = two_sum(x.hi, y.hi);
-  s.lo += x.lo + y.lo;
-  return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ cdd cdd_mul(const cdd &a, const cdd &b) {
-  const dd ar = {a.rh, a.rl}, ai = {a.ih, a.il}, br = {b.rh, b.rl}, bi = {b.ih, b.il};
-  dd t = dd_mul(ai, bi);
-  t.hi = -t.hi;
-  t.lo = -t.lo;
-  const dd re = dd_add(dd_mul(ar, br), t), im = dd_add(dd_mul(ar, bi), dd_mul(ai, br));
-  return {re.hi, re.lo, im.hi, im.lo};
-}
 
 // ---------------------------------------------------------------------------
 // z^n on the integer pipe.  On this GPU a 64-bit integer multiply-high issues
@@ -372,6 +337,124 @@ __host__ __device__ __forceinline__ xint xint_pow_unit(double mr, double mi, lon
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-point helpers for the per-window bookkeeping (exact conversions from
+// doubles, addition, the reciprocal 1/m, conversion to the output format):
+// they run on the integer pipe, which the FP64-bound window kernels leave
+// idle, instead of double-double FP64 chains.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ xint xint_neg(xint a) {
+  a.sx = a.x ? a.sx ^ 1 : 0;
+  a.sy = a.y ? a.sy ^ 1 : 0;
+  return a;
+}
+
+// |x| 2^-unit as a 128-bit magnitude (x finite, |x| 2^-unit < 2^127), truncated below 2^0
+__host__ __device__ __forceinline__ u128 mag_at(double x, long long unit) {
+  const unsigned long long bits = dbl_bits(x) & 0x7fffffffffffffffull;
+  const int ex = (int)(bits >> 52);
+  if (bits == 0) return 0;
+  const unsigned long long m = ex ? ((bits & 0xfffffffffffffull) | 0x10000000000000ull) : (bits & 0xfffffffffffffull);
+  const long long sh = (long long)(ex ? ex - 1075 : -1074) - unit;
+  if (sh >= 0) return sh < 75 ? (u128)m << sh : (u128)0;
+  return sh > -64 ? (u128)(m >> (-sh)) : (u128)0;
+}
+
+// top binary exponent of |x| (floor(log2 |x|)), x != 0 finite
+__host__ __device__ __forceinline__ long long top_exp(double x) {
+  const unsigned long long bits = dbl_bits(x) & 0x7fffffffffffffffull;
+  const int ex = (int)(bits >> 52);
+  if (ex) return ex - 1023;
+  unsigned long long m = bits & 0xfffffffffffffull;
+  int b = 0;
+  while (m >>= 1) ++b;
+  return -1074 + b;
+}
+
+// the complex value (rh + rl + i (ih + il)) 2^e as an xint, exactly (the
+// low parts at most 2^-50 of the high ones in magnitude, as in double-double)
+__host__ __device__ __forceinline__ xint xint_from_dd2(double rh, double rl, double ih, double il, long long e) {
+  long long t = LLONG_MIN;
+  if (rh != 0.0) t = top_exp(rh);
+  if (ih != 0.0 && top_exp(ih) > t) t = top_exp(ih);
+  if (t == LLONG_MIN) return xint_norm(0, 0, 0, 0, 0);
+  const long long unit = t - 123;  // top bit at 123: room for the low part and a carry
+  auto comp = [unit](double h, double l, u128 &m, int &sg) {
+    const u128 a = mag_at(h, unit), b = mag_at(l, unit);
+    const int sa = h < 0.0, sb = l < 0.0;
+    sadd128(a, a ? sa : 0, b, b ? sb : 0, m, sg);
+    if (!m) sg = 0;
+  };
+  u128 xr, xi;
+  int sr, si;
+  comp(rh, rl, xr, sr);
+  comp(ih, il, xi, si);
+  return xint_norm(xr, sr, xi, si, unit + e + 126);
+}
+
+// a + b
+__host__ __device__ __forceinline__ xint xint_add(const xint &a, const xint &b) {
+  if (!a.x && !a.y) return b;
+  if (!b.x && !b.y) return a;
+  const xint &hi = a.e >= b.e ? a : b, &lo = a.e >= b.e ? b : a;
+  const long long d = hi.e - lo.e;
+  const u128 lx = d < 128 ? (lo.x >> d) : (u128)0, ly = d < 128 ? (lo.y >> d) : (u128)0;
+  // operands below 2^127: halve both first so the sums cannot overflow
+  u128 rx, ry;
+  int sx, sy;
+  sadd128(hi.x >> 1, hi.sx, lx >> 1, lo.sx, rx, sx);
+  sadd128(hi.y >> 1, hi.sy, ly >> 1, lo.sy, ry, sy);
+  return xint_norm(rx, rx ? sx : 0, ry, ry ? sy : 0, hi.e + 1);
+}
+
+// 1/m for a complex m with max(|mr|, |mi|) in [0.5, 1): an FP64 seed
+// u0 = conj(m) / |m|^2 (relative error a few 2^-53), then one Newton step
+// u = u0 + u0 (1 - m u0) in fixed point, which squares the seed's error:
+// relative error about 2^-100.
+__host__ __device__ __forceinline__ xint recip_xint(double mr, double mi) {
+  const double inv = 1.0 / (mr * mr + mi * mi);
+  const xint u0 = xint_from_dd2(mr * inv, 0.0, -mi * inv, 0.0, 0);
+  const xint m = xint_from_dd2(mr, 0.0, mi, 0.0, 0);
+  const xint one = xint_norm((u128)1 << 126, 0, 0, 0, 0);
+  const xint e = xint_add(one, xint_neg(xint_mul(m, u0)));
+  return xint_add(u0, xint_mul(u0, e));
+}
+
+// the output format (fpe_xc64: max(|re|, |im|) in [0.5, 1)) from a
+// normalised xint, each component rounded to nearest at 53 bits
+__host__ __device__ __forceinline__ fpe_xc64 xc64_from_xint(const xint &v) {
+  fpe_xc64 o;
+  if (!v.x && !v.y) {
+    o.re = o.im = 0.0;
+    o.e = 0;
+    return o;
+  }
+  const unsigned long long hx = (unsigned long long)(v.x >> 74) + (unsigned long long)((v.x >> 73) & 1);
+  const unsigned long long hy = (unsigned long long)(v.y >> 74) + (unsigned long long)((v.y >> 73) & 1);
+  double re = (double)hx * 0x1p-53, im = (double)hy * 0x1p-53;  // exact: hx, hy <= 2^53
+  o.e = v.e + 1;
+  if (re == 1.0 || im == 1.0) {  // rounding carried into the next binade
+    re *= 0.5;
+    im *= 0.5;
+    o.e += 1;
+  }
+  o.re = v.sx ? -re : re;
+  o.im = v.sy ? -im : im;
+  return o;
+}
+
+// z^n (n >= 0) as an xint with z's binary exponent folded in
+__host__ __device__ __forceinline__ xint xint_pow_z(double zr, double zi, long long n, int f) {
+  if (n <= 0) return xint_norm((u128)1 << 126, 0, 0, 0, 0);
+#ifdef __CUDA_ARCH__
+  xint r = xint_pow_unit(scale2(zr, -f), scale2(zi, -f), n);
+#else
+  xint r = xint_pow_unit(ldexp(zr, -f), ldexp(zi, -f), n);
+#endif
+  r.e += (long long)f * n;
+  return r;
+}
+
 // the low 74 bits of a 128-bit magnitude, as a double scaled by 2^-74
 __host__ __device__ __forceinline__ double low74_scaled(u128 x) {
   const unsigned long long lo = (unsigned long long)x, up = (unsigned long long)(x >> 64) & 0x3ffull;
@@ -391,7 +474,8 @@ __device__ __forceinline__ xdd xdd_from_xint(const xint &v) {
   x.ih = (v.sy ? -hy : hy) * 0x1p-53;
   x.il = (v.sy ? -ly : ly) * 0x1p-53;
   x.e = v.e + 1;
-  return xdd_norm(x);
+  if (!v.x && !v.y) x.e = 0;
+  return x;  // max(|rh|, |ih|) is in [0.5, 1) already: the larger top bit is at 126
 }
 
 // z^n (n >= 0) as extended double-double, computed on the integer pipe.

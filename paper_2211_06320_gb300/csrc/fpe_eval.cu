@@ -340,7 +340,8 @@ __device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, 
 
 // Bottom-up Horner over trimmed indices [lo, hi] with multiplier 1/z:
 // returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-hi) = h * 2^rho(hi).
-// 1/z = u 2^ue with u in double-double.  Within piece j the step from k-1 to
+// 1/z = u 2^ue with u in extended double-double (u^3, u^4 likewise, each
+// with its own exponent).  Within piece j the step from k-1 to
 // k multiplies by v_j = 2^-beta_j / z; crossing from piece j to j+1 first
 // scales h by 2^-delta_j.  A single step is 8 FMA for complex z and
 // coefficients (v in double-double).
@@ -354,8 +355,8 @@ __device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, 
 // 3u of the block's term magnitudes) and the block step multiplies by v^4 in
 // double-double: 20 FMA per four terms instead of 32.  u3 = u^3, u4 = u^4.
 template <bool CC, bool CZ>
-__device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b, const cdd &u,
-                                                  const cdd &u3, const cdd &u4, bool blocks, int ue, double zr,
+__device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b, const xdd &u,
+                                                  const xdd &u3, const xdd &u4, bool blocks, int ue, double zr,
                                                   double zi, long long lo, long long hi, double &hr, double &hm,
                                                   long long &rho_hi) {
   int j = P.piece_first[lo >> P.log2_piece];
@@ -375,8 +376,9 @@ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double
   while (k <= hi) {
     const int beta = P.piece_beta[j];
     const int sh = ue - beta;
-    const double vhr = scale2(u.rh, sh), vlr = scale2(u.rl, sh);
-    const double vhi = CZ ? scale2(u.ih, sh) : 0.0, vli = CZ ? scale2(u.il, sh) : 0.0;
+    const int s1 = (int)u.e + sh;
+    const double vhr = scale2(u.rh, s1), vlr = scale2(u.rl, s1);
+    const double vhi = CZ ? scale2(u.ih, s1) : 0.0, vli = CZ ? scale2(u.il, s1) : 0.0;
     const long long kend = min((long long)P.piece_k0[j + 1] - 1, hi);
     // h <- h v + (br + i bi), v in double-double
     auto step_v = [&](double &xr, double &xm, double br, double bi) {
@@ -393,8 +395,9 @@ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double
     };
     if (blocks && kend - k + 1 >= 8 && sh > -200 && sh < 200) {  // v^4 and its low part stay normal
       const double wr = scale2(zr, beta), wi = CZ ? scale2(zi, beta) : 0.0;
-      const double ahr = scale2(u4.rh, 4 * sh), alr = scale2(u4.rl, 4 * sh);
-      const double ahi = CZ ? scale2(u4.ih, 4 * sh) : 0.0, ali = CZ ? scale2(u4.il, 4 * sh) : 0.0;
+      const int s4 = (int)u4.e + 4 * sh;
+      const double ahr = scale2(u4.rh, s4), alr = scale2(u4.rl, s4);
+      const double ahi = CZ ? scale2(u4.ih, s4) : 0.0, ali = CZ ? scale2(u4.il, s4) : 0.0;
       // s over [k, k + 3] by top-down Horner with w
       auto block_sum = [&](long long k0, double &sr, double &si) {
         double cr, ci, dr = 0.0, dm = 0.0;
@@ -423,8 +426,9 @@ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double
         hm = ni;
       }
       // h = v^3 G
-      const double chr = scale2(u3.rh, 3 * sh), clr = scale2(u3.rl, 3 * sh);
-      const double chi = CZ ? scale2(u3.ih, 3 * sh) : 0.0, cli = CZ ? scale2(u3.il, 3 * sh) : 0.0;
+      const int s3 = (int)u3.e + 3 * sh;
+      const double chr = scale2(u3.rh, s3), clr = scale2(u3.rl, s3);
+      const double chi = CZ ? scale2(u3.ih, s3) : 0.0, cli = CZ ? scale2(u3.il, s3) : 0.0;
       double nr, ni;
       if (CZ) {
         nr = fma(hr, chr, fma(-hm, chi, fma(hr, clr, -hm * cli)));
@@ -455,20 +459,15 @@ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double
   rho_hi = P.piece_rho0[j] + (long long)P.piece_beta[j] * (hi - P.piece_k0[j]);
 }
 
-__device__ __forceinline__ xdd xdd_from_cdd(const cdd &u, int ue) {
-  xdd x = {u.rh, u.rl, u.ih, u.il, ue};
-  return xdd_norm(x);
-}
-
 // sum_{k=lo}^{hi} a_k z^(k - base) in extended double-double for a range on
 // either side of the peak kl or straddling it.  The part at or above kl is
 // summed top-down (relative to z^max(kl, lo)), the part below bottom-up
 // (relative to z^(its top index)); base is kl - 1 when both parts exist.
 template <bool CC, bool CZ>
-__device__ __forceinline__ xdd range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
-                                         const cdd &u, long long lo, long long hi, long long kl, long long &base) {
+__device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
+                                          const xint &u, long long lo, long long hi, long long kl, long long &base) {
   constexpr long long kBlockMin = 16;  // below-peak terms from which the blocked pass pays for u^3, u^4
-  xdd X = xdd_zero();
+  xint X = xint_norm(0, 0, 0, 0, 0);
   const long long top_lo = max(kl, lo);
   const long long low_hi = min(top_lo - 1, hi);
   const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
@@ -476,22 +475,23 @@ __device__ __forceinline__ xdd range_sum(const DevPoly &P, double zr, double zi,
     double hr, hm, cr, cm;
     long long rho;
     window_horner<CC, CZ, false>(P, P.b, zr, zi, top_lo, hi, hr, hm, cr, cm, rho);
-    if (hr != 0.0 || hm != 0.0) X = xdd_from(hr, hm, rho);
+    X = xint_from_dd2(hr, 0.0, hm, 0.0, rho);
     base = top_lo;
   }
   if (has_low) {
     double hr, hm;
     long long rho;
     const bool blocks = low_hi - lo + 1 >= kBlockMin;
-    cdd u3 = u, u4 = u;
-    if (blocks) {
-      const cdd u2 = cdd_mul(u, u);
-      u3 = cdd_mul(u2, u);
-      u4 = cdd_mul(u2, u2);
+    const xdd u1 = xdd_from_xint(u);
+    xdd u3 = u1, u4 = u1;
+    if (blocks) {  // powers of 1/m on the integer pipe
+      const xint u2 = xint_sqr(u);
+      u3 = xdd_from_xint(xint_mul(u2, u));
+      u4 = xdd_from_xint(xint_sqr(u2));
     }
-    window_horner_rev<CC, CZ>(P, P.b, u, u3, u4, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho);
-    if (has_up && (X.rh != 0.0 || X.ih != 0.0)) X = xdd_mul_d(X, mr, mi, f);  // z^top_lo = z * z^low_hi
-    if (hr != 0.0 || hm != 0.0) X = xdd_add(X, xdd_from(hr, hm, rho));
+    window_horner_rev<CC, CZ>(P, P.b, u1, u3, u4, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho);
+    if (has_up && (X.x || X.y)) X = xint_mul(X, xint_from_dd2(mr, 0.0, mi, 0.0, f));  // z^top_lo = z * z^low_hi
+    X = xint_add(X, xint_from_dd2(hr, 0.0, hm, 0.0, rho));
     base = low_hi;
   }
   return X;
@@ -746,18 +746,17 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
       o.im = v.i;
       o.e = v.e;
     } else {
-      xdd X;
       if (ACC) {
-        X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
-      } else {
+        const xdd X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
+        o = xdd_out(xdd_mul(X, xdd_pow_int(r.zr, r.zi, base + P.v)));
+      } else {  // bookkeeping in fixed point (integer pipe): 1/z, its powers, the final product
         const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
         const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
-        cdd u = {0.0, 0.0, 0.0, 0.0};
-        if (r.lo < r.kl) u = recip_dd(mr, mi);
-        X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+        xint u = xint_norm(0, 0, 0, 0, 0);
+        if (r.lo < r.kl) u = recip_xint(mr, mi);
+        const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
+        o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, r.zi, base + P.v, f)));
       }
-      xdd pw = xdd_pow_int(r.zr, r.zi, base + P.v);
-      o = xdd_out(xdd_mul(X, pw));
     }
   }
   out[r.orig] = o;
@@ -790,6 +789,25 @@ __device__ __forceinline__ xdd shfl_up_xdd(xdd x, int s) {
   y.il = __shfl_up_sync(0xffffffffu, x.il, s);
   y.e = __shfl_up_sync(0xffffffffu, x.e, s);
   return y;
+}
+
+// warp shuffles of an xint: mode 0 up, 1 down, 2 xor
+__device__ __forceinline__ xint shfl_xint(const xint &v, int sft, int mode) {
+  auto sh64 = [sft, mode](unsigned long long x) -> unsigned long long {
+    return mode == 0 ? __shfl_up_sync(0xffffffffu, x, sft)
+                     : (mode == 1 ? __shfl_down_sync(0xffffffffu, x, sft) : __shfl_xor_sync(0xffffffffu, x, sft));
+  };
+  auto sh32 = [sft, mode](int x) -> int {
+    return mode == 0 ? __shfl_up_sync(0xffffffffu, x, sft)
+                     : (mode == 1 ? __shfl_down_sync(0xffffffffu, x, sft) : __shfl_xor_sync(0xffffffffu, x, sft));
+  };
+  xint r;
+  r.x = ((u128)sh64((unsigned long long)(v.x >> 64)) << 64) | sh64((unsigned long long)v.x);
+  r.y = ((u128)sh64((unsigned long long)(v.y >> 64)) << 64) | sh64((unsigned long long)v.y);
+  r.sx = sh32(v.sx);
+  r.sy = sh32(v.sy);
+  r.e = (long long)sh64((unsigned long long)v.e);
+  return r;
 }
 
 // Long windows: warp groups.  A window of length L gets ng = ceil(L / (32 lane_chunk))
@@ -869,35 +887,43 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
     gout_out = xdd_from_xd(go);
     return;
   }
-  xdd sv = xdd_zero(), carry = xdd_zero();
   if (ACC) {
+    xdd sv = xdd_zero();
     if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
-  } else if (clo <= chi) {
-    const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+    if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
+    for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
+    sv_out = sv;
+    gout_out = xdd_zero();
+    return;
+  }
+  // the bookkeeping in fixed point on the integer pipe: 1/z, the carries,
+  // the lanes' powers and the butterfly
+  const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+  const xint zero = xint_norm(0, 0, 0, 0, 0);
+  xint sv = zero, carry = zero;
+  if (clo <= chi) {
     const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
-    const cdd u = recip_dd(mr, mi);
+    const xint u = recip_xint(mr, mi);
     long long base;
-    xdd X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
+    const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
     if (chi < r.kl) {
-      carry = xdd_mul(X, xdd_from_cdd(u, -f));  // below the peak: X / z to the next slot
+      carry = xint_mul(X, u);  // below the peak: X / z to the next slot
+      carry.e -= f;
     } else if (base > clo) {
-      sv = xdd_mul(X, xdd_pow_int(r.zr, r.zi, base - clo));
+      sv = xint_mul(X, xint_pow_z(r.zr, r.zi, base - clo, f));
     } else {
       sv = X;
     }
   }
-  xdd gout = xdd_zero();
-  if (!ACC) {
-    xdd inc = shfl_up_xdd(carry, 1);
-    if (lane > 0) sv = xdd_add(sv, inc);
-    gout = shfl_down_xdd(carry, 31);  // lane 31's carry, read by lane 0
-  }
-  // sum_i (z^C)^i s_i: each lane scales its slot by its own power (integer
-  // pipe), then a butterfly adds the 32 slots with every lane busy
-  if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
-  for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
-  sv_out = sv;
-  gout_out = gout;
+  const xint inc = shfl_xint(carry, 1, 0);
+  if (lane > 0) sv = xint_add(sv, inc);
+  const xint gout = shfl_xint(carry, 31, 1);  // lane 31's carry, read by lane 0
+  // sum_i (z^C)^i s_i: each lane scales its slot by its own power, then a
+  // butterfly adds the 32 slots with every lane busy
+  if (lane > 0 && (sv.x || sv.y)) sv = xint_mul(sv, xint_pow_z(r.zr, r.zi, lane * C, f));
+  for (int s = 16; s >= 1; s >>= 1) sv = xint_add(sv, shfl_xint(sv, s, 2));
+  sv_out = xdd_from_xint(sv);
+  gout_out = xdd_from_xint(gout);
 }
 
 // A long window with one group: its value times z^(l + v), written by one thread.
