@@ -255,6 +255,30 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
                               fpe_tuning *best);
 
 /*
+ * Tensor-core window sums (the same Q_lambda(z) of Alg. A_p line 11,
+ * eq. reducedQlambda, computed on another unit; the paper has no
+ * counterpart).  In the FP64 default mode (not FPE_FP32, not FPE_ACCURATE),
+ * fpe_eval sums every window of at least min_window terms that lies inside
+ * one of the polynomial's longest (up to four) coefficient pieces with an
+ * integer cover slope on the bf16 tensor cores: coefficients and point
+ * powers are cut into exact 7-bit slices whose products are added exactly,
+ * and blocks of 32 terms are combined in 128-bit fixed point.  Points are
+ * grouped 128 at a time by log2|z|; a group also sums the terms of its
+ * neighbours' windows (all of them below the window threshold), and a group
+ * whose |z| spread is too wide for one shared scaling goes back to the FP64
+ * kernels.  The error stays below 2^-54 sum |a_k||z|^k.
+ *
+ * fpe_set_tensor_path: min_window in {0} or [32, 2^30]; 0 turns the path
+ *   off.  Default 64.  Applies to later fpe_eval calls of that handle
+ *   (not to fpe_eval_noalloc, the batch or the gradient paths).
+ *   FPE_ERR_INVALID_ARG for a NULL handle or a value out of range.
+ * fpe_get_tensor_path: the handle's current min_window, and in *n_pieces the
+ *   number of its pieces that qualify (0: the path never runs for it).
+ */
+fpe_status fpe_set_tensor_path(fpe_poly_t P, int64_t min_window);
+fpe_status fpe_get_tensor_path(fpe_poly_t P, int64_t *min_window, int32_t *n_pieces);
+
+/*
  * fpe_newton -- one Newton step N_P(z) = z - P(z)/P'(z) (§7.2, eq. newton) at n
  * points.  P(z) and P'(z) are evaluated by the FPE path as extended-exponent
  * values, so the increment P/P' never overflows where P and P' do (the

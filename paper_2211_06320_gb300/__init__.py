@@ -40,6 +40,7 @@ EXPORTED = [
     "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
     "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex", "fpe_analyse",
     "fpe_set_tuning", "fpe_get_tuning", "fpe_autotune", "fpe_batch_set_tuning", "fpe_batch_autotune",
+    "fpe_set_tensor_path", "fpe_get_tensor_path",
 ]
 
 
@@ -109,6 +110,8 @@ def _load():
         "fpe_autotune": ([P, P, P, I64, P, ctypes.POINTER(Tuning)], I32),
         "fpe_batch_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "fpe_batch_autotune": ([P, P, P, P, ctypes.POINTER(Tuning)], I32),
+        "fpe_set_tensor_path": ([P, I64], I32),
+        "fpe_get_tensor_path": ([P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -390,6 +393,17 @@ def fpe_get_tuning(P: Poly) -> dict:
     t = Tuning()
     _check(_load().fpe_get_tuning(P.handle, ctypes.byref(t)), "fpe_get_tuning")
     return t.as_dict()
+
+
+def fpe_set_tensor_path(P: Poly, min_window: int):
+    """Tensor-core window sums for windows of at least min_window terms (0: off)."""
+    _check(_load().fpe_set_tensor_path(P.handle, int(min_window)), "fpe_set_tensor_path")
+
+
+def fpe_get_tensor_path(P: Poly) -> dict:
+    mw, npc = ctypes.c_int64(), ctypes.c_int32()
+    _check(_load().fpe_get_tensor_path(P.handle, ctypes.byref(mw), ctypes.byref(npc)), "fpe_get_tensor_path")
+    return {"min_window": int(mw.value), "pieces": int(npc.value)}
 
 
 def fpe_autotune(P: Poly, z_re, z_im=None, stream=None) -> dict:

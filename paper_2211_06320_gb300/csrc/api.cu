@@ -340,6 +340,25 @@ fpe_status fpe_get_tuning(fpe_poly_t P, fpe_tuning *t) {
   return FPE_OK;
 }
 
+fpe_status fpe_set_tensor_path(fpe_poly_t P, int64_t min_window) {
+  if (!P || (min_window != 0 && (min_window < 32 || min_window > ((int64_t)1 << 30)))) {
+    set_error("fpe_set_tensor_path: NULL handle, or min_window not 0 and outside [32, 2^30]");
+    return FPE_ERR_INVALID_ARG;
+  }
+  P->tune.tc_min_window = min_window;
+  return FPE_OK;
+}
+
+fpe_status fpe_get_tensor_path(fpe_poly_t P, int64_t *min_window, int32_t *n_pieces) {
+  if (!P) {
+    set_error("fpe_get_tensor_path: NULL handle");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if (min_window) *min_window = P->tune.tc_min_window;
+  if (n_pieces) *n_pieces = P->dev.n_tc;
+  return FPE_OK;
+}
+
 fpe_status fpe_autotune(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, void *cuda_stream,
                         fpe_tuning *best) {
   fpe_tuning dummy;

@@ -839,4 +839,32 @@ __device__ __forceinline__ fpe_xc64 xdd_out(xdd x) {
   return o;
 }
 
+// ---------------------------------------------------------------------------
+// Lists a long-window point and reserves its warp groups: group 0 lives in
+// slot i (its list index), groups 1.. in extra slots; when the extra slots run
+// out the window gets one group and the slots of its failed reservation that
+// exist are marked unused (-1).
+__device__ __forceinline__ void list_long_window(long long L, long long span, uint32_t pos, uint32_t *cnt,
+                                                 int32_t *long_list, int32_t *long_ngroups, int32_t *long_gbase,
+                                                 int32_t *extra_owner, int32_t *extra_group, int extra_cap) {
+  uint32_t i = atomicAdd(&cnt[kCntLong], 1u);
+  long_list[i] = (int32_t)pos;
+  int ng = (int)min((L + span - 1) / span, 0x7fffLL);  // the upper 16 bits count finished groups
+  int gb = 0;
+  if (ng > 1) {
+    gb = (int)atomicAdd(&cnt[kCntExtra], (uint32_t)(ng - 1));
+    if (gb + ng - 1 > extra_cap) {
+      for (int g = 1; g < ng && gb + g - 1 < extra_cap; ++g) extra_owner[gb + g - 1] = -1;
+      ng = 1;
+    } else {
+      for (int g = 1; g < ng; ++g) {
+        extra_owner[gb + g - 1] = (int32_t)i;
+        extra_group[gb + g - 1] = g;
+      }
+    }
+  }
+  long_ngroups[i] = ng;
+  long_gbase[i] = gb;
+}
+
 }  // namespace fpe

@@ -143,11 +143,35 @@ __device__ __forceinline__ uint32_t bucket_of(double lam, int flags) {
   return (uint32_t)min(max(b, 0), kNumBins - 1);
 }
 
+// Bucket of a point whose window [lo, hi] (trimmed) qualifies for the
+// tensor-core sums: at least tc_min_window terms inside one tensor-core piece
+// r.  Bins kNumBins + r kTcBinsPerPiece + [0, kTcBinsPerPiece) order mu =
+// lambda + beta logarithmically (256 bins per binade of |mu| over
+// [2^-24, 2^8], negative mu first), so consecutive points share windows.
+__device__ __forceinline__ bool tc_bucket(const DevPoly &P, long long lo, long long hi, double lam,
+                                          long long tc_min_window, uint32_t &key) {
+  if (hi - lo + 1 < tc_min_window) return false;
+  int j = P.piece_first[lo >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= lo) ++j;
+  if (P.piece_k0[j + 1] <= hi) return false;
+  int r = -1;
+  for (int q = 0; q < P.n_tc && q < kTcMaxPieces; ++q)
+    if (P.tc_piece[q] == j) r = q;
+  if (r < 0) return false;
+  const double mu = lam + (double)P.piece_beta[j];
+  const float a = (float)fabs(mu);
+  int h = 0;
+  if (a >= 0x1p-24f) h = min((int)((log2f(a) + 24.0f) * 256.0f), kTcBinsPerPiece / 2 - 1);
+  const int b = mu < 0.0 ? kTcBinsPerPiece / 2 - 1 - h : kTcBinsPerPiece / 2 + h;
+  key = (uint32_t)(kNumBins + r * kTcBinsPerPiece + b);
+  return true;
+}
+
 template <bool CZ>
 __global__ void k_locate(DevPoly P, int n, const double *__restrict__ zre, const double *__restrict__ zim,
                          long long *__restrict__ lo_out, long long *__restrict__ hi_out,
                          long long *__restrict__ kl_out, double *__restrict__ N_out, uint32_t *__restrict__ key,
-                         uint32_t *__restrict__ hist) {
+                         uint32_t *__restrict__ hist, long long tc_min_window) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double zr = zre[p], zi = CZ ? zim[p] : 0.0;
@@ -157,21 +181,20 @@ __global__ void k_locate(DevPoly P, int n, const double *__restrict__ zre, const
   kl_out[p] = w.kl;
   N_out[p] = w.flags ? 0.0 : w.N + w.lam * (double)P.v;
   uint32_t k = bucket_of(w.lam, w.flags);
+  if (tc_min_window > 0 && !w.flags) tc_bucket(P, w.lo, w.hi, w.lam, tc_min_window, k);
   key[p] = k;
   atomicAdd(&hist[k], 1u);
 }
 
-// exclusive scan of the histogram into cursors; resets the long-window counters
-__global__ void k_scan_bins(uint32_t *bins) {
+// exclusive scan of the nbins-word histogram (a multiple of 1024) into
+// cursors; resets the counters and records where each tensor-core piece's
+// points start in bucketed order
+__global__ void k_scan_bins(uint32_t *bins, int nbins) {
   __shared__ uint32_t part[1024];
-  const int per = kNumBins / 1024;
+  const int per = nbins / 1024;
   int t = threadIdx.x;
-  uint32_t loc[kNumBins / 1024];
   uint32_t s = 0;
-  for (int i = 0; i < per; ++i) {
-    loc[i] = bins[t * per + i];
-    s += loc[i];
-  }
+  for (int i = 0; i < per; ++i) s += bins[t * per + i];
   part[t] = s;
   __syncthreads();
   for (int off = 1; off < 1024; off <<= 1) {
@@ -182,37 +205,17 @@ __global__ void k_scan_bins(uint32_t *bins) {
   }
   uint32_t run = part[t] - s;
   for (int i = 0; i < per; ++i) {
-    bins[kNumBins + t * per + i] = run;
-    run += loc[i];
+    const uint32_t c = bins[t * per + i];
+    bins[nbins + t * per + i] = run;
+    run += c;
   }
-  if (t < kNumCounters) bins[2 * kNumBins + t] = 0;
-}
-
-// Lists a long-window point and reserves its warp groups: group 0 lives in
-// slot i (its list index), groups 1.. in extra slots; when the extra slots run
-// out the window gets one group and the slots of its failed reservation that
-// exist are marked unused (-1).
-__device__ __forceinline__ void list_long_window(long long L, long long span, uint32_t pos, uint32_t *cnt,
-                                                 int32_t *long_list, int32_t *long_ngroups, int32_t *long_gbase,
-                                                 int32_t *extra_owner, int32_t *extra_group, int extra_cap) {
-  uint32_t i = atomicAdd(&cnt[kCntLong], 1u);
-  long_list[i] = (int32_t)pos;
-  int ng = (int)min((L + span - 1) / span, 0x7fffLL);  // the upper 16 bits count finished groups
-  int gb = 0;
-  if (ng > 1) {
-    gb = (int)atomicAdd(&cnt[kCntExtra], (uint32_t)(ng - 1));
-    if (gb + ng - 1 > extra_cap) {
-      for (int g = 1; g < ng && gb + g - 1 < extra_cap; ++g) extra_owner[gb + g - 1] = -1;
-      ng = 1;
-    } else {
-      for (int g = 1; g < ng; ++g) {
-        extra_owner[gb + g - 1] = (int32_t)i;
-        extra_group[gb + g - 1] = g;
-      }
-    }
+  uint32_t *cnt = bins + 2 * nbins;
+  if (t < kNumCounters) cnt[t] = 0;
+  __syncthreads();
+  if (t <= kTcMaxPieces) {
+    const int b = kNumBins + t * kTcBinsPerPiece;
+    cnt[kCntTcStart + t] = (t < kTcMaxPieces && b < nbins) ? bins[nbins + b] : part[1023];
   }
-  long_ngroups[i] = ng;
-  long_gbase[i] = gb;
 }
 
 template <bool CZ>
@@ -223,10 +226,11 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
                           PointRec *__restrict__ rec, int32_t *__restrict__ long_list,
                           int32_t *__restrict__ long_ngroups, int32_t *__restrict__ long_gbase,
                           int32_t *__restrict__ extra_owner, int32_t *__restrict__ extra_group, int extra_cap,
-                          int32_t *status, long long long_window, long long span) {
+                          int32_t *status, long long long_window, long long span, int nbins) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  uint32_t pos = atomicAdd(&bins[kNumBins + key[p]], 1u);
+  const uint32_t kp = key[p];
+  uint32_t pos = atomicAdd(&bins[nbins + kp], 1u);
   PointRec r;
   r.zr = zre[p];
   r.zi = CZ ? zim[p] : 0.0;
@@ -245,9 +249,10 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
   r.orig = p;
   r.pid = 0;
   r.pad = 0;
+  if (!r.flags && kp >= (uint32_t)kNumBins) r.flags = kPointTC;  // summed by the tensor-core kernels
   rec[pos] = r;
   if (!r.flags && r.hi - r.lo + 1 > long_window)
-    list_long_window(r.hi - r.lo + 1, span, pos, bins + 2 * kNumBins, long_list, long_ngroups, long_gbase,
+    list_long_window(r.hi - r.lo + 1, span, pos, bins + 2 * nbins, long_list, long_ngroups, long_gbase,
                      extra_owner, extra_group, extra_cap);
 }
 
@@ -834,6 +839,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, 
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const PointRec r = rec[q];
+  if (r.flags & kPointTC) return;
   if (r.flags || r.hi - r.lo + 1 <= long_window) sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
 }
 
@@ -1145,7 +1151,7 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
                          cudaStream_t st) {
   Workspace &w = P->ws;
   const int cap = (int)w.cap, xcap = (int)w.extra_cap;
-  uint32_t *cnt = w.bins + 2 * kNumBins;
+  uint32_t *cnt = w.bins + 2 * w.nbins;
   {
     ProfScope ps("k_sum_short", st);
     k_sum_short<CC, CZ, ACC, F32, false><<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms,
@@ -1175,26 +1181,33 @@ static void launch_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, in
     launch_sums4<CC, CZ, false, false>(P, n, out, nterms, bits_lost, st);
 }
 
-// locate, bucket and scatter the points into P->ws.rec (the front of fpe_eval)
-fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, cudaStream_t st) {
+// locate, bucket and scatter the points into P->ws.rec (the front of fpe_eval);
+// with allow_tc, windows that qualify for the tensor-core sums are bucketed
+// apart and marked kPointTC
+fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, cudaStream_t st,
+                        bool allow_tc) {
   fpe_status s = ensure_workspace(P, n64);
   if (s != FPE_OK) return s;
   const int n = (int)n64;
   Workspace &w = P->ws;
   const bool cz = z_im != nullptr;
-  cudaError_t e = cudaMemsetAsync(w.bins, 0, kNumBins * sizeof(uint32_t), st);
+  const bool tc = allow_tc && tc_enabled(P, cz);
+  if (tc && (s = ensure_tc_workspace(P, n64)) != FPE_OK) return s;
+  w.nbins = tc ? kNumBins + kTcBins : kNumBins;
+  const long long tcw = tc ? (long long)P->tune.tc_min_window : 0;
+  cudaError_t e = cudaMemsetAsync(w.bins, 0, w.nbins * sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   const int nb = (n + 255) / 256;
   {
     ProfScope ps("k_locate", st);
     if (cz)
-      k_locate<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+      k_locate<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, tcw);
     else
-      k_locate<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+      k_locate<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, tcw);
   }
   {
     ProfScope ps("k_scan_bins", st);
-    k_scan_bins<<<1, 1024, 0, st>>>(w.bins);
+    k_scan_bins<<<1, 1024, 0, st>>>(w.bins, w.nbins);
   }
   {
     ProfScope ps("k_scatter", st);
@@ -1202,26 +1215,28 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
       k_scatter<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                           w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                           w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
-                                          P->tune.group_span());
+                                          P->tune.group_span(), w.nbins);
     else
       k_scatter<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                            w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                            w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
-                                           P->tune.group_span());
+                                           P->tune.group_span(), w.nbins);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  if (tc) return launch_tc_plan(P, n, st);
   return FPE_OK;
 }
 
 fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n64, fpe_xc64 *out,
                        int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
   if (n64 == 0) return FPE_OK;
-  fpe_status s = launch_front(P, z_re, z_im, n64, st);
+  fpe_status s = launch_front(P, z_re, z_im, n64, st, true);
   if (s != FPE_OK) return s;
   const int n = (int)n64;
   const bool cz = z_im != nullptr;
   const bool cc = P->complex_coef;
+  const bool tc = P->ws.nbins > kNumBins;
   if (cc && cz)
     launch_sums<true, true>(P, n, out, nterms, bits_lost, st);
   else if (cc)
@@ -1230,6 +1245,7 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
     launch_sums<false, true>(P, n, out, nterms, bits_lost, st);
   else
     launch_sums<false, false>(P, n, out, nterms, bits_lost, st);
+  if (tc && (s = launch_tc_sums(P, n, out, nterms, bits_lost, st)) != FPE_OK) return s;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   P->last_n = n64;
@@ -1498,20 +1514,20 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
       s = cuda_fail(e, "cudaMemsetAsync");
     } else {
       if (cz)
-        k_locate<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
+        k_locate<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, 0);
       else
-        k_locate<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins);
-      k_scan_bins<<<1, 1024, 0, st>>>(w.bins);
+        k_locate<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, 0);
+      k_scan_bins<<<1, 1024, 0, st>>>(w.bins, kNumBins);
       if (cz)
         k_scatter<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                             w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                             w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
-                                            P->tune.group_span());
+                                            P->tune.group_span(), kNumBins);
       else
         k_scatter<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
                                              w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                              w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
-                                             P->tune.group_span());
+                                             P->tune.group_span(), kNumBins);
       const int cap = (int)w.cap, xcap = (int)w.extra_cap;
       const bool acc = P->dev.accurate != 0;
 #define FPE_NOALLOC_SUMS(CCv, CZv, ACCv, F32v)                                                                 \

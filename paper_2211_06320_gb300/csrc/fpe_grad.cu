@@ -355,10 +355,10 @@ fpe_status launch_grad_coeffs(fpe_poly_s *P, const double *z_re, const double *z
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int blocks = std::max(sms, 1) * 8;
     if (z_im)
-      k_grad_coeffs_long<true><<<blocks, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.bins + 2 * kNumBins, g_re, g_im,
+      k_grad_coeffs_long<true><<<blocks, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.bins + 2 * w.nbins, g_re, g_im,
                                                        ga_re, ga_im);
     else
-      k_grad_coeffs_long<false><<<blocks, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.bins + 2 * kNumBins, g_re,
+      k_grad_coeffs_long<false><<<blocks, 128, 0, st>>>(P->dev, w.rec, w.long_list, w.bins + 2 * w.nbins, g_re,
                                                         g_im, ga_re, ga_im);
   }
   cudaError_t e = cudaGetLastError();

@@ -67,8 +67,23 @@ constexpr int64_t kMaxLaneChunk = 1024;
 struct Tuning {
   int64_t long_window = kLongWindow;
   int64_t lane_chunk = kMaxLaneChunk;
+  int64_t tc_min_window = 64;  // tensor-core window sums for windows of at least this many terms (0: off)
   int64_t group_span() const { return 32 * lane_chunk; }
 };
+
+// Tensor-core window sums (fpe_tc.cu).  Windows of at least tc_min_window
+// terms that lie inside one long merged piece (an integer cover slope) are
+// summed as exact integer products of 7-bit slices on the bf16 tensor cores.
+// Their points are bucketed separately: kTcBinsPerPiece bins per such piece
+// (at most kTcMaxPieces per polynomial), on a logarithmic scale of
+// mu = log2|z| + beta, so consecutive points have nearly equal windows.
+constexpr int kTcMaxPieces = 4;
+constexpr int kTcBinsPerPiece = 16384;
+constexpr int kTcBins = kTcMaxPieces * kTcBinsPerPiece;
+constexpr int kTcMinPieceLen = 64;  // shorter pieces never get the tensor path
+constexpr int kTcPoints = 64;       // points per tile (one CTA)
+constexpr int kTcItemsPerSm = 16;   // work items per SM the planner aims at (at least)
+constexpr int kTcMinChunk = 256;    // blocks (of 32 terms) per work item, at least
 
 // Batched evaluation: lambda bins per polynomial (segmented bucketing).
 constexpr int kBatchBins = 32;
@@ -78,7 +93,11 @@ constexpr int kCntLong = 0;        // long-window points listed
 constexpr int kCntGroupWork = 1;   // group work cursor
 constexpr int kCntExtra = 2;       // extra group slots reserved (groups 1.. of very long windows)
 constexpr int kCntFinal = 3;       // finalize cursor
-constexpr int kNumCounters = 8;
+constexpr int kCntTcStart = 4;     // 5 words: bucketed start of each tensor-core piece's points, then n
+constexpr int kCntTcWork = 9;      // tensor-core work cursor
+constexpr int kCntTcItems = 10;    // tensor-core work items
+constexpr int kCntTcChunk = 11;    // blocks per tensor-core work item
+constexpr int kNumCounters = 16;
 
 // Device view of a preconditioned polynomial, passed to kernels by value.
 struct DevPoly {
@@ -107,6 +126,8 @@ struct DevPoly {
   int32_t log2_piece;  // kLog2PieceLen or kLog2PieceLenF32
   double a0_re, a0_im;  // a_0 as a normalised mantissa (0 when v > 0)
   int64_t a0_e;
+  int32_t tc_piece[kTcMaxPieces];  // pieces eligible for the tensor-core window sums
+  int32_t n_tc;                    // how many (0: none)
 };
 
 // One evaluation point after location, in bucketed order.
@@ -122,6 +143,7 @@ struct PointRec {
 };
 constexpr int32_t kPointZero = 1;
 constexpr int32_t kPointNonFinite = 2;
+constexpr int32_t kPointTC = 4;  // summed by the tensor-core kernels
 
 // Device status word bits.
 constexpr int32_t kStatusNonFinite = 1;
@@ -142,7 +164,17 @@ struct Workspace {
   void *group_val = nullptr;        // per group: value (40-byte extended double-double)
   void *group_carry = nullptr;      // per group: carry into the next group
   int64_t extra_cap = 0;            // extra group slots (after the cap group-0 slots)
-  uint32_t *bins = nullptr;         // 2 * kNumBins histogram words + kNumCounters counters
+  uint32_t *bins = nullptr;         // 2 * nbins histogram words + kNumCounters counters
+  int nbins = kNumBins;             // bins of the last front pass (kNumBins, or + kTcBins with the tensor path)
+  void *tc_tiles = nullptr;         // TcTile per tile
+  int32_t *tc_item_base = nullptr;  // first work item of each tile (tiles + 1 entries)
+  void *tc_slots = nullptr;         // per work item and tile point: the chunk's value (xint)
+  void *tc_points = nullptr;        // TcPoint per tile point
+  int32_t *tc_item_tile = nullptr;  // tile of each work item
+  void *tc_taus = nullptr;          // TcTau per tile
+  void *tc_z = nullptr;             // Z' slices per tile
+  void *tc_groups = nullptr;        // TcGroup per group of bins
+  int64_t tc_cap = 0;               // points the tensor-core arrays are sized for
   void *host_pinned = nullptr;   // staging for fpe_eval_host
   size_t host_pinned_bytes = 0;
   void *dev_io = nullptr;        // device staging for fpe_eval_host
@@ -202,11 +234,20 @@ void free_handle(fpe_poly_s *P);
 fpe_status ensure_workspace(fpe_poly_s *P, int64_t n);
 
 // fpe_eval.cu
-fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, cudaStream_t st);
+fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, cudaStream_t st,
+                        bool allow_tc = false);
 fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                        int32_t *nterms, int32_t *bits_lost, cudaStream_t st);
 fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
                         cudaStream_t st);
+// fpe_tc.cu: the tensor-core window sums of the points launch_front marked kPointTC
+// (tc_plan runs before the other window kernels: it hands back tiles it rejects)
+bool tc_enabled(const fpe_poly_s *P, bool complex_points);
+fpe_status ensure_tc_workspace(fpe_poly_s *P, int64_t n);
+fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st);
+fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
+                          cudaStream_t st);
+void free_tc_workspace(Workspace &w);
 // fpe_grad.cu
 fpe_status launch_newton(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *inc,
                          double *znr, double *zni, cudaStream_t st);

@@ -1,0 +1,834 @@
+// Window sums of Algorithm A_p (line 11: Q_lambda(z) = sum of a_k z^k over
+// G_p ∩ [l, r], eq. reducedQlambda) on the tensor cores, for the long windows
+// of FP64 evaluations.
+//
+// The FP64 pipe of this GPU retires about 1.8 lane-FMA per cycle per SM; its
+// bf16 tensor cores (mma.sync, fp32 accumulation) about 1000 multiply-adds.
+// A window sum over points that share a coefficient window is a dense
+// contraction, so it is moved there with every product exact:
+//
+//   Blocks.  The window is cut into blocks of 32 terms on a grid fixed by the
+//   piece's first index k0.  For block m (terms k = k0 + 32 m + i) and point z,
+//     C_m = sum_i b_k w^i,  w = 2^beta z  (b_k = a_k 2^-rho(k) on the piece),
+//   and the window sum is sum_m C_m W^m with W = w^32.
+//
+//   Tilt.  The points of a tile (up to 128, bucketed by mu = log2|w|) share a
+//   real tilt tau = 2^c with c near their mu: A'_{m,i} = b_k tau^i and
+//   Z'_i = u^i with u = w / tau, so A' Z' = b_k w^i, |u| is close to 1 and the
+//   products are balanced (the largest |A'| times the largest |Z'| is within
+//   2^(62 |mu - c|) of the block's largest term).
+//
+//   Slices.  Each component of A' (per block) and of Z' (per point) is a
+//   70-bit fixed-point number relative to a power of two above its block's or
+//   point's largest component, cut into ten 7-bit slices q_0..q_9 (exact in
+//   bf16).  A slice product q q' < 2^14; a 64-long dot product of slices is an
+//   integer below 2^20, and the at most ten slice pairs with the same
+//   s + s' = t add up below 2^24: fp32 accumulation is exact.  Pairs with
+//   t <= 9 are kept (55 of 100); the dropped ones and the truncation leave an
+//   error below 2^-66 per product relative to the scales.
+//
+//   Combination.  The ten integer accumulators of each (block, point) are
+//   joined into a 128-bit integer, and the blocks are combined by Horner's
+//   scheme in 128-bit fixed point (xint) on the integer pipe, where the order
+//   of summation does not matter for the error.
+//
+// Error per window: below 2^-54 times S(z) for tiles with 31 |mu - c| <= 2,
+// which the planner enforces (other tiles go back to the FP64 kernels).
+//
+// MMA layout (m16n8k16, A row-major 16 x 16, B column 16 x 8): the 16 rows of
+// A are 8 blocks x (real part, imaginary part) of the output, the 8 columns
+// of B are 8 points, and the contraction index kappa runs over the 32 terms'
+// (real, imaginary) point powers:
+//   out_re = sum_i (A'_re Z'_re - A'_im Z'_im),  out_im = sum_i (A'_im Z'_re + A'_re Z'_im).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "fpe_device.cuh"
+#include "fpe_internal.h"
+
+namespace fpe {
+
+namespace {
+
+constexpr int kTB = 32;                      // terms per block
+constexpr int kTK = 2 * kTB;                 // contraction length (re, im per term)
+constexpr int kSl = 10;                      // 7-bit slices per operand
+constexpr int kSub = 8;                      // blocks per MMA sub-tile (16 rows)
+constexpr int kTcWarps = kTcPoints / 8;      // one warp per 8 points (and per block of a sub-tile)
+constexpr int kTcThreads = 32 * kTcWarps;
+static_assert(kTcWarps == kSub, "the A' tile is built one block per warp");
+constexpr double kTcTiltBits = 2.0;          // max 31 |mu - c| over a group's points
+
+struct TcTile {
+  int32_t start, count;  // bucketed positions [start, start + count)
+  int32_t piece;
+  int32_t ok;            // 1: summed here; 0: empty, or handed back to the FP64 kernels
+  int64_t mlo;           // first block, counted from the piece's first index
+  int64_t nblk;          // blocks covering the union of the tile's windows
+  double c;              // tilt exponent
+};
+
+// Per tile point, computed once by k_tc_pre: W^(2^k) for k = 0..3 (W = w^32),
+// which combine blocks, and Z's scale exponent eq.
+struct TcPoint {
+  xint W[4];   // W, W^2, W^4, W^8
+  int eq;
+  int pad[3];
+};
+
+// Per tile: tau^i = tm[i] 2^te[i] for i < 32 (the tilt of A').
+struct TcTau {
+  unsigned long long tm[kTB];
+  int te[kTB];
+};
+
+constexpr int kZBytes = kSl * kTcPoints * kTK * 2;  // one tile's Z' slices, as laid out in shared memory
+
+struct TcSmem {
+  uint16_t zq[kSl][kTK][kTcPoints];   // Z' slices (bf16 bits); rows kappa of the 64 points, chunks swizzled
+  uint16_t aq[kSl][2 * kSub][kTK];    // A' slices of the current sub-tile
+  xint w8[kTcPoints];                 // W^8 per point
+  xint w1[kTcPoints];                 // W per point (the final combination)
+  unsigned long long tm[kTB];         // tau^i = tm[i] 2^te[i]
+  int te[kTB];
+  int eq[kTcPoints];                  // Z' scale exponent per point
+  int er[kSub];                       // A' scale exponent per block of the sub-tile
+  int item, tile;
+};
+
+// element index of (row, kappa) in a [rows][64] bf16 array with the 16-B
+// chunk index xor-ed by row & 7 (ldmatrix reads 8 rows without bank conflicts)
+__device__ __forceinline__ int swz(int row, int kappa) {
+  return row * kTK + ((((kappa >> 3) ^ (row & 7)) << 3) | (kappa & 7));
+}
+
+// Z' layout, per slice: 64 rows (kappa) of the 64 points' values (128 B), the
+// 16-B chunk (8 points) xor-ed by kappa & 7; B fragments are read transposed
+__device__ __forceinline__ int zswz(int kappa, int p) {
+  return kappa * kTcPoints + ((((p >> 3) ^ (kappa & 7)) << 3) | (p & 7));
+}
+
+// a 7-bit slice q (exact in bf16) with a sign, as bf16 bits
+__device__ __forceinline__ uint16_t q_bf16(uint32_t q, uint32_t neg) {
+  const float f = __uint_as_float(0x4B000000u | q) - 8388608.0f;  // q exactly
+  return (uint16_t)((__float_as_uint(f) >> 16) | (neg << 15));
+}
+
+// the ten slices of a 70-bit magnitude F (F < 2^70): q_s = bits [63 - 7s, 69 - 7s]
+__device__ __forceinline__ void slices70(u128 F, uint32_t (&q)[kSl]) {
+  const unsigned long long fh = (unsigned long long)(F >> 35), fl = (unsigned long long)F & ((1ull << 35) - 1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    q[s] = (uint32_t)(fh >> (28 - 7 * s)) & 127u;
+    q[s + 5] = (uint32_t)(fl >> (28 - 7 * s)) & 127u;
+  }
+}
+
+// X 2^-sr (sr may be negative), saturated below 2^70
+__device__ __forceinline__ u128 shift_to70(u128 X, int sr) {
+  const u128 cap = ((u128)1 << 70) - 1;
+  if (sr >= 128) return 0;
+  if (sr >= 0) {
+    const u128 F = X >> sr;
+    return F > cap ? cap : F;
+  }
+  if (sr <= -70 || (X >> (70 + sr)) != 0) return cap;
+  return X << (-sr);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// sum_t acc[t] 2^(7 (9 - t)) as a signed 128-bit integer (each acc[t] an
+// integer below 2^24 held exactly in fp32)
+__device__ __forceinline__ void join_acc(const float (&acc)[kSl][4], int c, u128 &mag, int &neg) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int t = 0; t < 5; ++t) hi += (long long)__float2int_rn(acc[t][c]) << (7 * (4 - t));
+#pragma unroll
+  for (int t = 5; t < 10; ++t) lo += (long long)__float2int_rn(acc[t][c]) << (7 * (9 - t));
+  __int128 X = ((__int128)hi << 35) + (__int128)lo;
+  neg = X < 0;
+  mag = (u128)(neg ? -X : X);
+}
+
+// xor-shuffle of an xint across the warp
+__device__ __forceinline__ xint shfl_xint_tc(const xint &v, int m) {
+  auto sh = [m](unsigned long long x) { return __shfl_xor_sync(0xffffffffu, x, m); };
+  xint r;
+  r.x = ((u128)sh((unsigned long long)(v.x >> 64)) << 64) | sh((unsigned long long)v.x);
+  r.y = ((u128)sh((unsigned long long)(v.y >> 64)) << 64) | sh((unsigned long long)v.y);
+  r.sx = __shfl_xor_sync(0xffffffffu, v.sx, m);
+  r.sy = __shfl_xor_sync(0xffffffffu, v.sy, m);
+  r.e = (long long)sh((unsigned long long)v.e);
+  return r;
+}
+
+__device__ __forceinline__ double point_lambda(double zr, double zi) {
+  const int f = frexp_exp(fmax(fabs(zr), fabs(zi)));
+  const double xr = scale2(zr, -f), xi = scale2(zi, -f);
+  return (double)f + 0.5 * log2(fma(xr, xr, xi * xi));
+}
+
+__device__ __forceinline__ void tc_write_diag(const DevPoly &P, const PointRec &r, const fpe_xc64 &o,
+                                              int32_t *nterms, int32_t *bits_lost) {
+  if (nterms) nterms[r.orig] = P.gcount[r.hi + 1] - P.gcount[r.lo];
+  if (bits_lost) {
+    int bl = 0;
+    if (o.re != 0.0 || o.im != 0.0) {
+      const double c = ceil(r.N) - (double)o.e;
+      bl = c > 0.0 ? (int)fmin(c, 2.0e9) : 0;
+    }
+    bits_lost[r.orig] = bl;
+  }
+}
+
+// V z^(kb + v) 2^rho(kb): the window value from its block sum starting at
+// trimmed index kb of piece j
+__device__ __forceinline__ fpe_xc64 tc_output(const DevPoly &P, int j, long long kb, const PointRec &r, xint V) {
+  const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+  const long long rho = P.piece_rho0[j] + (long long)P.piece_beta[j] * (kb - P.piece_k0[j]);
+  if (V.x || V.y) {
+    V = xint_mul(V, xint_pow_z(r.zr, r.zi, kb + P.v, f));
+    V.e += rho;
+  }
+  return xc64_from_xint(V);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// groups and tiles.  The bucketed points of tensor-core piece r occupy
+// [s_r, s_r+1); group q of the piece holds the whole bins whose first point
+// lies in [s_r + 64 q, s_r + 64 (q + 1)), so a group has about 64 points, or
+// one bin with more.  A group's tilt, the union of its points' windows and
+// its work-item boundaries are computed over all its points, and its points
+// are cut into tiles of kTcPoints in bucketed order.  Which point of a group
+// lands in which tile depends on the scatter's atomics, but nothing a point's
+// value depends on does (group boundaries follow from bin counts alone, and
+// every MMA column is one point's): results are reproducible bit for bit.
+// ---------------------------------------------------------------------------
+struct TcGroup {
+  int32_t start, count;  // bucketed positions of its points
+  int32_t piece;
+  int32_t ok;            // 1: tensor cores; 0: empty, or handed back to the FP64 kernels
+  int64_t mlo, nblk;     // block range (blocks of kTB terms from the piece's first index)
+  double c;              // tilt exponent
+};
+
+// the first bin boundary of piece r at or after position x (bins are
+// contiguous; after the scatter bins[nbins + b] is the end of bin b)
+__device__ __forceinline__ int tc_snap(const uint32_t *bins, int nbins, int r, int x, int s_end) {
+  const int b0 = kNumBins + r * kTcBinsPerPiece;
+  int a = 0, b = kTcBinsPerPiece;  // find the smallest i with start(b0 + i) >= x
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if ((int)bins[nbins + b0 + m - 1] >= x)
+      b = m;
+    else
+      a = m + 1;
+  }
+  return a < kTcBinsPerPiece ? min((int)bins[nbins + b0 + a - 1], s_end) : s_end;
+}
+
+// one warp per group: bounds, spread check, tilt, block range
+__global__ void k_tc_groups(DevPoly P, PointRec *__restrict__ rec, const uint32_t *__restrict__ bins, int nbins,
+                            uint32_t *cnt, TcGroup *__restrict__ groups, int groups_max, long long long_window,
+                            long long span, int32_t *__restrict__ long_list, int32_t *__restrict__ long_ngroups,
+                            int32_t *__restrict__ long_gbase, int32_t *__restrict__ extra_owner,
+                            int32_t *__restrict__ extra_group, int extra_cap) {
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (gw >= groups_max) return;
+  int s[kTcMaxPieces + 1];
+#pragma unroll
+  for (int q = 0; q <= kTcMaxPieces; ++q) s[q] = (int)cnt[kCntTcStart + q];
+  int r = -1, lg = 0, cum = 0;
+  for (int q = 0; q < P.n_tc && q < kTcMaxPieces; ++q) {
+    const int ng = (s[q + 1] - s[q] + kTcPoints - 1) / kTcPoints;
+    if (r < 0 && gw < cum + ng) {
+      r = q;
+      lg = gw - cum;
+    }
+    cum += ng;
+  }
+  TcGroup G;
+  G.start = G.count = G.piece = G.ok = 0;
+  G.mlo = G.nblk = 0;
+  G.c = 0.0;
+  if (r < 0) {
+    if (lane == 0) groups[gw] = G;
+    return;
+  }
+  const int x0 = s[r] + kTcPoints * lg, x1 = x0 + kTcPoints;
+  const int start = tc_snap(bins, nbins, r, x0, s[r + 1]);
+  const int end = x1 >= s[r + 1] ? s[r + 1] : tc_snap(bins, nbins, r, x1, s[r + 1]);
+  const int count = end - start;
+  if (count <= 0) {
+    if (lane == 0) groups[gw] = G;
+    return;
+  }
+  const int j = P.tc_piece[r];
+  const int beta = P.piece_beta[j];
+  const long long k0 = P.piece_k0[j];
+  double mumin = 1e300, mumax = -1e300;
+  long long lomin = LLONG_MAX, himax = LLONG_MIN;
+  for (int p = lane; p < count; p += 32) {
+    const PointRec q = rec[start + p];
+    const double mu = point_lambda(q.zr, q.zi) + (double)beta;
+    mumin = fmin(mumin, mu);
+    mumax = fmax(mumax, mu);
+    lomin = min(lomin, q.lo);
+    himax = max(himax, q.hi);
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    mumin = fmin(mumin, __shfl_xor_sync(0xffffffffu, mumin, o));
+    mumax = fmax(mumax, __shfl_xor_sync(0xffffffffu, mumax, o));
+    lomin = min(lomin, (long long)__shfl_xor_sync(0xffffffffu, lomin, o));
+    himax = max(himax, (long long)__shfl_xor_sync(0xffffffffu, himax, o));
+  }
+  G.start = start;
+  G.count = count;
+  G.piece = j;
+  if (31.0 * 0.5 * (mumax - mumin) > kTcTiltBits) {
+    // too wide for one tilt: hand the points back to the FP64 kernels
+    for (int p = lane; p < count; p += 32) {
+      const int pos = start + p;
+      rec[pos].flags = 0;
+      const long long L = rec[pos].hi - rec[pos].lo + 1;
+      if (L > long_window)
+        list_long_window(L, span, (uint32_t)pos, cnt, long_list, long_ngroups, long_gbase, extra_owner,
+                         extra_group, extra_cap);
+    }
+    if (lane == 0) groups[gw] = G;
+    return;
+  }
+  G.ok = 1;
+  G.mlo = (lomin - k0) / kTB;
+  G.nblk = (himax - k0) / kTB - G.mlo + 1;
+  G.c = 0.5 * (mumin + mumax);
+  if (lane == 0) groups[gw] = G;
+}
+
+// ---------------------------------------------------------------------------
+// plan (one block): tiles of each group, blocks per work item (so that there
+// are about kTcItemsPerSm items per SM, each at least kTcMinChunk blocks), and
+// each tile's first work item
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tc_plan(const TcGroup *__restrict__ groups, int groups_max,
+                                                  TcTile *__restrict__ tiles, int tiles_max,
+                                                  int32_t *__restrict__ item_base,
+                                                  int32_t *__restrict__ item_tile, uint32_t *cnt, int nsms) {
+  __shared__ unsigned long long red[1024];
+  __shared__ uint32_t part[1024];
+  __shared__ long long s_chunk;
+  const int t = threadIdx.x;
+  const int per = (groups_max + 1023) / 1024;
+  auto ntiles = [&](const TcGroup &G) { return G.ok ? (G.count + kTcPoints - 1) / kTcPoints : 0; };
+  unsigned long long blocks = 0;
+  uint32_t mytiles = 0;
+  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
+    const TcGroup G = groups[i];
+    blocks += (unsigned long long)ntiles(G) * (unsigned long long)G.nblk;
+    mytiles += (uint32_t)ntiles(G);
+  }
+  red[t] = blocks;
+  part[t] = mytiles;
+  __syncthreads();
+  for (int o = 512; o >= 1; o >>= 1) {
+    if (t < o) red[t] += red[t + o];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const unsigned long long target = (unsigned long long)nsms * kTcItemsPerSm;
+    long long ch = (long long)((red[0] + target - 1) / target);
+    ch = std::max<long long>(ch, kTcMinChunk);
+    s_chunk = (ch + kSub - 1) / kSub * kSub;
+  }
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the tile counts
+    const uint32_t v = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  const uint32_t ntile_total = part[1023];
+  const uint32_t tile0 = part[t] - mytiles;
+  __syncthreads();
+  const long long chunk = s_chunk;
+  uint32_t myitems = 0;
+  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
+    const TcGroup G = groups[i];
+    myitems += (uint32_t)ntiles(G) * (uint32_t)((G.nblk + chunk - 1) / chunk);
+  }
+  part[t] = myitems;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t v = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t tt = tile0, it = part[t] - myitems;
+  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
+    const TcGroup G = groups[i];
+    const int nt = ntiles(G);
+    const uint32_t ipt = (uint32_t)((G.nblk + chunk - 1) / chunk);
+    for (int lt = 0; lt < nt; ++lt, ++tt) {
+      TcTile T;
+      T.start = G.start + kTcPoints * lt;
+      T.count = min(kTcPoints, G.count - kTcPoints * lt);
+      T.piece = G.piece;
+      T.ok = 1;
+      T.mlo = G.mlo;
+      T.nblk = G.nblk;
+      T.c = G.c;
+      tiles[tt] = T;
+      item_base[tt] = (int32_t)it;
+      for (uint32_t c = 0; c < ipt; ++c) item_tile[it + c] = (int32_t)tt;
+      it += ipt;
+    }
+  }
+  for (int i = (int)ntile_total + t; i < tiles_max; i += 1024) {  // unused tiles
+    TcTile T;
+    T.start = T.count = T.piece = T.ok = 0;
+    T.mlo = T.nblk = 0;
+    T.c = 0.0;
+    tiles[i] = T;
+    item_base[i + 1] = (int32_t)part[1023];
+  }
+  if (t == 1023) {
+    item_base[ntile_total] = (int32_t)part[1023];
+    cnt[kCntTcItems] = part[1023];
+    cnt[kCntTcChunk] = (uint32_t)chunk;
+    cnt[kCntTcWork] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per tile: tau^i; per tile point (one thread each): u = w / tau, the Z'
+// slices of u^i (i < 32) written straight to global memory in the layout
+// k_tc_sum copies into shared memory (for each slice and term, the 64
+// points' values are one 128-B row, so a warp's stores are contiguous),
+// W^(2^k) = (u^32 tau^32)^(2^k), and Z's scale exponent.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
+                                                      const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
+                                                      TcTau *__restrict__ taus, uint16_t *__restrict__ zglob) {
+  __shared__ xint s_inv, s_tau32;
+  __shared__ double s_tmant;
+  __shared__ int s_tf;
+  const int t = blockIdx.x, p = threadIdx.x;
+  const TcTile T = tiles[t];
+  if (!T.ok) return;  // block-uniform
+  if (p == 0) {  // tau = tmant 2^tf, tmant in [0.5, 1); 1 / tau; tau^32
+    const double tau = exp2(T.c);
+    const int tf = frexp_exp(tau);
+    const double tmant = scale2(tau, -tf);
+    xint inv = recip_xint(tmant, 0.0);
+    inv.e -= tf;
+    xint t32 = xint_pow_unit(tmant, 0.0, kTB);
+    t32.e += (long long)tf * kTB;
+    s_inv = inv;
+    s_tau32 = t32;
+    s_tmant = tmant;
+    s_tf = tf;
+  }
+  __syncthreads();
+  if (p < kTB) {
+    xint ti = xint_norm((u128)1 << 126, 0, 0, 0, 0);
+    if (p > 0) {
+      ti = xint_pow_unit(s_tmant, 0.0, p);
+      ti.e += (long long)s_tf * p;
+    }
+    taus[t].tm[p] = (unsigned long long)(ti.x >> 63);  // in [2^63, 2^64)
+    taus[t].te[p] = (int)(ti.e - 63);
+  }
+  const bool valid = p < T.count;
+  const xint zero = xint_norm(0, 0, 0, 0, 0);
+  xint u = zero, cur = zero;
+  int eQ = 1;
+  if (valid) {
+    const PointRec r = rec[T.start + p];
+    u = xint_mul(xint_from_dd2(r.zr, 0.0, r.zi, 0.0, P.piece_beta[T.piece]), s_inv);
+    // every |component of u^i| (i < 32) is at most |u|^31 <= 2^(eQ - 1); |u| is
+    // near 1, so log2|u| in FP32 (error far below the 1e-3 / 31 margin) suffices:
+    // |u| = sqrt(mx^2 + my^2) 2^e with mx = X 2^-126 (X the magnitude, top bit at 126)
+    const float mx = (float)(unsigned long long)(u.x >> 64) * 0x1p-62f;
+    const float my = (float)(unsigned long long)(u.y >> 64) * 0x1p-62f;
+    const float l = 0.5f * log2f(fmaf(mx, mx, my * my)) + (float)u.e;
+    eQ = max(0, (int)ceilf(31.0f * l + 1e-3f)) + 1;
+    cur = xint_norm((u128)1 << 126, 0, 0, 0, 0);
+  }
+  uint16_t *zt = zglob + (size_t)t * (kZBytes / 2);
+  for (int i = 0; i < kTB; ++i) {
+    if (i > 0 && valid) cur = xint_mul(cur, u);
+    uint32_t qr[kSl], qi[kSl];
+    const int sr = 56 + eQ - (int)cur.e;
+    slices70(valid ? shift_to70(cur.x, sr) : (u128)0, qr);
+    slices70(valid ? shift_to70(cur.y, sr) : (u128)0, qi);
+    const int cre = zswz(i, p), cim = zswz(kTB + i, p);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+      zt[s * kTK * kTcPoints + cre] = q_bf16(qr[s], (uint32_t)cur.sx);
+      zt[s * kTK * kTcPoints + cim] = q_bf16(qi[s], (uint32_t)cur.sy);
+    }
+  }
+  TcPoint o;
+  xint W = zero;
+  if (valid) W = xint_mul(xint_mul(cur, u), s_tau32);  // u^32 tau^32 = w^32
+  o.W[0] = W;
+  for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
+  o.eq = eQ;
+  o.pad[0] = o.pad[1] = o.pad[2] = 0;
+  pts[(size_t)t * kTcPoints + p] = o;
+}
+
+// ---------------------------------------------------------------------------
+// the window sums: persistent CTAs of 8 warps (two per SM) take work items (a
+// tile and a run of at most `chunk` blocks) from a counter; each item's
+// value per point, sum over its blocks m of C_m W^(m - first), goes to a slot
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_tc_sum(DevPoly P, const TcTile *__restrict__ tiles, const TcPoint *__restrict__ pts,
+             const TcTau *__restrict__ taus, const uint4 *__restrict__ zglob, const int32_t *__restrict__ item_base,
+             const int32_t *__restrict__ item_tile, uint32_t *cnt, xint *__restrict__ slots) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t nitems = *(volatile uint32_t *)&cnt[kCntTcItems];
+  const long long chunk = (long long)*(volatile uint32_t *)&cnt[kCntTcChunk];
+  const xint zero = xint_norm(0, 0, 0, 0, 0);
+  while (true) {
+    if (tid == 0) {
+      const uint32_t it = atomicAdd(&cnt[kCntTcWork], 1u);
+      S.item = (int)it;
+      S.tile = it < nitems ? item_tile[it] : -1;
+    }
+    __syncthreads();
+    const int item = S.item, t = S.tile;
+    if (t < 0) break;
+    const TcTile T = tiles[t];
+    const int j = T.piece;
+    const long long k0 = P.piece_k0[j], k1 = (long long)P.piece_k0[j + 1] - 1;
+    const long long mb = T.mlo + (long long)(item - item_base[t]) * chunk;
+    const long long me = min((long long)(T.mlo + T.nblk), mb + chunk);
+    const TcPoint *tp = pts + (size_t)t * kTcPoints;
+
+    // ---- setup: the tile's Z' slices, tau^i, W^8 and Z's scales into shared memory
+    {
+      const uint4 *src = zglob + (size_t)t * (kZBytes / 16);
+      uint4 *dst = reinterpret_cast<uint4 *>(&S.zq[0][0][0]);
+      for (int i = tid; i < kZBytes / 16; i += kTcThreads) dst[i] = src[i];
+      if (tid < kTB) {
+        S.tm[tid] = taus[t].tm[tid];
+        S.te[tid] = taus[t].te[tid];
+      }
+      if (tid < kTcPoints) {
+        const bool v = tid < T.count;
+        S.w8[tid] = v ? tp[tid].W[3] : zero;
+        S.eq[tid] = v ? tp[tid].eq : 1;
+        S.w1[tid] = v ? tp[tid].W[0] : zero;
+      }
+    }
+    __syncthreads();
+
+    // ---- sub-tiles of 8 blocks, from the top down (Horner in W^8 per lane)
+    const int g = lane >> 2, tq = lane & 3;
+    const int p0 = 8 * wid + 2 * tq;
+    xint H0 = zero, H1 = zero;
+    const int nsub = (int)((me - mb + kSub - 1) / kSub);
+    // coefficient of this lane in block mb + 8 ts + wid (0 outside the item or the piece)
+    auto load_b = [&](int ts_) -> double2 {
+      const long long m = mb + (long long)kSub * ts_ + wid;
+      const long long k = k0 + kTB * m + lane;
+      double2 c = make_double2(0.0, 0.0);
+      if (ts_ >= 0 && m < me && k <= k1) {
+        if (P.complex_coef)
+          c = __ldg(reinterpret_cast<const double2 *>(P.b) + k);
+        else
+          c.x = __ldg(P.b + k);
+      }
+      return c;
+    };
+    double2 bnext = load_b(nsub - 1);
+    for (int ts = nsub - 1; ts >= 0; --ts) {
+      const long long m0 = mb + (long long)kSub * ts;
+      {  // A' for block m0 + wid, lane = term i
+        const double br = bnext.x, bi = bnext.y;
+        bnext = load_b(ts - 1);  // in flight during this sub-tile's MMAs
+        const unsigned long long tmi = S.tm[lane];
+        const int tei = S.te[lane];
+        u128 pr = 0, pi = 0;
+        int er_ = 0, ei_ = 0, top = INT_MIN;
+        auto prod = [&](double x, u128 &pp, int &E) {
+          const unsigned long long bits = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+          if (bits == 0) return;
+          const int ex = (int)(bits >> 52);
+          const unsigned long long mm = ex ? ((bits & 0xfffffffffffffull) | 0x10000000000000ull)
+                                           : (bits & 0xfffffffffffffull);
+          pp = (u128)mm * tmi;
+          E = (ex ? ex : 1) - 1075 + tei;
+          top = max(top, 127 - clz128(pp) + E);
+        };
+        prod(br, pr, er_);
+        prod(bi, pi, ei_);
+        for (int o = 16; o >= 1; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+        const int eR = top == INT_MIN ? 0 : top + 1;  // every |component| < 2^eR
+        uint32_t qr[kSl], qi[kSl];
+        slices70(pr ? shift_to70(pr, eR - 70 - er_) : (u128)0, qr);
+        slices70(pi ? shift_to70(pi, eR - 70 - ei_) : (u128)0, qi);
+        const uint32_t nr = br < 0.0, ni = bi < 0.0;
+        uint16_t *are = &S.aq[0][0][0] + wid * kTK, *aim = &S.aq[0][0][0] + (kSub + wid) * kTK;
+        const int c_lo = ((lane >> 3) ^ wid) << 3 | (lane & 7), c_hi = ((4 + (lane >> 3)) ^ wid) << 3 | (lane & 7);
+#pragma unroll
+        for (int s = 0; s < kSl; ++s) {
+          // out_re row: ( A'_re | -A'_im ), out_im row: ( A'_im | A'_re )
+          are[s * 2 * kSub * kTK + c_lo] = q_bf16(qr[s], nr);
+          are[s * 2 * kSub * kTK + c_hi] = q_bf16(qi[s], ni ^ 1u);
+          aim[s * 2 * kSub * kTK + c_lo] = q_bf16(qi[s], ni);
+          aim[s * 2 * kSub * kTK + c_hi] = q_bf16(qr[s], nr);
+        }
+        if (lane == 0) S.er[wid] = eR;
+      }
+      __syncthreads();
+      float acc[kSl][4];
+#pragma unroll
+      for (int s = 0; s < kSl; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.0f;
+#pragma unroll
+      for (int kp = 0; kp < 2; ++kp) {
+        uint32_t bq[kSl][4];
+        {  // rows kappa = 32 kp + lane (8 per matrix), the warp's 8 points
+          const int row = 32 * kp + lane;
+#pragma unroll
+          for (int s = 0; s < kSl; ++s)
+            ldsm_x4_t(bq[s], &S.zq[s][0][0] + row * kTcPoints + ((wid ^ (row & 7)) << 3));
+        }
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const int ks = 2 * kp + kk;
+          const int row = (lane & 7) + 8 * ((lane >> 3) & 1), ch = 2 * ks + (lane >> 4);
+#pragma unroll
+          for (int sa = 0; sa < kSl; ++sa) {
+            uint32_t a[4];
+            ldsm_x4(a, &S.aq[sa][0][0] + row * kTK + ((ch ^ (row & 7)) << 3));
+#pragma unroll
+            for (int sz = 0; sz < kSl - sa; ++sz) mma_bf16(acc[sa + sz], a, bq[sz][2 * kk], bq[sz][2 * kk + 1]);
+          }
+        }
+      }
+      __syncthreads();  // the A' tile is free for the next sub-tile
+      // combine: lane holds block m0 + g at points p0, p0 + 1
+      const bool inblk = m0 + g < me;
+      const int eRg = S.er[g];
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp) {
+        const int p = p0 + pp;
+        xint C = zero;
+        if (inblk && p < T.count) {
+          u128 xr, xi;
+          int sr, si;
+          join_acc(acc, pp, xr, sr);
+          join_acc(acc, 2 + pp, xi, si);
+          C = xint_norm(xr, sr, xi, si, 49 + (long long)eRg + S.eq[p]);
+        }
+        xint &H = pp ? H1 : H0;
+        if (H.x || H.y) H = xint_mul(H, S.w8[p]);
+        H = xint_add(H, C);
+      }
+    }
+    // ---- V = sum_g W^g H_g: the lanes' H into shared memory (over the Z'
+    // tiles, no longer read), then one thread per point, Horner over g
+    xint *hs = reinterpret_cast<xint *>(&S.zq[0][0][0]);  // [point][g]
+    hs[p0 * kSub + g] = H0;
+    hs[(p0 + 1) * kSub + g] = H1;
+    __syncthreads();
+    if (tid < T.count) {
+      const xint W = S.w1[tid];
+      xint V = hs[tid * kSub + kSub - 1];
+      for (int gg = kSub - 2; gg >= 0; --gg) {
+        if (V.x || V.y) V = xint_mul(V, W);
+        V = xint_add(V, hs[tid * kSub + gg]);
+      }
+      slots[(size_t)item * kTcPoints + tid] = V;
+    }
+    __syncthreads();  // shared memory is reused by the next item
+  }
+}
+
+// Per tile point: Horner over the tile's items in W^chunk (item c starts
+// chunk c blocks after the first), then z^(kb + v) 2^rho(kb) with kb the
+// first block's index, and the point's output.
+__global__ void __launch_bounds__(kTcPoints) k_tc_finalize(DevPoly P, const PointRec *__restrict__ rec,
+                                                           const TcTile *__restrict__ tiles,
+                                                           const int32_t *__restrict__ item_base, const uint32_t *cnt,
+                                                           const xint *__restrict__ slots, fpe_xc64 *__restrict__ out,
+                                                           int32_t *nterms, int32_t *bits_lost) {
+  const int t = blockIdx.x, p = threadIdx.x;
+  const TcTile T = tiles[t];
+  if (!T.ok || p >= T.count) return;
+  const int base = item_base[t], nit = item_base[t + 1] - base;
+  const long long chunk = (long long)cnt[kCntTcChunk];
+  const PointRec r = rec[T.start + p];
+  const int j = T.piece;
+  xint V = slots[(size_t)(base + nit - 1) * kTcPoints + p];
+  if (nit > 1) {
+    const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+    xint Wc = xint_pow_z(r.zr, r.zi, kTB * chunk, f);
+    Wc.e += (long long)kTB * chunk * P.piece_beta[j];
+    for (int c = nit - 2; c >= 0; --c) {
+      if (V.x || V.y) V = xint_mul(V, Wc);
+      V = xint_add(V, slots[(size_t)(base + c) * kTcPoints + p]);
+    }
+  }
+  const fpe_xc64 o = tc_output(P, j, P.piece_k0[j] + kTB * T.mlo, r, V);
+  out[r.orig] = o;
+  tc_write_diag(P, r, o, nterms, bits_lost);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int tc_num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+static int64_t tc_groups_max(int64_t n) { return (n + kTcPoints - 1) / kTcPoints + kTcMaxPieces; }
+static int64_t tc_tiles_max(int64_t n) { return (n + kTcPoints - 1) / kTcPoints + tc_groups_max(n); }
+static int64_t tc_items_cap(int64_t n) { return tc_tiles_max(n) + (int64_t)tc_num_sms() * kTcItemsPerSm; }
+constexpr int kTcCtasPerSm = 2;
+
+bool tc_enabled(const fpe_poly_s *P, bool complex_points) {
+  (void)complex_points;
+  return P->dev.n_tc > 0 && !P->dev.fp32 && !P->dev.accurate && P->tune.tc_min_window > 0;
+}
+
+void free_tc_workspace(Workspace &w) {
+  void *ptrs[] = {w.tc_tiles, w.tc_item_base, w.tc_slots, w.tc_points, w.tc_item_tile, w.tc_taus, w.tc_z,
+                  w.tc_groups};
+  for (void *a : ptrs)
+    if (a) cudaFree(a);
+  w.tc_tiles = nullptr;
+  w.tc_item_base = nullptr;
+  w.tc_slots = nullptr;
+  w.tc_points = nullptr;
+  w.tc_item_tile = nullptr;
+  w.tc_taus = nullptr;
+  w.tc_z = nullptr;
+  w.tc_groups = nullptr;
+  w.tc_cap = 0;
+}
+
+fpe_status ensure_tc_workspace(fpe_poly_s *P, int64_t n) {
+  Workspace &w = P->ws;
+  const int64_t cap = std::max<int64_t>(n, 1024);
+  if (w.tc_cap >= cap && w.tc_tiles) return FPE_OK;
+  free_tc_workspace(w);
+  const int64_t tm = tc_tiles_max(cap), ic = tc_items_cap(cap);
+  cudaError_t e = cudaMalloc(&w.tc_tiles, tm * sizeof(TcTile));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&w.tc_item_base, (tm + 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&w.tc_slots, (size_t)ic * kTcPoints * sizeof(xint));
+  if (e == cudaSuccess) e = cudaMalloc(&w.tc_points, (size_t)tm * kTcPoints * sizeof(TcPoint));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&w.tc_item_tile, (size_t)ic * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&w.tc_taus, (size_t)tm * sizeof(TcTau));
+  if (e == cudaSuccess) e = cudaMalloc(&w.tc_z, (size_t)tm * kZBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&w.tc_groups, (size_t)tc_groups_max(cap) * sizeof(TcGroup));
+  if (e != cudaSuccess) {
+    free_tc_workspace(w);
+    return cuda_fail(e, "cudaMalloc(tensor-core workspace)");
+  }
+  w.tc_cap = cap;
+  return FPE_OK;
+}
+
+// the kernels' dynamic shared memory above the default 48 KB, once per device
+static fpe_status tc_set_smem_attrs() {
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_sum, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tensor-core kernels)");
+    attr_set[dev] = true;
+  }
+  return FPE_OK;
+}
+
+fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
+  fpe_status s = tc_set_smem_attrs();
+  if (s != FPE_OK) return s;
+  Workspace &w = P->ws;
+  uint32_t *cnt = w.bins + 2 * w.nbins;
+  const int tm = (int)tc_tiles_max(n), gm = (int)tc_groups_max(n);
+  {
+    ProfScope ps("k_tc_groups", st);
+    k_tc_groups<<<(gm + 7) / 8, 256, 0, st>>>(P->dev, w.rec, w.bins, w.nbins, cnt, (TcGroup *)w.tc_groups, gm,
+                                              P->tune.long_window, P->tune.group_span(), w.long_list,
+                                              w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
+                                              (int)w.extra_cap);
+  }
+  {
+    ProfScope ps("k_tc_plan", st);
+    k_tc_plan<<<1, 1024, 0, st>>>((const TcGroup *)w.tc_groups, gm, (TcTile *)w.tc_tiles, tm, w.tc_item_base,
+                                  w.tc_item_tile, cnt, tc_num_sms());
+  }
+  {
+    ProfScope ps("k_tc_pre", st);
+    k_tc_pre<<<tm, kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, (TcPoint *)w.tc_points,
+                                                 (TcTau *)w.tc_taus, (uint16_t *)w.tc_z);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core plan launch");
+}
+
+fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
+                          cudaStream_t st) {
+  Workspace &w = P->ws;
+  uint32_t *cnt = w.bins + 2 * w.nbins;
+  const int tm = (int)tc_tiles_max(n);
+  fpe_status s = tc_set_smem_attrs();
+  if (s != FPE_OK) return s;
+  {
+    ProfScope ps("k_tc_sum", st);
+    k_tc_sum<<<tc_num_sms() * kTcCtasPerSm, kTcThreads, sizeof(TcSmem), st>>>(
+        P->dev, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, (const TcTau *)w.tc_taus,
+        (const uint4 *)w.tc_z, w.tc_item_base, w.tc_item_tile, cnt, (xint *)w.tc_slots);
+  }
+  {
+    ProfScope ps("k_tc_finalize", st);
+    k_tc_finalize<<<tm, kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt,
+                                             (const xint *)w.tc_slots, out, nterms, bits_lost);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core sum launch");
+}
+
+}  // namespace fpe

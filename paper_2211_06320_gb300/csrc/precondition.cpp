@@ -1,6 +1,7 @@
 // Host preconditioning of Algorithm A_p (lines 2-4, §5.1): exact integer scales,
 // the concave cover of k -> s(a_k), the good set G_p, and the device layout of
 // the coefficients.  Runs once per polynomial; not on the evaluation path.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -150,6 +151,7 @@ void free_workspace(Workspace &w) {
   for (void *a : ptrs)
     if (a) cudaFree(a);
   if (w.host_pinned) cudaFreeHost(w.host_pinned);
+  free_tc_workspace(w);
   w = Workspace();
 }
 
@@ -186,7 +188,7 @@ fpe_status alloc_workspace(Workspace &w, int64_t n) {
 fpe_status ensure_workspace(fpe_poly_s *P, int64_t n) {
   Workspace &w = P->ws;
   if (w.bins == nullptr) {
-    cudaError_t e = cudaMalloc((void **)&w.bins, (2 * kNumBins + kNumCounters) * sizeof(uint32_t));
+    cudaError_t e = cudaMalloc((void **)&w.bins, (2 * (kNumBins + kTcBins) + kNumCounters) * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bins)");
   }
   if (n <= w.cap) return FPE_OK;
@@ -393,6 +395,19 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
       pfirst[g] = j;
     }
     P->dev.npieces = npm;
+    // pieces for the tensor-core window sums: complex FP64 default mode, the
+    // longest (merged) pieces of at least kTcMinPieceLen terms
+    P->dev.n_tc = 0;
+    for (int r = 0; r < kTcMaxPieces; ++r) P->dev.tc_piece[r] = -1;
+    if (!fp32 && !(flags & FPE_ACCURATE)) {
+      std::vector<std::pair<int64_t, int>> byLen;
+      for (int q = 0; q < npm; ++q) {
+        const int64_t len = (int64_t)pk0[q + 1] - pk0[q];
+        if (len >= kTcMinPieceLen) byLen.push_back({-len, q});
+      }
+      std::sort(byLen.begin(), byLen.end());
+      for (size_t r = 0; r < byLen.size() && r < (size_t)kTcMaxPieces; ++r) P->dev.tc_piece[P->dev.n_tc++] = byLen[r].second;
+    }
   }
 
   // coefficients b_k = a_k 2^-rho(k), trimmed; bad ones zeroed in b
