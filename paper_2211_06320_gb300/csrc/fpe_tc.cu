@@ -61,6 +61,91 @@ constexpr int kTcThreads = 32 * kTcWarps;
 static_assert(kTcWarps == kSub, "the A' tile is built one block per warp");
 constexpr double kTcTiltBits = 2.0;          // max 31 |mu - c| over a group's points
 
+// A complex value with 64-bit mantissas, ((-1)^sx x + i (-1)^sy y) 2^(e - 63),
+// max(x, y) in [2^63, 2^64) or both 0: the per-block Horner inside a work
+// item runs in it (at most chunk / 8 steps, each truncating at 2^-63 of the
+// partial sum, so the item's error stays below 2^-57 of its terms' sum).
+struct xh {
+  unsigned long long x, y;
+  int sx, sy;
+  long long e;
+};
+
+__device__ __forceinline__ xh xh_norm(unsigned long long x, int sx, unsigned long long y, int sy, long long e) {
+  const unsigned long long m = x > y ? x : y;
+  xh r;
+  if (m == 0) {
+    r.x = r.y = 0;
+    r.sx = r.sy = 0;
+    r.e = 0;
+    return r;
+  }
+  const int sh = __clzll(m);
+  r.x = x << sh;
+  r.y = y << sh;
+  r.sx = r.x ? sx : 0;
+  r.sy = r.y ? sy : 0;
+  r.e = e - sh;
+  return r;
+}
+
+// top 64 bits of a 128-bit magnitude pair (value X 2^(e - 126) as in xint)
+__device__ __forceinline__ xh xh_from128(u128 X, int sx, u128 Y, int sy, long long e) {
+  const u128 m = X > Y ? X : Y;
+  if (m == 0) return xh_norm(0, 0, 0, 0, 0);
+  const int sh = clz128(m);  // bring the top bit to 127
+  X <<= sh;
+  Y <<= sh;
+  return xh_norm((unsigned long long)(X >> 64), sx, (unsigned long long)(Y >> 64), sy, e - sh + 1);
+}
+
+__device__ __forceinline__ xh xh_from_xint(const xint &v) { return xh_from128(v.x, v.sx, v.y, v.sy, v.e); }
+
+__device__ __forceinline__ xint xint_from_xh(const xh &v) {
+  return xint_norm((u128)v.x << 62, v.sx, (u128)v.y << 62, v.sy, v.e + 1);
+}
+
+// signed-magnitude a + b (halved, so no overflow)
+__device__ __forceinline__ void sadd64h(unsigned long long a, int sa, unsigned long long b, int sb,
+                                        unsigned long long &r, int &sr) {
+  a >>= 1;
+  b >>= 1;
+  if (sa == sb) {
+    r = a + b;
+    sr = sa;
+  } else if (a >= b) {
+    r = a - b;
+    sr = sa;
+  } else {
+    r = b - a;
+    sr = sb;
+  }
+}
+
+__device__ __forceinline__ xh xh_mul(const xh &a, const xh &b) {
+  const unsigned long long p1 = __umul64hi(a.x, b.x), p2 = __umul64hi(a.y, b.y);
+  const unsigned long long p3 = __umul64hi(a.x, b.y), p4 = __umul64hi(a.y, b.x);
+  unsigned long long re, im;
+  int sre, sim;
+  sadd64h(p1, a.sx ^ b.sx, p2, 1 ^ a.sy ^ b.sy, re, sre);
+  sadd64h(p3, a.sx ^ b.sy, p4, a.sy ^ b.sx, im, sim);
+  // p = a b 2^-64 in units of 2^(ea + eb - 126), halved: exponent ea + eb - 126 + 64 + 1 + 63
+  return xh_norm(re, sre, im, sim, a.e + b.e + 2);
+}
+
+__device__ __forceinline__ xh xh_add(const xh &a, const xh &b) {
+  if (!a.x && !a.y) return b;
+  if (!b.x && !b.y) return a;
+  const xh &hi = a.e >= b.e ? a : b, &lo = a.e >= b.e ? b : a;
+  const long long d = hi.e - lo.e;
+  const unsigned long long lx = d < 64 ? (lo.x >> d) : 0ull, ly = d < 64 ? (lo.y >> d) : 0ull;
+  unsigned long long rx, ry;
+  int sx, sy;
+  sadd64h(hi.x, hi.sx, lx, lo.sx, rx, sx);
+  sadd64h(hi.y, hi.sy, ly, lo.sy, ry, sy);
+  return xh_norm(rx, rx ? sx : 0, ry, ry ? sy : 0, hi.e + 1);
+}
+
 struct TcTile {
   int32_t start, count;  // bucketed positions [start, start + count)
   int32_t piece;
@@ -89,7 +174,7 @@ constexpr int kZBytes = kSl * kTcPoints * kTK * 2;  // one tile's Z' slices, as 
 struct TcSmem {
   uint16_t zq[kSl][kTK][kTcPoints];   // Z' slices (bf16 bits); rows kappa of the 64 points, chunks swizzled
   uint16_t aq[kSl][2 * kSub][kTK];    // A' slices of the current sub-tile
-  xint w8[kTcPoints];                 // W^8 per point
+  xh w8[kTcPoints];                   // W^8 per point (64-bit mantissas)
   xint w1[kTcPoints];                 // W per point (the final combination)
   unsigned long long tm[kTB];         // tau^i = tm[i] 2^te[i]
   int te[kTB];
@@ -465,11 +550,13 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
   }
   const bool valid = p < T.count;
   const xint zero = xint_norm(0, 0, 0, 0, 0);
-  xint u = zero, cur = zero;
+  xint u = zero;
+  xh uh = xh_norm(0, 0, 0, 0, 0), cur = uh;
   int eQ = 1;
   if (valid) {
     const PointRec r = rec[T.start + p];
     u = xint_mul(xint_from_dd2(r.zr, 0.0, r.zi, 0.0, P.piece_beta[T.piece]), s_inv);
+    uh = xh_from_xint(u);
     // every |component of u^i| (i < 32) is at most |u|^31 <= 2^(eQ - 1); |u| is
     // near 1, so log2|u| in FP32 (error far below the 1e-3 / 31 margin) suffices:
     // |u| = sqrt(mx^2 + my^2) 2^e with mx = X 2^-126 (X the magnitude, top bit at 126)
@@ -477,15 +564,17 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
     const float my = (float)(unsigned long long)(u.y >> 64) * 0x1p-62f;
     const float l = 0.5f * log2f(fmaf(mx, mx, my * my)) + (float)u.e;
     eQ = max(0, (int)ceilf(31.0f * l + 1e-3f)) + 1;
-    cur = xint_norm((u128)1 << 126, 0, 0, 0, 0);
+    cur = xh_norm(1ull << 63, 0, 0, 0, 0);  // 1
   }
+  // powers u^i in 64-bit mantissas: each product truncates at 2^-63, so u^31
+  // is within 2^-58 of its value relative to itself
   uint16_t *zt = zglob + (size_t)t * (kZBytes / 2);
   for (int i = 0; i < kTB; ++i) {
-    if (i > 0 && valid) cur = xint_mul(cur, u);
+    if (i > 0 && valid) cur = xh_mul(cur, uh);
     uint32_t qr[kSl], qi[kSl];
-    const int sr = 56 + eQ - (int)cur.e;
-    slices70(valid ? shift_to70(cur.x, sr) : (u128)0, qr);
-    slices70(valid ? shift_to70(cur.y, sr) : (u128)0, qi);
+    const int sr = eQ - 7 - (int)cur.e;  // x 2^(e - 63) 2^(70 - eQ) = x 2^-sr: 70-bit fixed point below 2^eQ
+    slices70(valid ? shift_to70((u128)cur.x, sr) : (u128)0, qr);
+    slices70(valid ? shift_to70((u128)cur.y, sr) : (u128)0, qi);
     const int cre = zswz(i, p), cim = zswz(kTB + i, p);
 #pragma unroll
     for (int s = 0; s < kSl; ++s) {
@@ -495,7 +584,7 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
   }
   TcPoint o;
   xint W = zero;
-  if (valid) W = xint_mul(xint_mul(cur, u), s_tau32);  // u^32 tau^32 = w^32
+  if (valid) W = xint_mul(xint_from_xh(xh_mul(cur, uh)), s_tau32);  // u^32 tau^32 = w^32 (to 2^-57)
   o.W[0] = W;
   for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
   o.eq = eQ;
@@ -545,7 +634,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       }
       if (tid < kTcPoints) {
         const bool v = tid < T.count;
-        S.w8[tid] = v ? tp[tid].W[3] : zero;
+        S.w8[tid] = xh_from_xint(v ? tp[tid].W[3] : zero);
         S.eq[tid] = v ? tp[tid].eq : 1;
         S.w1[tid] = v ? tp[tid].W[0] : zero;
       }
@@ -555,7 +644,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     // ---- sub-tiles of 8 blocks, from the top down (Horner in W^8 per lane)
     const int g = lane >> 2, tq = lane & 3;
     const int p0 = 8 * wid + 2 * tq;
-    xint H0 = zero, H1 = zero;
+    xh H0 = xh_norm(0, 0, 0, 0, 0), H1 = H0;
     const int nsub = (int)((me - mb + kSub - 1) / kSub);
     // coefficient of this lane in block mb + 8 ts + wid (0 outside the item or the piece)
     auto load_b = [&](int ts_) -> double2 {
@@ -643,24 +732,24 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 #pragma unroll
       for (int pp = 0; pp < 2; ++pp) {
         const int p = p0 + pp;
-        xint C = zero;
+        xh C = xh_norm(0, 0, 0, 0, 0);
         if (inblk && p < T.count) {
           u128 xr, xi;
           int sr, si;
           join_acc(acc, pp, xr, sr);
           join_acc(acc, 2 + pp, xi, si);
-          C = xint_norm(xr, sr, xi, si, 49 + (long long)eRg + S.eq[p]);
+          C = xh_from128(xr, sr, xi, si, 49 + (long long)eRg + S.eq[p]);
         }
-        xint &H = pp ? H1 : H0;
-        if (H.x || H.y) H = xint_mul(H, S.w8[p]);
-        H = xint_add(H, C);
+        xh &H = pp ? H1 : H0;
+        if (H.x || H.y) H = xh_mul(H, S.w8[p]);
+        H = xh_add(H, C);
       }
     }
     // ---- V = sum_g W^g H_g: the lanes' H into shared memory (over the Z'
     // tiles, no longer read), then one thread per point, Horner over g
     xint *hs = reinterpret_cast<xint *>(&S.zq[0][0][0]);  // [point][g]
-    hs[p0 * kSub + g] = H0;
-    hs[(p0 + 1) * kSub + g] = H1;
+    hs[p0 * kSub + g] = xint_from_xh(H0);
+    hs[(p0 + 1) * kSub + g] = xint_from_xh(H1);
     __syncthreads();
     if (tid < T.count) {
       const xint W = S.w1[tid];
