@@ -36,7 +36,7 @@ UNIT = "evals/s"
 # workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on: the file records their SHA-256.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_unit_disk_d2pow20.txt")
-KERNEL_SOURCES = ["fpe_eval.cu", "fpe_device.cuh", "fpe_internal.h"]
+KERNEL_SOURCES = ["fpe_eval.cu", "fpe_device.cuh", "fpe_internal.h", "fpe_tc.cu"]
 
 
 def kernel_sources_sha() -> str:
@@ -61,6 +61,16 @@ def measured_traffic(kernel: str):
                 return None, "ncu traffic record predates the current kernel sources"
             return float(parts[1]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one full-size launch"
     return None, "no ncu traffic record for " + kernel
+
+
+def measured_bf16_peak():
+    """Dense bf16 TFLOP/s of the GB300s (measured cuBLAS burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops"])
+        return v, "measured: MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM burst on this pool's GB300s)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback: 1.9 PFLOP/s bf16 burst (one earlier GB300 measurement)"
 
 
 def parse():
@@ -327,7 +337,9 @@ def main():
     k_short, n_short = F.fpe_profile_read("k_sum_short")
     k_long, n_long = F.fpe_profile_read("k_sum_groups")
     k_fin, _ = F.fpe_profile_read("k_finalize_long")
+    k_tc, n_tc = F.fpe_profile_read("k_tc_sum")
     k_all, launches = F.fpe_profile_read("")
+    tcs = F.fpe_tensor_stats(P)
     if world > 1:
         t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -336,31 +348,61 @@ def main():
 
     extras = {}
     if rank == 0:
-        # roofline of the dominant kernel: algorithmic FP64 flops of the kept terms
-        # (8 per complex x complex term, eq. complexityAlgo's Horner part) / its event time
-        long_mask = L > tuning["long_window"]
-        fl_short = 8.0 * float(nt[~long_mask].sum())
+        # Which points took the tensor-core path: windows of at least min_window
+        # terms (one coefficient piece here), minus any handed back (stats).
+        tcp = F.fpe_get_tensor_path(P)
+        tc_mask = (L >= tcp["min_window"]) if (tcp["min_window"] > 0 and tcp["pieces"] > 0) else np.zeros_like(L, bool)
+        long_mask = (L > tuning["long_window"]) & ~tc_mask
+        short_mask = ~long_mask & ~tc_mask
+        # algorithmic FP64 flops of the kept terms: 8 per complex x complex term
+        # (eq. complexityAlgo's Horner part)
+        fl_short = 8.0 * float(nt[short_mask].sum())
         fl_long = 8.0 * float(nt[long_mask].sum())
+        fl_tc_alg = 8.0 * float(nt[tc_mask].sum())
         fma_peak = F.fpe_measure_fma_peak(64, 5)
-        peak_tflops = 2.0 * fma_peak / 1e12
+        fp64_peak_tflops = 2.0 * fma_peak / 1e12
+        mma_peak_tflops = F.fpe_measure_mma_peak(5) / 1e12
+        bf16_peak, bf16_src = measured_bf16_peak()
+        # the tensor-core kernel's own work: each MMA sub-tile is 8 warps x 220
+        # mma.sync m16n8k16 (4096 flop each) of exact 7-bit slice products
+        fl_tc = float(tcs["subtiles"]) * 8 * 220 * 4096
         kern = {"k_sum_short": (k_short / max(n_short, 1), fl_short),
-                "k_sum_groups": (k_long / max(n_long, 1), fl_long)}
+                "k_sum_groups": (k_long / max(n_long, 1), fl_long),
+                "k_tc_sum": (k_tc / max(n_tc, 1), fl_tc)}
         dom = max(kern, key=lambda k: kern[k][0])
         ms, fl = kern[dom]
-        achieved = fl / (ms * 1e-3) / 1e12
         traffic, traffic_note = measured_traffic(dom)
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                    "traffic_source": traffic_note,
-                    "peak_source": "measured: fpe_measure_fma_peak(64) on this GPU in this run (FP64 FMA x2)",
-                    "share": {k: (v[0] * args.steps) / max(k_all, 1e-9) for k, v in kern.items()},
-                    "all_window_kernels_frac": ((fl_short + fl_long) / ((k_short + k_long + k_fin) / args.steps
-                                                                        * 1e-3) / 1e12 / peak_tflops),
-                    "whole_step_frac": (fl_short + fl_long) / (float(step_ms.mean()) * 1e-3) / 1e12 / peak_tflops,
-                    "flops_per_launch": fl, "launch_ms": ms,
-                    "algorithmic_flops": "8 per kept complex term (4 FMA: one complex multiply-add of "
-                                         "Horner's scheme on G_p cap [l, r])",
-                    "fma_issued_per_term": "4 at or above the peak term, 5 below it (blocks of four)"}
+        share = {k: (v[0] * args.steps) / max(k_all, 1e-9) for k, v in kern.items()}
+        step_s = float(step_ms.mean()) * 1e-3
+        fp64_equiv = {"algorithmic_flops_per_step": fl_short + fl_long + fl_tc_alg,
+                      "achieved_tflops": (fl_short + fl_long + fl_tc_alg) / step_s / 1e12,
+                      "fp64_peak_tflops": fp64_peak_tflops,
+                      "frac_of_fp64_peak": (fl_short + fl_long + fl_tc_alg) / step_s / 1e12 / fp64_peak_tflops,
+                      "note": "8 flop per kept complex term (the paper's count) over the whole step, against the "
+                              "measured FP64 FMA peak; above 1 because the long windows run on the tensor cores"}
+        if dom == "k_tc_sum":
+            achieved = fl / (ms * 1e-3) / 1e12
+            roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": bf16_peak,
+                        "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": traffic,
+                        "traffic_source": traffic_note, "peak_source": bf16_src,
+                        "mma_sync_peak": mma_peak_tflops, "frac_of_mma_sync_peak": achieved / mma_peak_tflops,
+                        "mma_sync_peak_source": "measured: fpe_measure_mma_peak on this GPU in this run",
+                        "share": share, "flops_per_launch": fl, "launch_ms": ms,
+                        "algorithmic_flops": "bf16 tensor flops of the exact slice products: 55 slice pairs x "
+                                             "4 real products per complex term, 2 flop per multiply-add, over "
+                                             "the union of each tile's windows (tensor_stats.subtiles x 7.2e6)",
+                        "tensor_stats": tcs, "fp64_equivalent": fp64_equiv}
+        else:
+            achieved = fl / (ms * 1e-3) / 1e12
+            roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak_tflops,
+                        "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
+                        "traffic_source": traffic_note,
+                        "peak_source": "measured: fpe_measure_fma_peak(64) on this GPU in this run (FP64 FMA x2)",
+                        "share": share, "flops_per_launch": fl, "launch_ms": ms,
+                        "algorithmic_flops": "8 per kept complex term (4 FMA: one complex multiply-add of "
+                                             "Horner's scheme on G_p cap [l, r])",
+                        "fma_issued_per_term": "4 at or above the peak term, 5 below it (blocks of four)",
+                        "fp64_equivalent": fp64_equiv}
         extras["roofline"] = roofline
         extras["gpu_launches"] = int(launches)
         extras["avg_kept_terms"] = float(nt.mean())

@@ -277,6 +277,17 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
  */
 fpe_status fpe_set_tensor_path(fpe_poly_t P, int64_t min_window);
 fpe_status fpe_get_tensor_path(fpe_poly_t P, int64_t *min_window, int32_t *n_pieces);
+/*
+ * fpe_tensor_stats: what the tensor-core path did in the handle's last
+ *   fpe_eval, in stats[0..5]: points it summed, tiles (up to 64 points that
+ *   share a tilt and a block range), work items, MMA sub-tiles (8 blocks of
+ *   32 terms by a tile's points; each is 8 warps x 220 mma.sync of
+ *   m16n8k16, i.e. 7.2e6 bf16 flop), blocks per work item, and the points
+ *   handed back to the FP64 kernels (their group's |z| spread too wide).
+ *   All zero when the path did not run.  Waits for the work queued on
+ *   cuda_stream.  FPE_ERR_INVALID_ARG for NULL arguments or n < 6.
+ */
+fpe_status fpe_tensor_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream);
 
 /*
  * fpe_newton -- one Newton step N_P(z) = z - P(z)/P'(z) (§7.2, eq. newton) at n

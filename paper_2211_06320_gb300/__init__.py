@@ -40,7 +40,7 @@ EXPORTED = [
     "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
     "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex", "fpe_analyse",
     "fpe_set_tuning", "fpe_get_tuning", "fpe_autotune", "fpe_batch_set_tuning", "fpe_batch_autotune",
-    "fpe_set_tensor_path", "fpe_get_tensor_path",
+    "fpe_set_tensor_path", "fpe_get_tensor_path", "fpe_tensor_stats", "fpe_measure_mma_peak",
 ]
 
 
@@ -112,6 +112,8 @@ def _load():
         "fpe_batch_autotune": ([P, P, P, P, ctypes.POINTER(Tuning)], I32),
         "fpe_set_tensor_path": ([P, I64], I32),
         "fpe_get_tensor_path": ([P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32)], I32),
+        "fpe_tensor_stats": ([P, ctypes.POINTER(I64), I32, P], I32),
+        "fpe_measure_mma_peak": ([I32, ctypes.POINTER(D)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -404,6 +406,23 @@ def fpe_get_tensor_path(P: Poly) -> dict:
     mw, npc = ctypes.c_int64(), ctypes.c_int32()
     _check(_load().fpe_get_tensor_path(P.handle, ctypes.byref(mw), ctypes.byref(npc)), "fpe_get_tensor_path")
     return {"min_window": int(mw.value), "pieces": int(npc.value)}
+
+
+TENSOR_STATS = ("points", "tiles", "items", "subtiles", "chunk_blocks", "rejected")
+
+
+def fpe_tensor_stats(P: Poly, stream=None) -> dict:
+    """What the tensor-core path did in the handle's last evaluation (all 0 if it did not run)."""
+    v = (ctypes.c_int64 * len(TENSOR_STATS))()
+    _check(_load().fpe_tensor_stats(P.handle, v, len(TENSOR_STATS), _stream(stream)), "fpe_tensor_stats")
+    return dict(zip(TENSOR_STATS, (int(x) for x in v)))
+
+
+def fpe_measure_mma_peak(reps: int = 5) -> float:
+    """Measured bf16 mma.sync flop/s of the current device (the tensor-core sums' instruction)."""
+    v = ctypes.c_double()
+    _check(_load().fpe_measure_mma_peak(int(reps), ctypes.byref(v)), "fpe_measure_mma_peak")
+    return v.value
 
 
 def fpe_autotune(P: Poly, z_re, z_im=None, stream=None) -> dict:

@@ -97,6 +97,10 @@ constexpr int kCntTcStart = 4;     // 5 words: bucketed start of each tensor-cor
 constexpr int kCntTcWork = 9;      // tensor-core work cursor
 constexpr int kCntTcItems = 10;    // tensor-core work items
 constexpr int kCntTcChunk = 11;    // blocks per tensor-core work item
+constexpr int kCntTcTiles = 12;    // tensor-core tiles
+constexpr int kCntTcSubtiles = 13; // tensor-core MMA sub-tiles
+constexpr int kCntTcPoints = 14;   // points summed on the tensor cores
+constexpr int kCntTcRejected = 15; // tensor-core points handed back to the FP64 kernels
 constexpr int kNumCounters = 16;
 
 // Device view of a preconditioned polynomial, passed to kernels by value.

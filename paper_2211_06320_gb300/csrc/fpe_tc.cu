@@ -211,6 +211,29 @@ __device__ __forceinline__ void slices70(u128 F, uint32_t (&q)[kSl]) {
   }
 }
 
+// signed digits d_0..d_9 of F < 2^69: F = sum_j d_j 128^(9 - j) with every
+// |d_j| <= 64 (a chunk c_j >= 64 becomes c_j - 128 and carries one into the
+// next chunk up; the top chunk is below 64, so it takes the last carry
+// without leaving [0, 64]).  Products of two digits stay within 2^12, and the
+// ten slice pairs of one accumulator over a 64-long dot product within
+// 10 x 2^18 < 2^22: fp32 accumulation is exact with room to spare.
+__device__ __forceinline__ void sdigits70(u128 F, int (&d)[kSl]) {
+  uint32_t c[kSl];
+  slices70(F, c);
+  int carry = 0;
+#pragma unroll
+  for (int j = kSl - 1; j >= 0; --j) {
+    const int x = (int)c[j] + carry;
+    carry = (j > 0 && x >= 64) ? 1 : 0;
+    d[j] = x - (carry << 7);
+  }
+}
+
+// a signed digit (|d| <= 64, exact in bf16) times (-1)^neg, as bf16 bits
+__device__ __forceinline__ uint16_t d_bf16(int d, uint32_t neg) {
+  return q_bf16((uint32_t)(d < 0 ? -d : d), (uint32_t)(d < 0) ^ neg);
+}
+
 // X 2^-sr (sr may be negative), saturated below 2^70
 __device__ __forceinline__ u128 shift_to70(u128 X, int sr) {
   const u128 cap = ((u128)1 << 70) - 1;
@@ -246,13 +269,16 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 // sum_t acc[t] 2^(7 (9 - t)) as a signed 128-bit integer (each acc[t] an
-// integer below 2^24 held exactly in fp32)
+// integer below 2^22 in magnitude held exactly in fp32, read back exactly by
+// adding 1.5 2^23: the integer lands in the low mantissa bits)
+__device__ __forceinline__ int f2i_exact(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
+
 __device__ __forceinline__ void join_acc(const float (&acc)[kSl][4], int c, u128 &mag, int &neg) {
   long long hi = 0, lo = 0;
 #pragma unroll
-  for (int t = 0; t < 5; ++t) hi += (long long)__float2int_rn(acc[t][c]) << (7 * (4 - t));
+  for (int t = 0; t < 5; ++t) hi += (long long)f2i_exact(acc[t][c]) << (7 * (4 - t));
 #pragma unroll
-  for (int t = 5; t < 10; ++t) lo += (long long)__float2int_rn(acc[t][c]) << (7 * (9 - t));
+  for (int t = 5; t < 10; ++t) lo += (long long)f2i_exact(acc[t][c]) << (7 * (9 - t));
   __int128 X = ((__int128)hi << 35) + (__int128)lo;
   neg = X < 0;
   mag = (u128)(neg ? -X : X);
@@ -397,6 +423,7 @@ __global__ void k_tc_groups(DevPoly P, PointRec *__restrict__ rec, const uint32_
   G.piece = j;
   if (31.0 * 0.5 * (mumax - mumin) > kTcTiltBits) {
     // too wide for one tilt: hand the points back to the FP64 kernels
+    if (lane == 0) atomicAdd(&cnt[kCntTcRejected], (uint32_t)count);
     for (int p = lane; p < count; p += 32) {
       const int pos = start + p;
       rec[pos].flags = 0;
@@ -501,11 +528,39 @@ __global__ void __launch_bounds__(1024) k_tc_plan(const TcGroup *__restrict__ gr
     tiles[i] = T;
     item_base[i + 1] = (int32_t)part[1023];
   }
-  if (t == 1023) {
+  // statistics: points, and MMA sub-tiles (8 blocks each) over all items
+  unsigned long long pts = 0, sub = 0;
+  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
+    const TcGroup G = groups[i];
+    if (!G.ok) continue;
+    const long long ipt = (G.nblk + chunk - 1) / chunk;
+    const long long last = G.nblk - (ipt - 1) * chunk;
+    pts += (unsigned long long)G.count;
+    sub += (unsigned long long)ntiles(G) * (unsigned long long)((ipt - 1) * (chunk / kSub) + (last + kSub - 1) / kSub);
+  }
+  __syncthreads();
+  red[t] = pts;
+  __syncthreads();
+  for (int o = 512; o >= 1; o >>= 1) {
+    if (t < o) red[t] += red[t + o];
+    __syncthreads();
+  }
+  const unsigned long long pts_all = red[0];
+  __syncthreads();
+  red[t] = sub;
+  __syncthreads();
+  for (int o = 512; o >= 1; o >>= 1) {
+    if (t < o) red[t] += red[t + o];
+    __syncthreads();
+  }
+  if (t == 0) {
     item_base[ntile_total] = (int32_t)part[1023];
     cnt[kCntTcItems] = part[1023];
     cnt[kCntTcChunk] = (uint32_t)chunk;
     cnt[kCntTcWork] = 0;
+    cnt[kCntTcTiles] = ntile_total;
+    cnt[kCntTcPoints] = (uint32_t)pts_all;
+    cnt[kCntTcSubtiles] = (uint32_t)min(red[0], 0xffffffffull);
   }
 }
 
@@ -571,23 +626,29 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
   uint16_t *zt = zglob + (size_t)t * (kZBytes / 2);
   for (int i = 0; i < kTB; ++i) {
     if (i > 0 && valid) cur = xh_mul(cur, uh);
-    uint32_t qr[kSl], qi[kSl];
-    const int sr = eQ - 7 - (int)cur.e;  // x 2^(e - 63) 2^(70 - eQ) = x 2^-sr: 70-bit fixed point below 2^eQ
-    slices70(valid ? shift_to70((u128)cur.x, sr) : (u128)0, qr);
-    slices70(valid ? shift_to70((u128)cur.y, sr) : (u128)0, qi);
+    int dr[kSl], di[kSl];
+    // x 2^(e - 63) 2^(70 - (eQ + 1)) = x 2^-sr: fixed point below 2^69 (components <= 2^(eQ - 1))
+    const int sr = eQ + 1 - 7 - (int)cur.e;
+    sdigits70(valid ? shift_to70((u128)cur.x, sr) : (u128)0, dr);
+    sdigits70(valid ? shift_to70((u128)cur.y, sr) : (u128)0, di);
     const int cre = zswz(i, p), cim = zswz(kTB + i, p);
 #pragma unroll
     for (int s = 0; s < kSl; ++s) {
-      zt[s * kTK * kTcPoints + cre] = q_bf16(qr[s], (uint32_t)cur.sx);
-      zt[s * kTK * kTcPoints + cim] = q_bf16(qi[s], (uint32_t)cur.sy);
+      zt[s * kTK * kTcPoints + cre] = d_bf16(dr[s], (uint32_t)cur.sx);
+      zt[s * kTK * kTcPoints + cim] = d_bf16(di[s], (uint32_t)cur.sy);
     }
   }
   TcPoint o;
   xint W = zero;
-  if (valid) W = xint_mul(xint_from_xh(xh_mul(cur, uh)), s_tau32);  // u^32 tau^32 = w^32 (to 2^-57)
+  if (valid) {  // W = u^32 tau^32 = w^32 from the 128-bit u: the block weights W^g and
+    // (W^8)^tau of the Horner must not inherit the 64-bit powers' error
+    xint u32 = u;
+    for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
+    W = xint_mul(u32, s_tau32);
+  }
   o.W[0] = W;
   for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
-  o.eq = eQ;
+  o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
   o.pad[0] = o.pad[1] = o.pad[2] = 0;
   pts[(size_t)t * kTcPoints + p] = o;
 }
@@ -682,20 +743,20 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         prod(br, pr, er_);
         prod(bi, pi, ei_);
         for (int o = 16; o >= 1; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
-        const int eR = top == INT_MIN ? 0 : top + 1;  // every |component| < 2^eR
-        uint32_t qr[kSl], qi[kSl];
-        slices70(pr ? shift_to70(pr, eR - 70 - er_) : (u128)0, qr);
-        slices70(pi ? shift_to70(pi, eR - 70 - ei_) : (u128)0, qi);
+        const int eR = top == INT_MIN ? 0 : top + 2;  // every |component| < 2^(eR - 1): below 2^69 in F
+        int qr[kSl], qi[kSl];
+        sdigits70(pr ? shift_to70(pr, eR - 70 - er_) : (u128)0, qr);
+        sdigits70(pi ? shift_to70(pi, eR - 70 - ei_) : (u128)0, qi);
         const uint32_t nr = br < 0.0, ni = bi < 0.0;
         uint16_t *are = &S.aq[0][0][0] + wid * kTK, *aim = &S.aq[0][0][0] + (kSub + wid) * kTK;
         const int c_lo = ((lane >> 3) ^ wid) << 3 | (lane & 7), c_hi = ((4 + (lane >> 3)) ^ wid) << 3 | (lane & 7);
 #pragma unroll
         for (int s = 0; s < kSl; ++s) {
           // out_re row: ( A'_re | -A'_im ), out_im row: ( A'_im | A'_re )
-          are[s * 2 * kSub * kTK + c_lo] = q_bf16(qr[s], nr);
-          are[s * 2 * kSub * kTK + c_hi] = q_bf16(qi[s], ni ^ 1u);
-          aim[s * 2 * kSub * kTK + c_lo] = q_bf16(qi[s], ni);
-          aim[s * 2 * kSub * kTK + c_hi] = q_bf16(qr[s], nr);
+          are[s * 2 * kSub * kTK + c_lo] = d_bf16(qr[s], nr);
+          are[s * 2 * kSub * kTK + c_hi] = d_bf16(qi[s], ni ^ 1u);
+          aim[s * 2 * kSub * kTK + c_lo] = d_bf16(qi[s], ni);
+          aim[s * 2 * kSub * kTK + c_hi] = d_bf16(qr[s], nr);
         }
         if (lane == 0) S.er[wid] = eR;
       }
@@ -921,3 +982,29 @@ fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, 
 }
 
 }  // namespace fpe
+
+extern "C" fpe_status fpe_tensor_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream) {
+  using namespace fpe;
+  if (!P || !stats || n < 6) {
+    set_error("fpe_tensor_stats: NULL handle or output, or n < 6");
+    return FPE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) stats[i] = 0;
+  if (!P->ws.bins || P->ws.nbins <= kNumBins) return FPE_OK;  // the last evaluation did not use the path
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != P->device) cudaSetDevice(P->device);
+  uint32_t c[kNumCounters];
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemcpyAsync(c, P->ws.bins + 2 * P->ws.nbins, sizeof c, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (prev >= 0 && prev != P->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "fpe_tensor_stats");
+  stats[0] = c[kCntTcPoints];
+  stats[1] = c[kCntTcTiles];
+  stats[2] = c[kCntTcItems];
+  stats[3] = c[kCntTcSubtiles];
+  stats[4] = c[kCntTcChunk];
+  stats[5] = c[kCntTcRejected];
+  return FPE_OK;
+}
