@@ -269,8 +269,10 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
  * kernels.  The error stays below 2^-54 sum |a_k||z|^k.
  *
  * fpe_set_tensor_path: min_window in {0} or [32, 2^30]; 0 turns the path
- *   off.  Default 64.  Applies to later fpe_eval calls of that handle
- *   (not to fpe_eval_noalloc, the batch or the gradient paths).
+ *   off.  Default 384 (below a few hundred terms the FP64 kernels are
+ *   cheaper than building a point's slices).  Applies to later fpe_eval
+ *   calls of that handle (not to fpe_eval_noalloc, the batch or the gradient
+ *   paths).
  *   FPE_ERR_INVALID_ARG for a NULL handle or a value out of range.
  * fpe_get_tensor_path: the handle's current min_window, and in *n_pieces the
  *   number of its pieces that qualify (0: the path never runs for it).

@@ -1193,7 +1193,7 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
   const bool cz = z_im != nullptr;
   const bool tc = allow_tc && tc_enabled(P, cz);
   if (tc && (s = ensure_tc_workspace(P, n64)) != FPE_OK) return s;
-  w.nbins = tc ? kNumBins + kTcBins : kNumBins;
+  w.nbins = tc ? kNumBins + P->dev.n_tc * kTcBinsPerPiece : kNumBins;  // bins of the pieces that exist
   const long long tcw = tc ? (long long)P->tune.tc_min_window : 0;
   cudaError_t e = cudaMemsetAsync(w.bins, 0, w.nbins * sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -1224,7 +1224,7 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  if (tc) return launch_tc_plan(P, n, st);
+  if (tc) return launch_tc_groups(P, n, st);
   return FPE_OK;
 }
 
@@ -1245,7 +1245,10 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
     launch_sums<false, true>(P, n, out, nterms, bits_lost, st);
   else
     launch_sums<false, false>(P, n, out, nterms, bits_lost, st);
-  if (tc && (s = launch_tc_sums(P, n, out, nterms, bits_lost, st)) != FPE_OK) return s;
+  if (tc) {
+    if ((s = launch_tc_plan(P, n, st)) != FPE_OK) return s;
+    if ((s = launch_tc_sums(P, n, out, nterms, bits_lost, st)) != FPE_OK) return s;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   P->last_n = n64;

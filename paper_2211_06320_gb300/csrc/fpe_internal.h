@@ -67,7 +67,7 @@ constexpr int64_t kMaxLaneChunk = 1024;
 struct Tuning {
   int64_t long_window = kLongWindow;
   int64_t lane_chunk = kMaxLaneChunk;
-  int64_t tc_min_window = 64;  // tensor-core window sums for windows of at least this many terms (0: off)
+  int64_t tc_min_window = 384;  // tensor-core window sums for windows of at least this many terms (0: off)
   int64_t group_span() const { return 32 * lane_chunk; }
 };
 
@@ -248,6 +248,7 @@ fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, 
 // (tc_plan runs before the other window kernels: it hands back tiles it rejects)
 bool tc_enabled(const fpe_poly_s *P, bool complex_points);
 fpe_status ensure_tc_workspace(fpe_poly_s *P, int64_t n);
+fpe_status launch_tc_groups(fpe_poly_s *P, int n, cudaStream_t st);
 fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st);
 fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
                           cudaStream_t st);

@@ -917,6 +917,7 @@ fpe_status ensure_tc_workspace(fpe_poly_s *P, int64_t n) {
   return FPE_OK;
 }
 
+
 // the kernels' dynamic shared memory above the default 48 KB, once per device
 static fpe_status tc_set_smem_attrs() {
   static bool attr_set[64] = {false};
@@ -932,12 +933,12 @@ static fpe_status tc_set_smem_attrs() {
   return FPE_OK;
 }
 
-fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
+fpe_status launch_tc_groups(fpe_poly_s *P, int n, cudaStream_t st) {
   fpe_status s = tc_set_smem_attrs();
   if (s != FPE_OK) return s;
   Workspace &w = P->ws;
   uint32_t *cnt = w.bins + 2 * w.nbins;
-  const int tm = (int)tc_tiles_max(n), gm = (int)tc_groups_max(n);
+  const int gm = (int)tc_groups_max(n);
   {
     ProfScope ps("k_tc_groups", st);
     k_tc_groups<<<(gm + 7) / 8, 256, 0, st>>>(P->dev, w.rec, w.bins, w.nbins, cnt, (TcGroup *)w.tc_groups, gm,
@@ -945,6 +946,14 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
                                               w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,
                                               (int)w.extra_cap);
   }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core groups launch");
+}
+
+fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
+  Workspace &w = P->ws;
+  uint32_t *cnt = w.bins + 2 * w.nbins;
+  const int tm = (int)tc_tiles_max(n), gm = (int)tc_groups_max(n);
   {
     ProfScope ps("k_tc_plan", st);
     k_tc_plan<<<1, 1024, 0, st>>>((const TcGroup *)w.tc_groups, gm, (TcTile *)w.tc_tiles, tm, w.tc_item_base,
@@ -953,7 +962,7 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
   {
     ProfScope ps("k_tc_pre", st);
     k_tc_pre<<<tm, kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, (TcPoint *)w.tc_points,
-                                                 (TcTau *)w.tc_taus, (uint16_t *)w.tc_z);
+                                       (TcTau *)w.tc_taus, (uint16_t *)w.tc_z);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core plan launch");

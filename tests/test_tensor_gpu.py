@@ -40,12 +40,15 @@ def _eval(env, P, zre, zim):
     return out.cpu().numpy(), nt.cpu().numpy(), F.fpe_tensor_stats(P)
 
 
-def _check(env, coef, zre, zim, n_full=128, min_tc_points=1):
-    """Tensor path on: values vs the oracle (window sums on every point, full
-    Horner on a sample); returns the stats and the outputs."""
+def _check(env, coef, zre, zim, n_full=128, min_tc_points=1, min_window=64):
+    """Tensor path on for windows of at least min_window terms (64: more
+    points than the default takes, down to one block per window): values vs
+    the oracle (window sums on every point, full Horner on a sample); returns
+    the stats and the outputs."""
     torch, F = env
     P = F.fpe_precondition(coef.re, coef.im, coef.e2, 53)
     assert F.fpe_get_tensor_path(P)["pieces"] >= 1
+    F.fpe_set_tensor_path(P, min_window)
     out, nt, st = _eval(env, P, zre, zim)
     assert st["points"] >= min_tc_points, st
     pre = oracle.precondition(coef, 53)
@@ -82,6 +85,17 @@ def test_sphere_points_unit_disk(env):
     pts = W.sphere_points(1 << 15, rng)
     _, st, _ = _check(env, coef, pts.re, pts.im, min_tc_points=1 << 13)
     assert st["tiles"] >= 1 and st["subtiles"] >= st["items"] >= st["tiles"]
+
+
+def test_default_threshold(env):
+    """The default setting (windows of 384 terms or more) on sphere points."""
+    torch, F = env
+    rng = np.random.default_rng(108)
+    coef = _flat_disk(1 << 16, rng)
+    pts = W.sphere_points(1 << 14, rng)
+    P = F.fpe_precondition(coef.re, coef.im)
+    assert F.fpe_get_tensor_path(P)["min_window"] == 384
+    _check(env, coef, pts.re, pts.im, min_tc_points=512, min_window=384)
 
 
 def test_reproducible_and_same_as_fp64_path(env):
