@@ -178,6 +178,7 @@ struct Workspace {
   void *tc_taus = nullptr;          // TcTau per tile
   void *tc_z = nullptr;             // Z' slices per tile
   void *tc_groups = nullptr;        // TcGroup per group of bins
+  void *tc_plan = nullptr;          // planning scratch (totals; per group tiles, first tile, first item)
   int64_t tc_cap = 0;               // points the tensor-core arrays are sized for
   void *host_pinned = nullptr;   // staging for fpe_eval_host
   size_t host_pinned_bytes = 0;

@@ -175,7 +175,7 @@ struct TcSmem {
   uint16_t zq[kSl][kTK][kTcPoints];   // Z' slices (bf16 bits); rows kappa of the 64 points, chunks swizzled
   uint16_t aq[kSl][2 * kSub][kTK];    // A' slices of the current sub-tile
   xh w8[kTcPoints];                   // W^8 per point (64-bit mantissas)
-  xint w1[kTcPoints];                 // W per point (the final combination)
+  xh w1[kTcPoints];                   // W per point (the final combination)
   unsigned long long tm[kTB];         // tau^i = tm[i] 2^te[i]
   int te[kTB];
   int eq[kTcPoints];                  // Z' scale exponent per point
@@ -443,69 +443,130 @@ __global__ void k_tc_groups(DevPoly P, PointRec *__restrict__ rec, const uint32_
 }
 
 // ---------------------------------------------------------------------------
-// plan (one block): tiles of each group, blocks per work item (so that there
-// are about kTcItemsPerSm items per SM, each at least kTcMinChunk blocks), and
-// each tile's first work item
+// plan, in three launches: (a) per group its tile count, with the blocks of
+// all tiles and the points summed into 64-bit totals; (b) one block: blocks
+// per work item (about kTcItemsPerSm items per SM, each at least
+// kTcMinChunk blocks) and the scans of tiles and items over the groups;
+// (c) per group its tiles, their first items and each item's tile.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_tc_plan(const TcGroup *__restrict__ groups, int groups_max,
-                                                  TcTile *__restrict__ tiles, int tiles_max,
-                                                  int32_t *__restrict__ item_base,
-                                                  int32_t *__restrict__ item_tile, uint32_t *cnt, int nsms) {
-  __shared__ unsigned long long red[1024];
-  __shared__ uint32_t part[1024];
-  __shared__ long long s_chunk;
-  const int t = threadIdx.x;
-  const int per = (groups_max + 1023) / 1024;
-  auto ntiles = [&](const TcGroup &G) { return G.ok ? (G.count + kTcPoints - 1) / kTcPoints : 0; };
-  unsigned long long blocks = 0;
-  uint32_t mytiles = 0;
-  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
-    const TcGroup G = groups[i];
-    blocks += (unsigned long long)ntiles(G) * (unsigned long long)G.nblk;
-    mytiles += (uint32_t)ntiles(G);
+struct TcPlanAcc {
+  unsigned long long blocks, points;
+};
+
+__device__ __forceinline__ int tc_ntiles(const TcGroup &G) {
+  return G.ok ? (G.count + kTcPoints - 1) / kTcPoints : 0;
+}
+
+__global__ void __launch_bounds__(256) k_tc_plan_a(const TcGroup *__restrict__ groups, int gm,
+                                                   int32_t *__restrict__ g_nt, TcPlanAcc *acc) {
+  __shared__ unsigned long long sb[8], sp[8];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long blocks = 0, pts = 0;
+  if (g < gm) {
+    const TcGroup G = groups[g];
+    const int nt = tc_ntiles(G);
+    g_nt[g] = nt;
+    if (nt) {
+      blocks = (unsigned long long)nt * (unsigned long long)G.nblk;
+      pts = (unsigned long long)G.count;
+    }
   }
-  red[t] = blocks;
-  part[t] = mytiles;
+  for (int o = 16; o >= 1; o >>= 1) {
+    blocks += __shfl_xor_sync(0xffffffffu, blocks, o);
+    pts += __shfl_xor_sync(0xffffffffu, pts, o);
+  }
+  if (lane == 0) {
+    sb[wid] = blocks;
+    sp[wid] = pts;
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tb = 0, tp = 0;
+    for (int i = 0; i < 8; ++i) {
+      tb += sb[i];
+      tp += sp[i];
+    }
+    if (tb) atomicAdd(&acc->blocks, tb);
+    if (tp) atomicAdd(&acc->points, tp);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_tc_plan_b(const TcGroup *__restrict__ groups, int gm,
+                                                    const int32_t *__restrict__ g_nt, const TcPlanAcc *acc,
+                                                    int32_t *__restrict__ g_tile0, int32_t *__restrict__ g_item0,
+                                                    uint32_t *cnt, int nsms) {
+  __shared__ uint32_t pt[1024], pi[1024];
+  __shared__ unsigned long long red[1024];
+  const int t = threadIdx.x;
+  const int per = (gm + 1023) / 1024;
+  const unsigned long long target = (unsigned long long)nsms * kTcItemsPerSm;
+  long long chunk = (long long)((acc->blocks + target - 1) / target);
+  chunk = std::max<long long>(chunk, kTcMinChunk);
+  chunk = (chunk + kSub - 1) / kSub * kSub;
+  uint32_t ntl = 0, nit = 0;
+  unsigned long long sub = 0;
+  const int g0 = min(gm, t * per), g1 = min(gm, (t + 1) * per);
+  for (int g = g0; g < g1; ++g) {
+    const int nt = g_nt[g];
+    if (!nt) continue;
+    const long long nblk = groups[g].nblk;
+    const long long ipt = (nblk + chunk - 1) / chunk;
+    ntl += (uint32_t)nt;
+    nit += (uint32_t)(nt * ipt);
+    sub += (unsigned long long)nt * (unsigned long long)((ipt - 1) * (chunk / kSub) +
+                                                         (nblk - (ipt - 1) * chunk + kSub - 1) / kSub);
+  }
+  pt[t] = ntl;
+  pi[t] = nit;
+  red[t] = sub;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scans of tiles and items
+    const uint32_t a = t >= o ? pt[t - o] : 0u, b = t >= o ? pi[t - o] : 0u;
+    __syncthreads();
+    pt[t] += a;
+    pi[t] += b;
+    __syncthreads();
+  }
   for (int o = 512; o >= 1; o >>= 1) {
     if (t < o) red[t] += red[t + o];
     __syncthreads();
   }
+  uint32_t tt = pt[t] - ntl, it = pi[t] - nit;
+  for (int g = g0; g < g1; ++g) {
+    const int nt = g_nt[g];
+    g_tile0[g] = (int32_t)tt;
+    g_item0[g] = (int32_t)it;
+    if (!nt) continue;
+    const long long ipt = (groups[g].nblk + chunk - 1) / chunk;
+    tt += (uint32_t)nt;
+    it += (uint32_t)(nt * ipt);
+  }
   if (t == 0) {
-    const unsigned long long target = (unsigned long long)nsms * kTcItemsPerSm;
-    long long ch = (long long)((red[0] + target - 1) / target);
-    ch = std::max<long long>(ch, kTcMinChunk);
-    s_chunk = (ch + kSub - 1) / kSub * kSub;
+    cnt[kCntTcItems] = pi[1023];
+    cnt[kCntTcChunk] = (uint32_t)chunk;
+    cnt[kCntTcWork] = 0;
+    cnt[kCntTcTiles] = pt[1023];
+    cnt[kCntTcPoints] = (uint32_t)acc->points;
+    cnt[kCntTcSubtiles] = (uint32_t)min(red[0], 0xffffffffull);
   }
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the tile counts
-    const uint32_t v = t >= o ? part[t - o] : 0u;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  const uint32_t ntile_total = part[1023];
-  const uint32_t tile0 = part[t] - mytiles;
-  __syncthreads();
-  const long long chunk = s_chunk;
-  uint32_t myitems = 0;
-  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
-    const TcGroup G = groups[i];
-    myitems += (uint32_t)ntiles(G) * (uint32_t)((G.nblk + chunk - 1) / chunk);
-  }
-  part[t] = myitems;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t v = t >= o ? part[t - o] : 0u;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  uint32_t tt = tile0, it = part[t] - myitems;
-  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
-    const TcGroup G = groups[i];
-    const int nt = ntiles(G);
-    const uint32_t ipt = (uint32_t)((G.nblk + chunk - 1) / chunk);
-    for (int lt = 0; lt < nt; ++lt, ++tt) {
+}
+
+__global__ void __launch_bounds__(256) k_tc_plan_c(const TcGroup *__restrict__ groups, int gm,
+                                                   const int32_t *__restrict__ g_nt,
+                                                   const int32_t *__restrict__ g_tile0,
+                                                   const int32_t *__restrict__ g_item0, const uint32_t *cnt,
+                                                   TcTile *__restrict__ tiles, int tiles_max,
+                                                   int32_t *__restrict__ item_base, int32_t *__restrict__ item_tile) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const long long chunk = (long long)cnt[kCntTcChunk];
+  const int ntile_total = (int)cnt[kCntTcTiles];
+  const int nitem_total = (int)cnt[kCntTcItems];
+  if (tid < gm && g_nt[tid]) {
+    const TcGroup G = groups[tid];
+    const int nt = g_nt[tid];
+    const int ipt = (int)((G.nblk + chunk - 1) / chunk);
+    for (int lt = 0; lt < nt; ++lt) {
+      const int tt = g_tile0[tid] + lt, it = g_item0[tid] + lt * ipt;
       TcTile T;
       T.start = G.start + kTcPoints * lt;
       T.count = min(kTcPoints, G.count - kTcPoints * lt);
@@ -515,53 +576,19 @@ __global__ void __launch_bounds__(1024) k_tc_plan(const TcGroup *__restrict__ gr
       T.nblk = G.nblk;
       T.c = G.c;
       tiles[tt] = T;
-      item_base[tt] = (int32_t)it;
-      for (uint32_t c = 0; c < ipt; ++c) item_tile[it + c] = (int32_t)tt;
-      it += ipt;
+      item_base[tt] = it;
+      for (int c = 0; c < ipt; ++c) item_tile[it + c] = tt;
     }
   }
-  for (int i = (int)ntile_total + t; i < tiles_max; i += 1024) {  // unused tiles
+  for (int i = ntile_total + tid; i < tiles_max; i += nthr) {  // unused tiles
     TcTile T;
     T.start = T.count = T.piece = T.ok = 0;
     T.mlo = T.nblk = 0;
     T.c = 0.0;
     tiles[i] = T;
-    item_base[i + 1] = (int32_t)part[1023];
+    item_base[i + 1] = nitem_total;
   }
-  // statistics: points, and MMA sub-tiles (8 blocks each) over all items
-  unsigned long long pts = 0, sub = 0;
-  for (int i = t * per; i < min(groups_max, (t + 1) * per); ++i) {
-    const TcGroup G = groups[i];
-    if (!G.ok) continue;
-    const long long ipt = (G.nblk + chunk - 1) / chunk;
-    const long long last = G.nblk - (ipt - 1) * chunk;
-    pts += (unsigned long long)G.count;
-    sub += (unsigned long long)ntiles(G) * (unsigned long long)((ipt - 1) * (chunk / kSub) + (last + kSub - 1) / kSub);
-  }
-  __syncthreads();
-  red[t] = pts;
-  __syncthreads();
-  for (int o = 512; o >= 1; o >>= 1) {
-    if (t < o) red[t] += red[t + o];
-    __syncthreads();
-  }
-  const unsigned long long pts_all = red[0];
-  __syncthreads();
-  red[t] = sub;
-  __syncthreads();
-  for (int o = 512; o >= 1; o >>= 1) {
-    if (t < o) red[t] += red[t + o];
-    __syncthreads();
-  }
-  if (t == 0) {
-    item_base[ntile_total] = (int32_t)part[1023];
-    cnt[kCntTcItems] = part[1023];
-    cnt[kCntTcChunk] = (uint32_t)chunk;
-    cnt[kCntTcWork] = 0;
-    cnt[kCntTcTiles] = ntile_total;
-    cnt[kCntTcPoints] = (uint32_t)pts_all;
-    cnt[kCntTcSubtiles] = (uint32_t)min(red[0], 0xffffffffull);
-  }
+  if (tid == 0) item_base[ntile_total] = nitem_total;
 }
 
 // ---------------------------------------------------------------------------
@@ -697,7 +724,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const bool v = tid < T.count;
         S.w8[tid] = xh_from_xint(v ? tp[tid].W[3] : zero);
         S.eq[tid] = v ? tp[tid].eq : 1;
-        S.w1[tid] = v ? tp[tid].W[0] : zero;
+        S.w1[tid] = xh_from_xint(v ? tp[tid].W[0] : zero);
       }
     }
     __syncthreads();
@@ -807,19 +834,20 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       }
     }
     // ---- V = sum_g W^g H_g: the lanes' H into shared memory (over the Z'
-    // tiles, no longer read), then one thread per point, Horner over g
-    xint *hs = reinterpret_cast<xint *>(&S.zq[0][0][0]);  // [point][g]
-    hs[p0 * kSub + g] = xint_from_xh(H0);
-    hs[(p0 + 1) * kSub + g] = xint_from_xh(H1);
+    // tiles, no longer read), then one thread per point, Horner over g in
+    // 64-bit mantissas (seven steps: within 2^-57 of the terms' sum)
+    xh *hs = reinterpret_cast<xh *>(&S.zq[0][0][0]);  // [point][g]
+    hs[p0 * kSub + g] = H0;
+    hs[(p0 + 1) * kSub + g] = H1;
     __syncthreads();
     if (tid < T.count) {
-      const xint W = S.w1[tid];
-      xint V = hs[tid * kSub + kSub - 1];
+      const xh W = S.w1[tid];
+      xh V = hs[tid * kSub + kSub - 1];
       for (int gg = kSub - 2; gg >= 0; --gg) {
-        if (V.x || V.y) V = xint_mul(V, W);
-        V = xint_add(V, hs[tid * kSub + gg]);
+        if (V.x || V.y) V = xh_mul(V, W);
+        V = xh_add(V, hs[tid * kSub + gg]);
       }
-      slots[(size_t)item * kTcPoints + tid] = V;
+      slots[(size_t)item * kTcPoints + tid] = xint_from_xh(V);
     }
     __syncthreads();  // shared memory is reused by the next item
   }
@@ -881,7 +909,7 @@ bool tc_enabled(const fpe_poly_s *P, bool complex_points) {
 
 void free_tc_workspace(Workspace &w) {
   void *ptrs[] = {w.tc_tiles, w.tc_item_base, w.tc_slots, w.tc_points, w.tc_item_tile, w.tc_taus, w.tc_z,
-                  w.tc_groups};
+                  w.tc_groups, w.tc_plan};
   for (void *a : ptrs)
     if (a) cudaFree(a);
   w.tc_tiles = nullptr;
@@ -892,6 +920,7 @@ void free_tc_workspace(Workspace &w) {
   w.tc_taus = nullptr;
   w.tc_z = nullptr;
   w.tc_groups = nullptr;
+  w.tc_plan = nullptr;
   w.tc_cap = 0;
 }
 
@@ -909,6 +938,9 @@ fpe_status ensure_tc_workspace(fpe_poly_s *P, int64_t n) {
   if (e == cudaSuccess) e = cudaMalloc(&w.tc_taus, (size_t)tm * sizeof(TcTau));
   if (e == cudaSuccess) e = cudaMalloc(&w.tc_z, (size_t)tm * kZBytes);
   if (e == cudaSuccess) e = cudaMalloc(&w.tc_groups, (size_t)tc_groups_max(cap) * sizeof(TcGroup));
+  // plan scratch: the 64-bit totals, then per group its tiles, first tile and first item
+  if (e == cudaSuccess)
+    e = cudaMalloc(&w.tc_plan, sizeof(TcPlanAcc) + 3 * (size_t)tc_groups_max(cap) * sizeof(int32_t));
   if (e != cudaSuccess) {
     free_tc_workspace(w);
     return cuda_fail(e, "cudaMalloc(tensor-core workspace)");
@@ -956,8 +988,15 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
   const int tm = (int)tc_tiles_max(n), gm = (int)tc_groups_max(n);
   {
     ProfScope ps("k_tc_plan", st);
-    k_tc_plan<<<1, 1024, 0, st>>>((const TcGroup *)w.tc_groups, gm, (TcTile *)w.tc_tiles, tm, w.tc_item_base,
-                                  w.tc_item_tile, cnt, tc_num_sms());
+    TcPlanAcc *acc = (TcPlanAcc *)w.tc_plan;
+    int32_t *g_nt = (int32_t *)(acc + 1), *g_tile0 = g_nt + gm, *g_item0 = g_tile0 + gm;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(TcPlanAcc), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(plan)");
+    k_tc_plan_a<<<(gm + 255) / 256, 256, 0, st>>>((const TcGroup *)w.tc_groups, gm, g_nt, acc);
+    k_tc_plan_b<<<1, 1024, 0, st>>>((const TcGroup *)w.tc_groups, gm, g_nt, acc, g_tile0, g_item0, cnt,
+                                    tc_num_sms());
+    k_tc_plan_c<<<(gm + 255) / 256, 256, 0, st>>>((const TcGroup *)w.tc_groups, gm, g_nt, g_tile0, g_item0, cnt,
+                                                  (TcTile *)w.tc_tiles, tm, w.tc_item_base, w.tc_item_tile);
   }
   {
     ProfScope ps("k_tc_pre", st);
