@@ -183,12 +183,6 @@ struct TcSmem {
   int item, tile;
 };
 
-// element index of (row, kappa) in a [rows][64] bf16 array with the 16-B
-// chunk index xor-ed by row & 7 (ldmatrix reads 8 rows without bank conflicts)
-__device__ __forceinline__ int swz(int row, int kappa) {
-  return row * kTK + ((((kappa >> 3) ^ (row & 7)) << 3) | (kappa & 7));
-}
-
 // Z' layout, per slice: 64 rows (kappa) of the 64 points' values (128 B), the
 // 16-B chunk (8 points) xor-ed by kappa & 7; B fragments are read transposed
 __device__ __forceinline__ int zswz(int kappa, int p) {
@@ -315,17 +309,6 @@ __device__ __forceinline__ void tc_write_diag(const DevPoly &P, const PointRec &
   }
 }
 
-// V z^(kb + v) 2^rho(kb): the window value from its block sum starting at
-// trimmed index kb of piece j
-__device__ __forceinline__ fpe_xc64 tc_output(const DevPoly &P, int j, long long kb, const PointRec &r, xint V) {
-  const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
-  const long long rho = P.piece_rho0[j] + (long long)P.piece_beta[j] * (kb - P.piece_k0[j]);
-  if (V.x || V.y) {
-    V = xint_mul(V, xint_pow_z(r.zr, r.zi, kb + P.v, f));
-    V.e += rho;
-  }
-  return xc64_from_xint(V);
-}
 
 }  // namespace
 
@@ -600,84 +583,87 @@ __global__ void __launch_bounds__(256) k_tc_plan_c(const TcGroup *__restrict__ g
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
                                                       const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
-                                                      TcTau *__restrict__ taus, uint16_t *__restrict__ zglob) {
+                                                      TcTau *__restrict__ taus, uint16_t *__restrict__ zglob,
+                                                      const uint32_t *cnt) {
   __shared__ xint s_inv, s_tau32;
   __shared__ double s_tmant;
   __shared__ int s_tf;
-  const int t = blockIdx.x, p = threadIdx.x;
-  const TcTile T = tiles[t];
-  if (!T.ok) return;  // block-uniform
-  if (p == 0) {  // tau = tmant 2^tf, tmant in [0.5, 1); 1 / tau; tau^32
-    const double tau = exp2(T.c);
-    const int tf = frexp_exp(tau);
-    const double tmant = scale2(tau, -tf);
-    xint inv = recip_xint(tmant, 0.0);
-    inv.e -= tf;
-    xint t32 = xint_pow_unit(tmant, 0.0, kTB);
-    t32.e += (long long)tf * kTB;
-    s_inv = inv;
-    s_tau32 = t32;
-    s_tmant = tmant;
-    s_tf = tf;
-  }
-  __syncthreads();
-  if (p < kTB) {
-    xint ti = xint_norm((u128)1 << 126, 0, 0, 0, 0);
-    if (p > 0) {
-      ti = xint_pow_unit(s_tmant, 0.0, p);
-      ti.e += (long long)s_tf * p;
+  const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TcTile T = tiles[t];
+    __syncthreads();  // the previous tile's shared values are read
+    if (p == 0) {  // tau = tmant 2^tf, tmant in [0.5, 1); 1 / tau; tau^32
+      const double tau = exp2(T.c);
+      const int tf = frexp_exp(tau);
+      const double tmant = scale2(tau, -tf);
+      xint inv = recip_xint(tmant, 0.0);
+      inv.e -= tf;
+      xint t32 = xint_pow_unit(tmant, 0.0, kTB);
+      t32.e += (long long)tf * kTB;
+      s_inv = inv;
+      s_tau32 = t32;
+      s_tmant = tmant;
+      s_tf = tf;
     }
-    taus[t].tm[p] = (unsigned long long)(ti.x >> 63);  // in [2^63, 2^64)
-    taus[t].te[p] = (int)(ti.e - 63);
-  }
-  const bool valid = p < T.count;
-  const xint zero = xint_norm(0, 0, 0, 0, 0);
-  xint u = zero;
-  xh uh = xh_norm(0, 0, 0, 0, 0), cur = uh;
-  int eQ = 1;
-  if (valid) {
-    const PointRec r = rec[T.start + p];
-    u = xint_mul(xint_from_dd2(r.zr, 0.0, r.zi, 0.0, P.piece_beta[T.piece]), s_inv);
-    uh = xh_from_xint(u);
-    // every |component of u^i| (i < 32) is at most |u|^31 <= 2^(eQ - 1); |u| is
-    // near 1, so log2|u| in FP32 (error far below the 1e-3 / 31 margin) suffices:
-    // |u| = sqrt(mx^2 + my^2) 2^e with mx = X 2^-126 (X the magnitude, top bit at 126)
-    const float mx = (float)(unsigned long long)(u.x >> 64) * 0x1p-62f;
-    const float my = (float)(unsigned long long)(u.y >> 64) * 0x1p-62f;
-    const float l = 0.5f * log2f(fmaf(mx, mx, my * my)) + (float)u.e;
-    eQ = max(0, (int)ceilf(31.0f * l + 1e-3f)) + 1;
-    cur = xh_norm(1ull << 63, 0, 0, 0, 0);  // 1
-  }
-  // powers u^i in 64-bit mantissas: each product truncates at 2^-63, so u^31
-  // is within 2^-58 of its value relative to itself
-  uint16_t *zt = zglob + (size_t)t * (kZBytes / 2);
-  for (int i = 0; i < kTB; ++i) {
-    if (i > 0 && valid) cur = xh_mul(cur, uh);
-    int dr[kSl], di[kSl];
-    // x 2^(e - 63) 2^(70 - (eQ + 1)) = x 2^-sr: fixed point below 2^69 (components <= 2^(eQ - 1))
-    const int sr = eQ + 1 - 7 - (int)cur.e;
-    sdigits70(valid ? shift_to70((u128)cur.x, sr) : (u128)0, dr);
-    sdigits70(valid ? shift_to70((u128)cur.y, sr) : (u128)0, di);
-    const int cre = zswz(i, p), cim = zswz(kTB + i, p);
-#pragma unroll
-    for (int s = 0; s < kSl; ++s) {
-      zt[s * kTK * kTcPoints + cre] = d_bf16(dr[s], (uint32_t)cur.sx);
-      zt[s * kTK * kTcPoints + cim] = d_bf16(di[s], (uint32_t)cur.sy);
+    __syncthreads();
+    if (p < kTB) {
+      xint ti = xint_norm((u128)1 << 126, 0, 0, 0, 0);
+      if (p > 0) {
+        ti = xint_pow_unit(s_tmant, 0.0, p);
+        ti.e += (long long)s_tf * p;
+      }
+      taus[t].tm[p] = (unsigned long long)(ti.x >> 63);  // in [2^63, 2^64)
+      taus[t].te[p] = (int)(ti.e - 63);
     }
+    const bool valid = p < T.count;
+    const xint zero = xint_norm(0, 0, 0, 0, 0);
+    xint u = zero;
+    xh uh = xh_norm(0, 0, 0, 0, 0), cur = uh;
+    int eQ = 1;
+    if (valid) {
+      const PointRec r = rec[T.start + p];
+      u = xint_mul(xint_from_dd2(r.zr, 0.0, r.zi, 0.0, P.piece_beta[T.piece]), s_inv);
+      uh = xh_from_xint(u);
+      // every |component of u^i| (i < 32) is at most |u|^31 <= 2^(eQ - 1); |u| is
+      // near 1, so log2|u| in FP32 (error far below the 1e-3 / 31 margin) suffices:
+      // |u| = sqrt(mx^2 + my^2) 2^e with mx = X 2^-126 (X the magnitude, top bit at 126)
+      const float mx = (float)(unsigned long long)(u.x >> 64) * 0x1p-62f;
+      const float my = (float)(unsigned long long)(u.y >> 64) * 0x1p-62f;
+      const float l = 0.5f * log2f(fmaf(mx, mx, my * my)) + (float)u.e;
+      eQ = max(0, (int)ceilf(31.0f * l + 1e-3f)) + 1;
+      cur = xh_norm(1ull << 63, 0, 0, 0, 0);  // 1
+    }
+    // powers u^i in 64-bit mantissas: each product truncates at 2^-63, so u^31
+    // is within 2^-58 of its value relative to itself
+    uint16_t *zt = zglob + (size_t)t * (kZBytes / 2);
+    for (int i = 0; i < kTB; ++i) {
+      if (i > 0 && valid) cur = xh_mul(cur, uh);
+      int dr[kSl], di[kSl];
+      // x 2^(e - 63) 2^(70 - (eQ + 1)) = x 2^-sr: fixed point below 2^69 (components <= 2^(eQ - 1))
+      const int sr = eQ + 1 - 7 - (int)cur.e;
+      sdigits70(valid ? shift_to70((u128)cur.x, sr) : (u128)0, dr);
+      sdigits70(valid ? shift_to70((u128)cur.y, sr) : (u128)0, di);
+      const int cre = zswz(i, p), cim = zswz(kTB + i, p);
+  #pragma unroll
+      for (int s = 0; s < kSl; ++s) {
+        zt[s * kTK * kTcPoints + cre] = d_bf16(dr[s], (uint32_t)cur.sx);
+        zt[s * kTK * kTcPoints + cim] = d_bf16(di[s], (uint32_t)cur.sy);
+      }
+    }
+    TcPoint o;
+    xint W = zero;
+    if (valid) {  // W = u^32 tau^32 = w^32 from the 128-bit u: the block weights W^g and
+      // (W^8)^tau of the Horner must not inherit the 64-bit powers' error
+      xint u32 = u;
+      for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
+      W = xint_mul(u32, s_tau32);
+    }
+    o.W[0] = W;
+    for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
+    o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
+    o.pad[0] = o.pad[1] = o.pad[2] = 0;
+    pts[(size_t)t * kTcPoints + p] = o;
   }
-  TcPoint o;
-  xint W = zero;
-  if (valid) {  // W = u^32 tau^32 = w^32 from the 128-bit u: the block weights W^g and
-    // (W^8)^tau of the Horner must not inherit the 64-bit powers' error
-    xint u32 = u;
-    for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
-    W = xint_mul(u32, s_tau32);
-  }
-  o.W[0] = W;
-  for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
-  o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
-  o.pad[0] = o.pad[1] = o.pad[2] = 0;
-  pts[(size_t)t * kTcPoints + p] = o;
 }
 
 // ---------------------------------------------------------------------------
@@ -853,34 +839,69 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   }
 }
 
-// Per tile point: Horner over the tile's items in W^chunk (item c starts
-// chunk c blocks after the first), then z^(kb + v) 2^rho(kb) with kb the
-// first block's index, and the point's output.
-__global__ void __launch_bounds__(kTcPoints) k_tc_finalize(DevPoly P, const PointRec *__restrict__ rec,
-                                                           const TcTile *__restrict__ tiles,
-                                                           const int32_t *__restrict__ item_base, const uint32_t *cnt,
-                                                           const xint *__restrict__ slots, fpe_xc64 *__restrict__ out,
-                                                           int32_t *nterms, int32_t *bits_lost) {
-  const int t = blockIdx.x, p = threadIdx.x;
-  const TcTile T = tiles[t];
-  if (!T.ok || p >= T.count) return;
-  const int base = item_base[t], nit = item_base[t + 1] - base;
-  const long long chunk = (long long)cnt[kCntTcChunk];
-  const PointRec r = rec[T.start + p];
-  const int j = T.piece;
-  xint V = slots[(size_t)(base + nit - 1) * kTcPoints + p];
-  if (nit > 1) {
-    const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
-    xint Wc = xint_pow_z(r.zr, r.zi, kTB * chunk, f);
-    Wc.e += (long long)kTB * chunk * P.piece_beta[j];
-    for (int c = nit - 2; c >= 0; --c) {
-      if (V.x || V.y) V = xint_mul(V, Wc);
-      V = xint_add(V, slots[(size_t)(base + c) * kTcPoints + p]);
+// Per tile point: the sum over the tile's items, item c starting c chunks of
+// blocks after the first, i.e. sum_c V_c (W^chunk)^c; then z^(kb + v)
+// 2^rho(kb) with kb the first block's index, and the point's output.  Four
+// threads per point: thread q takes a contiguous quarter of the items by
+// Horner in Wc = W^chunk and scales it by Wc^(its first item); thread 1 also
+// computes z^(kb + v); the four parts are added by shuffles.
+constexpr int kFinLanes = 4;
+__global__ void __launch_bounds__(kFinLanes * kTcPoints)
+    k_tc_finalize(DevPoly P, const PointRec *__restrict__ rec, const TcTile *__restrict__ tiles,
+                  const int32_t *__restrict__ item_base, const uint32_t *cnt, const xint *__restrict__ slots,
+                  fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
+  const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x / kFinLanes, q = threadIdx.x % kFinLanes;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TcTile T = tiles[t];
+    const bool valid = p < T.count;
+    const int base = item_base[t], nit = item_base[t + 1] - base;
+    const long long chunk = (long long)cnt[kCntTcChunk];
+    const int j = T.piece;
+    const xint zero = xint_norm(0, 0, 0, 0, 0);
+    PointRec r;
+    r.zr = r.zi = 0.0;
+    if (valid) r = rec[T.start + p];
+    const int f = valid ? frexp_exp(fmax(fabs(r.zr), fabs(r.zi))) : 0;
+    const int per = (nit + kFinLanes - 1) / kFinLanes;
+    const int c0 = q * per, c1 = min(nit, c0 + per);
+    xint V = zero, zp = zero;
+    if (valid) {
+      xint Wc = zero;
+      if (nit > 1) {
+        Wc = xint_pow_z(r.zr, r.zi, kTB * chunk, f);
+        Wc.e += (long long)kTB * chunk * P.piece_beta[j];
+      }
+      for (int c = c1 - 1; c >= c0; --c) {
+        if (V.x || V.y) V = xint_mul(V, Wc);
+        V = xint_add(V, slots[(size_t)(base + c) * kTcPoints + p]);
+      }
+      if (c0 > 0 && c0 < nit && (V.x || V.y)) {  // times Wc^c0, c0 = q per
+        xint Wp = xint_norm((u128)1 << 126, 0, 0, 0, 0), b = Wc;
+        for (int e = c0; e > 0; e >>= 1) {
+          if (e & 1) Wp = xint_mul(Wp, b);
+          if (e > 1) b = xint_sqr(b);
+        }
+        V = xint_mul(V, Wp);
+      }
+      if (q == 1) {  // z^(kb + v), kb = k0 + 32 mlo
+        const long long kb = P.piece_k0[j] + kTB * T.mlo;
+        zp = xint_pow_z(r.zr, r.zi, kb + P.v, f);
+        zp.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (kb - P.piece_k0[j]);
+      }
+    }
+    // add the four parts (lanes 4p .. 4p + 3 of one warp)
+    for (int o = 1; o < kFinLanes; o <<= 1) {
+      const xint w = shfl_xint_tc(V, o);
+      V = xint_add(V, w);
+    }
+    zp = shfl_xint_tc(zp, 1);  // thread 0 gets thread 1's power
+    if (valid && q == 0) {
+      if (V.x || V.y) V = xint_mul(V, zp);
+      const fpe_xc64 o = xc64_from_xint(V);
+      out[r.orig] = o;
+      tc_write_diag(P, r, o, nterms, bits_lost);
     }
   }
-  const fpe_xc64 o = tc_output(P, j, P.piece_k0[j] + kTB * T.mlo, r, V);
-  out[r.orig] = o;
-  tc_write_diag(P, r, o, nterms, bits_lost);
 }
 
 // ---------------------------------------------------------------------------
@@ -1000,8 +1021,9 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
   }
   {
     ProfScope ps("k_tc_pre", st);
-    k_tc_pre<<<tm, kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, (TcPoint *)w.tc_points,
-                                       (TcTau *)w.tc_taus, (uint16_t *)w.tc_z);
+    k_tc_pre<<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(
+        P->dev, w.rec, (const TcTile *)w.tc_tiles, (TcPoint *)w.tc_points, (TcTau *)w.tc_taus, (uint16_t *)w.tc_z,
+        cnt);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core plan launch");
@@ -1022,7 +1044,7 @@ fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, 
   }
   {
     ProfScope ps("k_tc_finalize", st);
-    k_tc_finalize<<<tm, kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt,
+    k_tc_finalize<<<std::min(tm, tc_num_sms() * 4), kFinLanes * kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt,
                                              (const xint *)w.tc_slots, out, nterms, bits_lost);
   }
   cudaError_t e = cudaGetLastError();
