@@ -79,7 +79,7 @@ enum {
 };
 
 /*
- * fpe_precondition -- preconditioning of Alg. A_p (lines 2-4; §5.1).
+ * fpe_precondition -- preconditioning of Alg. A_p (§5.1).
  *
  * Computes the exact integer scales s(a_k) = 1 + floor(log2|a_k|) (eq. dsz),
  * the concave cover of k -> s(a_k) over the nonzero coefficients (def. EP),
@@ -104,7 +104,7 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
                             uint32_t flags, fpe_poly_t *out);
 
 /*
- * fpe_eval -- evaluation of Alg. A_p (lines 6-11; §5.2) at n points.
+ * fpe_eval -- evaluation of Alg. A_p (§5.2) at n points.
  *
  * For each point: lambda = log2|z| (eq. defLambda), k_lambda = argmax of
  * cover(k) + lambda*k by binary search on the cover's slopes (eq. defN),
@@ -255,8 +255,8 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
                               fpe_tuning *best);
 
 /*
- * Tensor-core window sums (the same Q_lambda(z) of Alg. A_p line 11,
- * eq. reducedQlambda, computed on another unit; the paper has no
+ * Tensor-core window sums (the same Q_lambda(z) of Alg. A_p, eq. reducedQlambda,
+ * computed on another unit; the paper has no
  * counterpart).  In the FP64 default mode (not FPE_FP32, not FPE_ACCURATE),
  * fpe_eval sums every window of at least min_window terms that lies inside
  * one of the polynomial's longest (up to four) coefficient pieces with an

@@ -110,7 +110,7 @@ def scale_of_int(n: int) -> int:
 
 
 def offset_T(p: int, d: int) -> int:
-    """T = p + s(d) + 3 (Alg. A_p, line 4; eq. threshold), d = degree.
+    """T = p + s(d) + 3 (Alg. A_p; eq. threshold), d = degree.
     For d = 0 (a constant) the window is always {0}; s(0) is taken as 0."""
     return p + (scale_of_int(d) if d >= 1 else 0) + 3
 
@@ -223,7 +223,7 @@ def cover_value(hk: np.ndarray, hs: np.ndarray, k: int) -> Fraction:
 
 
 # ----------------------------------------------------------------------------
-# good indices  (Alg. A_p line 4, eq. threshold)
+# good indices  (Alg. A_p, eq. threshold)
 # ----------------------------------------------------------------------------
 
 def good_mask(s: np.ndarray, hk: np.ndarray, hs: np.ndarray, T: int) -> np.ndarray:
@@ -251,7 +251,7 @@ def good_mask(s: np.ndarray, hk: np.ndarray, hs: np.ndarray, T: int) -> np.ndarr
 
 
 # ----------------------------------------------------------------------------
-# windows  (Alg. A_p lines 7-10; eq. defN, def. LRN)
+# windows  (Alg. A_p; eq. defN, def. LRN)
 # ----------------------------------------------------------------------------
 
 def log2_abs(zre: np.ndarray, zim: Optional[np.ndarray]) -> np.ndarray:
@@ -472,7 +472,7 @@ def num_threads() -> int:
 # ----------------------------------------------------------------------------
 
 class Preconditioned:
-    """Output of the preconditioning part of Algorithm A_p (lines 2-4)."""
+    """Output of the preconditioning part of Algorithm A_p (§5.1)."""
 
     def __init__(self, coef, p: int):
         self.coef = coef
@@ -493,7 +493,7 @@ def precondition(coef, p: int) -> Preconditioned:
 
 
 def fpe_eval(pre: Preconditioned, zre, zim=None, with_S: bool = False):
-    """Algorithm A_p evaluation (lines 6-11): returns (values, (k_lambda, N, l, r)).
+    """Algorithm A_p evaluation (§5.2): returns (values, (k_lambda, N, l, r)).
     At z = 0 the value is a_0 (§4.2: P(0) = a_0 is immediately available)."""
     lam = log2_abs(np.asarray(zre, dtype=np.float64), None if zim is None else np.asarray(zim, dtype=np.float64))
     kl, N, L, R = windows(pre.hk, pre.hs, pre.T, lam)

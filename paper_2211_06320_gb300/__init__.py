@@ -173,7 +173,7 @@ class Poly:
 
 
 def fpe_precondition(re, im=None, e2=None, p: int = 53, flags: int = 0) -> Poly:
-    """Preconditioning (Alg. A_p lines 2-4) of a_k = (re[k] + i im[k]) 2^e2[k]; host arrays."""
+    """Preconditioning (preconditioning part of Alg. A_p, §5.1) of a_k = (re[k] + i im[k]) 2^e2[k]; host arrays."""
     lib = _load()
     re = np.ascontiguousarray(re, dtype=np.float64)
     im = None if im is None else np.ascontiguousarray(im, dtype=np.float64)
@@ -198,7 +198,7 @@ def split_xc64(out):
 
 
 def fpe_eval(P: Poly, z_re, z_im=None, out=None, nterms=None, bits_lost=None, stream=None):
-    """Evaluation (Alg. A_p lines 6-11) at device points; returns the (n, 3) result tensor."""
+    """Evaluation (evaluation part of Alg. A_p, §5.2) at device points; returns the (n, 3) result tensor."""
     lib = _load()
     n = int(z_re.shape[0])
     if out is None:

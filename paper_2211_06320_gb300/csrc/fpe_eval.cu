@@ -1,4 +1,4 @@
-// Evaluation phase of Algorithm A_p (lines 6-11; §5.2) on the GPU.
+// Evaluation phase of Algorithm A_p (its evaluation part, §5.2) on the GPU.
 //
 // Stages, all asynchronous on the caller's stream, with grid sizes that depend
 // only on n (so the sequence can be captured in a CUDA graph):
@@ -38,7 +38,7 @@
 namespace fpe {
 
 // ---------------------------------------------------------------------------
-// location (Alg. A_p lines 7-10)
+// location (Alg. A_p: k_lambda, N, l, r; eq. defN, def. LRN)
 // ---------------------------------------------------------------------------
 
 struct Window {
@@ -257,7 +257,7 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
 }
 
 // ---------------------------------------------------------------------------
-// window sums (Alg. A_p line 11)
+// window sums (Alg. A_p: Q_lambda, eq. reducedQlambda)
 // ---------------------------------------------------------------------------
 
 // Horner over trimmed indices [lo, hi] on the rescaled coefficients b:

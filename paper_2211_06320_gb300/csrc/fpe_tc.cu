@@ -1,4 +1,4 @@
-// Window sums of Algorithm A_p (line 11: Q_lambda(z) = sum of a_k z^k over
+// Window sums of Algorithm A_p (Q_lambda(z) = sum of a_k z^k over
 // G_p ∩ [l, r], eq. reducedQlambda) on the tensor cores, for the long windows
 // of FP64 evaluations.
 //
@@ -12,27 +12,28 @@
 //     C_m = sum_i b_k w^i,  w = 2^beta z  (b_k = a_k 2^-rho(k) on the piece),
 //   and the window sum is sum_m C_m W^m with W = w^32.
 //
-//   Tilt.  The points of a tile (up to 128, bucketed by mu = log2|w|) share a
+//   Tilt.  The points of a tile (up to 64, bucketed by mu = log2|w|) share a
 //   real tilt tau = 2^c with c near their mu: A'_{m,i} = b_k tau^i and
 //   Z'_i = u^i with u = w / tau, so A' Z' = b_k w^i, |u| is close to 1 and the
 //   products are balanced (the largest |A'| times the largest |Z'| is within
 //   2^(62 |mu - c|) of the block's largest term).
 //
 //   Slices.  Each component of A' (per block) and of Z' (per point) is a
-//   70-bit fixed-point number relative to a power of two above its block's or
-//   point's largest component, cut into ten 7-bit slices q_0..q_9 (exact in
-//   bf16).  A slice product q q' < 2^14; a 64-long dot product of slices is an
-//   integer below 2^20, and the at most ten slice pairs with the same
-//   s + s' = t add up below 2^24: fp32 accumulation is exact.  Pairs with
-//   t <= 9 are kept (55 of 100); the dropped ones and the truncation leave an
-//   error below 2^-66 per product relative to the scales.
+//   69-bit fixed-point number relative to a power of two above its block's or
+//   point's largest component, written as ten balanced base-128 digits d_0..d_9
+//   (|d| <= 64, exact in bf16).  A digit product is at most 2^12 in
+//   magnitude, a 64-long dot product of digits at most 2^18, and the at most
+//   ten digit pairs with the same s + s' = t add up below 2^22: fp32
+//   accumulation is exact.  Pairs with t <= 9 are kept (55 of 100); the
+//   dropped ones and the truncation leave an error below 2^-66 per product
+//   relative to the scales.
 //
 //   Combination.  The ten integer accumulators of each (block, point) are
-//   joined into a 128-bit integer, and the blocks are combined by Horner's
-//   scheme in 128-bit fixed point (xint) on the integer pipe, where the order
-//   of summation does not matter for the error.
+//   joined into a 128-bit integer; the blocks of a work item are combined by
+//   Horner's scheme in 64-bit mantissas (xh) on the integer pipe, and the work
+//   items of a tile in 128-bit ones (xint).
 //
-// Error per window: below 2^-54 times S(z) for tiles with 31 |mu - c| <= 2,
+// Error per window: below 2^-53.5 times S(z) for tiles with 31 |mu - c| <= 2,
 // which the planner enforces (other tiles go back to the FP64 kernels).
 //
 // MMA layout (m16n8k16, A row-major 16 x 16, B column 16 x 8): the 16 rows of
@@ -72,7 +73,7 @@ struct xh {
 };
 
 __device__ __forceinline__ xh xh_norm(unsigned long long x, int sx, unsigned long long y, int sy, long long e) {
-  const unsigned long long m = x > y ? x : y;
+  const unsigned long long m = x | y;  // the same leading bit as max(x, y)
   xh r;
   if (m == 0) {
     r.x = r.y = 0;
@@ -91,12 +92,18 @@ __device__ __forceinline__ xh xh_norm(unsigned long long x, int sx, unsigned lon
 
 // top 64 bits of a 128-bit magnitude pair (value X 2^(e - 126) as in xint)
 __device__ __forceinline__ xh xh_from128(u128 X, int sx, u128 Y, int sy, long long e) {
-  const u128 m = X > Y ? X : Y;
+  const u128 m = X | Y;  // the same leading bit as max(X, Y)
   if (m == 0) return xh_norm(0, 0, 0, 0, 0);
-  const int sh = clz128(m);  // bring the top bit to 127
+  const int sh = clz128(m);  // bring the top bit to 127: the larger top half is then normalised
   X <<= sh;
   Y <<= sh;
-  return xh_norm((unsigned long long)(X >> 64), sx, (unsigned long long)(Y >> 64), sy, e - sh + 1);
+  xh r;
+  r.x = (unsigned long long)(X >> 64);
+  r.y = (unsigned long long)(Y >> 64);
+  r.sx = r.x ? sx : 0;
+  r.sy = r.y ? sy : 0;
+  r.e = e - sh + 1;
+  return r;
 }
 
 __device__ __forceinline__ xh xh_from_xint(const xint &v) { return xh_from128(v.x, v.sx, v.y, v.sy, v.e); }
@@ -189,43 +196,48 @@ __device__ __forceinline__ int zswz(int kappa, int p) {
   return kappa * kTcPoints + ((((p >> 3) ^ (kappa & 7)) << 3) | (p & 7));
 }
 
-// a 7-bit slice q (exact in bf16) with a sign, as bf16 bits
-__device__ __forceinline__ uint16_t q_bf16(uint32_t q, uint32_t neg) {
-  const float f = __uint_as_float(0x4B000000u | q) - 8388608.0f;  // q exactly
-  return (uint16_t)((__float_as_uint(f) >> 16) | (neg << 15));
-}
-
-// the ten slices of a 70-bit magnitude F (F < 2^70): q_s = bits [63 - 7s, 69 - 7s]
-__device__ __forceinline__ void slices70(u128 F, uint32_t (&q)[kSl]) {
-  const unsigned long long fh = (unsigned long long)(F >> 35), fl = (unsigned long long)F & ((1ull << 35) - 1);
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    q[s] = (uint32_t)(fh >> (28 - 7 * s)) & 127u;
-    q[s + 5] = (uint32_t)(fl >> (28 - 7 * s)) & 127u;
-  }
-}
-
-// signed digits d_0..d_9 of F < 2^69: F = sum_j d_j 128^(9 - j) with every
-// |d_j| <= 64 (a chunk c_j >= 64 becomes c_j - 128 and carries one into the
-// next chunk up; the top chunk is below 64, so it takes the last carry
-// without leaving [0, 64]).  Products of two digits stay within 2^12, and the
-// ten slice pairs of one accumulator over a 64-long dot product within
+// Balanced base-128 digits of F < 2^69: F = sum_j d_j 128^(9 - j) with d_j in
+// [-64, 63] for j > 0 and d_0 in [0, 64].  Adding B = sum_j 64 128^j makes
+// them plain chunks c_j = d_j + 64 of G = F + B (7 bits each; the top one,
+// everything above bit 63, at most 128).  Each chunk is returned as the bits
+// of the float 2^23 + c_j, from which one fused multiply-add by +-1 gives
+// +-d_j exactly (bf16_pair).  Products of two digits stay within 2^12, and
+// the ten slice pairs of one accumulator over a 64-long dot product within
 // 10 x 2^18 < 2^22: fp32 accumulation is exact with room to spare.
-__device__ __forceinline__ void sdigits70(u128 F, int (&d)[kSl]) {
-  uint32_t c[kSl];
-  slices70(F, c);
-  int carry = 0;
+__device__ __forceinline__ void bchunks70(u128 F, uint32_t (&x)[kSl]) {
+  const u128 G = F + (((u128)0x20 << 64) | 0x4081020408102040ull);
+  const unsigned long long lo = (unsigned long long)G, hi = (unsigned long long)(G >> 64);
+  x[0] = 0x4B000000u | (uint32_t)((hi << 1) | (lo >> 63));
 #pragma unroll
-  for (int j = kSl - 1; j >= 0; --j) {
-    const int x = (int)c[j] + carry;
-    carry = (j > 0 && x >= 64) ? 1 : 0;
-    d[j] = x - (carry << 7);
-  }
+  for (int j = 1; j < kSl; ++j) x[j] = 0x4B000000u | ((uint32_t)(lo >> (7 * (kSl - 1 - j))) & 127u);
 }
 
-// a signed digit (|d| <= 64, exact in bf16) times (-1)^neg, as bf16 bits
-__device__ __forceinline__ uint16_t d_bf16(int d, uint32_t neg) {
-  return q_bf16((uint32_t)(d < 0 ? -d : d), (uint32_t)(d < 0) ^ neg);
+// the multiplier and addend that turn a chunk's float 2^23 + c into
+// (-1)^neg (c - 64), exactly
+struct DigitSign {
+  float s, k;
+};
+__device__ __forceinline__ DigitSign digit_sign(uint32_t neg) {
+  DigitSign r;
+  r.s = neg ? -1.0f : 1.0f;
+  r.k = neg ? 8388672.0f : -8388672.0f;
+  return r;
+}
+
+// two signed digits as a pair of bf16 (a in the low half, i.e. at the lower
+// address): the digits are small integers, exact in bf16, so the bf16 is the
+// float's upper half
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t xa, DigitSign sa, uint32_t xb, DigitSign sb) {
+  const uint32_t a = __float_as_uint(fmaf(__uint_as_float(xa), sa.s, sa.k));
+  const uint32_t b = __float_as_uint(fmaf(__uint_as_float(xb), sb.s, sb.k));
+  return __byte_perm(a, b, 0x7632);
+}
+
+// a 128-bit value across lane ^ 1
+__device__ __forceinline__ u128 shfl_u128_x1(u128 v) {
+  const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, 1);
+  const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), 1);
+  return ((u128)hi << 64) | lo;
 }
 
 // X 2^-sr (sr may be negative), saturated below 2^70
@@ -262,18 +274,23 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// sum_t acc[t] 2^(7 (9 - t)) as a signed 128-bit integer (each acc[t] an
-// integer below 2^22 in magnitude held exactly in fp32, read back exactly by
-// adding 1.5 2^23: the integer lands in the low mantissa bits)
-__device__ __forceinline__ int f2i_exact(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
-
+// X = sum_t v_t 128^(9 - t), v_t = acc[t][c], as a 128-bit magnitude and a
+// sign.  Each v_t is an integer below 2^22 in magnitude held exactly in fp32;
+// adding 1.5 2^23 puts it in the low mantissa bits, so the float's bits are
+// w_t = v_t + 0x4B400000.  The pairs v_2j 128 + v_2j+1 (below 2^29.1) come
+// from the w's in wrap-around 32-bit arithmetic, and three 32 x 32 + 64-bit
+// products join them.
 __device__ __forceinline__ void join_acc(const float (&acc)[kSl][4], int c, u128 &mag, int &neg) {
-  long long hi = 0, lo = 0;
+  int pr[kSl / 2];
 #pragma unroll
-  for (int t = 0; t < 5; ++t) hi += (long long)f2i_exact(acc[t][c]) << (7 * (4 - t));
-#pragma unroll
-  for (int t = 5; t < 10; ++t) lo += (long long)f2i_exact(acc[t][c]) << (7 * (9 - t));
-  __int128 X = ((__int128)hi << 35) + (__int128)lo;
+  for (int j = 0; j < kSl / 2; ++j) {
+    const uint32_t wa = __float_as_uint(acc[2 * j][c] + 12582912.0f);
+    const uint32_t wb = __float_as_uint(acc[2 * j + 1][c] + 12582912.0f);
+    pr[j] = (int)(wa * 128u + wb - 129u * 0x4B400000u);
+  }
+  const long long lo = (long long)pr[2] * (1ll << 28) + (long long)pr[3] * (1ll << 14) + pr[4];
+  const long long hi = (long long)pr[0] * (1ll << 14) + pr[1];
+  const __int128 X = ((__int128)hi << 42) + (__int128)lo;
   neg = X < 0;
   mag = (u128)(neg ? -X : X);
 }
@@ -634,21 +651,27 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
       cur = xh_norm(1ull << 63, 0, 0, 0, 0);  // 1
     }
     // powers u^i in 64-bit mantissas: each product truncates at 2^-63, so u^31
-    // is within 2^-58 of its value relative to itself
-    uint16_t *zt = zglob + (size_t)t * (kZBytes / 2);
+    // is within 2^-58 of its value relative to itself.  Lane pairs (points
+    // p even, p + 1) share the stores: the even lane writes both points' real
+    // parts, the odd lane both imaginary parts, each as bf16 pairs.
+    const int odd = p & 1, pb = p & ~1;
+    uint32_t *zt = reinterpret_cast<uint32_t *>(zglob + (size_t)t * (kZBytes / 2));
     for (int i = 0; i < kTB; ++i) {
       if (i > 0 && valid) cur = xh_mul(cur, uh);
-      int dr[kSl], di[kSl];
       // x 2^(e - 63) 2^(70 - (eQ + 1)) = x 2^-sr: fixed point below 2^69 (components <= 2^(eQ - 1))
       const int sr = eQ + 1 - 7 - (int)cur.e;
-      sdigits70(valid ? shift_to70((u128)cur.x, sr) : (u128)0, dr);
-      sdigits70(valid ? shift_to70((u128)cur.y, sr) : (u128)0, di);
-      const int cre = zswz(i, p), cim = zswz(kTB + i, p);
-  #pragma unroll
-      for (int s = 0; s < kSl; ++s) {
-        zt[s * kTK * kTcPoints + cre] = d_bf16(dr[s], (uint32_t)cur.sx);
-        zt[s * kTK * kTcPoints + cim] = d_bf16(di[s], (uint32_t)cur.sy);
-      }
+      const u128 fr = valid ? shift_to70((u128)cur.x, sr) : (u128)0;
+      const u128 fi = valid ? shift_to70((u128)cur.y, sr) : (u128)0;
+      const u128 mine = odd ? fi : fr, recv = shfl_u128_x1(odd ? fr : fi);
+      const uint32_t nmine = (uint32_t)(odd ? cur.sy : cur.sx);
+      const uint32_t nrecv = __shfl_xor_sync(0xffffffffu, (uint32_t)(odd ? cur.sx : cur.sy), 1);
+      uint32_t xa[kSl], xb[kSl];  // point pb, point pb + 1
+      bchunks70(odd ? recv : mine, xa);
+      bchunks70(odd ? mine : recv, xb);
+      const DigitSign sa = digit_sign(odd ? nrecv : nmine), sb = digit_sign(odd ? nmine : nrecv);
+      const int c = zswz(odd ? kTB + i : i, pb) >> 1;
+#pragma unroll
+      for (int s = 0; s < kSl; ++s) zt[s * (kTK * kTcPoints / 2) + c] = bf16_pair(xa[s], sa, xb[s], sb);
     }
     TcPoint o;
     xint W = zero;
@@ -757,19 +780,31 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         prod(bi, pi, ei_);
         for (int o = 16; o >= 1; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
         const int eR = top == INT_MIN ? 0 : top + 2;  // every |component| < 2^(eR - 1): below 2^69 in F
-        int qr[kSl], qi[kSl];
-        sdigits70(pr ? shift_to70(pr, eR - 70 - er_) : (u128)0, qr);
-        sdigits70(pi ? shift_to70(pi, eR - 70 - ei_) : (u128)0, qi);
+        const u128 fr = pr ? shift_to70(pr, eR - 70 - er_) : (u128)0;
+        const u128 fi = pi ? shift_to70(pi, eR - 70 - ei_) : (u128)0;
         const uint32_t nr = br < 0.0, ni = bi < 0.0;
-        uint16_t *are = &S.aq[0][0][0] + wid * kTK, *aim = &S.aq[0][0][0] + (kSub + wid) * kTK;
-        const int c_lo = ((lane >> 3) ^ wid) << 3 | (lane & 7), c_hi = ((4 + (lane >> 3)) ^ wid) << 3 | (lane & 7);
+        // lane pairs (terms i even, i + 1) share the stores: the even lane
+        // takes both terms' real parts, the odd lane both imaginary parts
+        const int odd = lane & 1, ib = lane & ~1;
+        const u128 mine = odd ? fi : fr, recv = shfl_u128_x1(odd ? fr : fi);
+        const uint32_t nmine = odd ? ni : nr, nrecv = __shfl_xor_sync(0xffffffffu, odd ? nr : ni, 1);
+        uint32_t xa[kSl], xb[kSl];  // term ib, term ib + 1
+        bchunks70(odd ? recv : mine, xa);
+        bchunks70(odd ? mine : recv, xb);
+        const DigitSign sa = digit_sign(odd ? nrecv : nmine), sb = digit_sign(odd ? nmine : nrecv);
+        // out_re row (wid): ( A'_re | -A'_im ), out_im row (8 + wid): ( A'_im | A'_re ).
+        // Even lane: the A'_re pair at (re row, low half) and (im row, high
+        // half); odd lane: -A'_im at (re row, high half), A'_im at (im row, low half).
+        const int c_lo = ((ib >> 3) ^ wid) << 3 | (ib & 7), c_hi = ((4 + (ib >> 3)) ^ wid) << 3 | (ib & 7);
+        const int o_re = (wid * kTK + (odd ? c_hi : c_lo)) >> 1;
+        const int o_im = ((kSub + wid) * kTK + (odd ? c_lo : c_hi)) >> 1;
+        const uint32_t flip = odd ? 0x80008000u : 0u;
+        uint32_t *a32 = reinterpret_cast<uint32_t *>(&S.aq[0][0][0]);
 #pragma unroll
         for (int s = 0; s < kSl; ++s) {
-          // out_re row: ( A'_re | -A'_im ), out_im row: ( A'_im | A'_re )
-          are[s * 2 * kSub * kTK + c_lo] = d_bf16(qr[s], nr);
-          are[s * 2 * kSub * kTK + c_hi] = d_bf16(qi[s], ni ^ 1u);
-          aim[s * 2 * kSub * kTK + c_lo] = d_bf16(qi[s], ni);
-          aim[s * 2 * kSub * kTK + c_hi] = d_bf16(qr[s], nr);
+          const uint32_t w = bf16_pair(xa[s], sa, xb[s], sb);
+          a32[s * (kSub * kTK) + o_re] = w ^ flip;
+          a32[s * (kSub * kTK) + o_im] = w;
         }
         if (lane == 0) S.er[wid] = eR;
       }

@@ -1,4 +1,4 @@
-// Host preconditioning of Algorithm A_p (lines 2-4, §5.1): exact integer scales,
+// Host preconditioning of Algorithm A_p (its preconditioning part, §5.1): exact integer scales,
 // the concave cover of k -> s(a_k), the good set G_p, and the device layout of
 // the coefficients.  Runs once per polynomial; not on the evaluation path.
 #include <algorithm>
@@ -267,7 +267,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   P->v = v;
   P->complex_coef = cplx;
   const int64_t D = d - v;
-  // T = p + s(d) + 3 with s(d) the bit length of the degree (Alg. A_p line 4)
+  // T = p + s(d) + 3 with s(d) the bit length of the degree (Alg. A_p, eq. threshold)
   P->T = p + (d >= 1 ? bit_length(d) : 0) + 3;
   const int64_t T = P->T;
 
