@@ -261,12 +261,13 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
  * fpe_eval sums every window of at least min_window terms that lies inside
  * one of the polynomial's longest (up to four) coefficient pieces with an
  * integer cover slope on the bf16 tensor cores: coefficients and point
- * powers are cut into exact 7-bit slices whose products are added exactly,
- * and blocks of 32 terms are combined in 128-bit fixed point.  Points are
- * grouped 128 at a time by log2|z|; a group also sums the terms of its
- * neighbours' windows (all of them below the window threshold), and a group
- * whose |z| spread is too wide for one shared scaling goes back to the FP64
- * kernels.  The error stays below 2^-54 sum |a_k||z|^k.
+ * powers are cut into exact 7-bit digits whose products are added exactly,
+ * and blocks of 32 terms are combined in 64-bit (within a work item) and
+ * 128-bit (across work items) fixed point.  Points are grouped up to 64 at
+ * a time by log2|z|; a group also sums the terms of its neighbours' windows
+ * (all of them below the window threshold), and a group whose |z| spread is
+ * too wide for one shared scaling goes back to the FP64 kernels.  The error
+ * stays below 2^-53.5 sum |a_k||z|^k.
  *
  * fpe_set_tensor_path: min_window in {0} or [32, 2^30]; 0 turns the path
  *   off.  Default 384 (below a few hundred terms the FP64 kernels are
