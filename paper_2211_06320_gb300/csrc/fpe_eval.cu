@@ -171,7 +171,7 @@ template <bool CZ>
 __global__ void k_locate(DevPoly P, int n, const double *__restrict__ zre, const double *__restrict__ zim,
                          long long *__restrict__ lo_out, long long *__restrict__ hi_out,
                          long long *__restrict__ kl_out, double *__restrict__ N_out, uint32_t *__restrict__ key,
-                         uint32_t *__restrict__ hist, long long tc_min_window) {
+                         uint32_t *__restrict__ rank, uint32_t *__restrict__ hist, long long tc_min_window) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double zr = zre[p], zi = CZ ? zim[p] : 0.0;
@@ -183,7 +183,7 @@ __global__ void k_locate(DevPoly P, int n, const double *__restrict__ zre, const
   uint32_t k = bucket_of(w.lam, w.flags);
   if (tc_min_window > 0 && !w.flags) tc_bucket(P, w.lo, w.hi, w.lam, tc_min_window, k);
   key[p] = k;
-  atomicAdd(&hist[k], 1u);
+  rank[p] = atomicAdd(&hist[k], 1u);  // the point's place within its bin
 }
 
 // exclusive scan of the nbins-word histogram (a multiple of 1024) into
@@ -222,7 +222,7 @@ template <bool CZ>
 __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, const double *__restrict__ zim,
                           const long long *__restrict__ lo, const long long *__restrict__ hi,
                           const long long *__restrict__ kl, const double *__restrict__ N,
-                          const uint32_t *__restrict__ key, uint32_t *bins,
+                          const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank, uint32_t *bins,
                           PointRec *__restrict__ rec, int32_t *__restrict__ long_list,
                           int32_t *__restrict__ long_ngroups, int32_t *__restrict__ long_gbase,
                           int32_t *__restrict__ extra_owner, int32_t *__restrict__ extra_group, int extra_cap,
@@ -230,7 +230,7 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const uint32_t kp = key[p];
-  uint32_t pos = atomicAdd(&bins[nbins + kp], 1u);
+  const uint32_t pos = bins[nbins + kp] + rank[p];  // bin start (scanned) + place in the bin
   PointRec r;
   r.zr = zre[p];
   r.zi = CZ ? zim[p] : 0.0;
@@ -1201,9 +1201,9 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
   {
     ProfScope ps("k_locate", st);
     if (cz)
-      k_locate<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, tcw);
+      k_locate<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, tcw);
     else
-      k_locate<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, tcw);
+      k_locate<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, tcw);
   }
   {
     ProfScope ps("k_scan_bins", st);
@@ -1212,12 +1212,12 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
   {
     ProfScope ps("k_scatter", st);
     if (cz)
-      k_scatter<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+      k_scatter<true><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, w.rec,
                                           w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                           w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
                                           P->tune.group_span(), w.nbins);
     else
-      k_scatter<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+      k_scatter<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, w.rec,
                                            w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                            w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
                                            P->tune.group_span(), w.nbins);
@@ -1431,7 +1431,7 @@ constexpr size_t kNaHi = kNaLo + align256(kNoAllocMaxPoints * sizeof(long long))
 constexpr size_t kNaKl = kNaHi + align256(kNoAllocMaxPoints * sizeof(long long));
 constexpr size_t kNaN = kNaKl + align256(kNoAllocMaxPoints * sizeof(long long));
 constexpr size_t kNaKey = kNaN + align256(kNoAllocMaxPoints * sizeof(double));
-constexpr size_t kNaRec = kNaKey + align256(kNoAllocMaxPoints * sizeof(uint32_t));
+constexpr size_t kNaRec = kNaKey + align256(2 * kNoAllocMaxPoints * sizeof(uint32_t));  // keys, ranks
 constexpr size_t kNaLong = kNaRec + align256(kNoAllocMaxPoints * sizeof(PointRec));
 constexpr size_t kNaNg = kNaLong + align256(kNoAllocMaxPoints * sizeof(int32_t));
 constexpr size_t kNaGb = kNaNg + align256(kNoAllocMaxPoints * sizeof(int32_t));
@@ -1517,17 +1517,17 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
       s = cuda_fail(e, "cudaMemsetAsync");
     } else {
       if (cz)
-        k_locate<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, 0);
+        k_locate<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, 0);
       else
-        k_locate<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, 0);
+        k_locate<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, 0);
       k_scan_bins<<<1, 1024, 0, st>>>(w.bins, kNumBins);
       if (cz)
-        k_scatter<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+        k_scatter<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, w.rec,
                                             w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                             w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
                                             P->tune.group_span(), kNumBins);
       else
-        k_scatter<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.bins, w.rec,
+        k_scatter<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, w.rec,
                                              w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
                                              w.extra_group, (int)w.extra_cap, P->d_status, P->tune.long_window,
                                              P->tune.group_span(), kNumBins);

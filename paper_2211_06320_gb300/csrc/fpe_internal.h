@@ -158,7 +158,7 @@ struct Workspace {
   long long *lo = nullptr, *hi = nullptr;  // per point, caller order (untrimmed)
   long long *kl = nullptr;                 // per point, caller order (trimmed k_lambda)
   double *N = nullptr;
-  uint32_t *key = nullptr;
+  uint32_t *key = nullptr;       // per point, caller order: bucket key; at key + cap, its place in the bin
   PointRec *rec = nullptr;       // bucketed order
   int32_t *long_list = nullptr;     // bucketed positions of long-window points
   int32_t *long_ngroups = nullptr;  // warp groups per long-window point

@@ -170,10 +170,12 @@ struct TcPoint {
   int pad[3];
 };
 
-// Per tile: tau^i = tm[i] 2^te[i] for i < 32 (the tilt of A').
+// Per tile: tau^i = tm[i] 2^te[i] for i < 32 (the tilt of A'), 1 / tau and
+// tau^32 in 128-bit mantissas (for u = w / tau and W = u^32 tau^32).
 struct TcTau {
   unsigned long long tm[kTB];
   int te[kTB];
+  xint inv, tau32;
 };
 
 constexpr int kZBytes = kSl * kTcPoints * kTK * 2;  // one tile's Z' slices, as laid out in shared memory
@@ -349,18 +351,19 @@ struct TcGroup {
 };
 
 // the first bin boundary of piece r at or after position x (bins are
-// contiguous; after the scatter bins[nbins + b] is the end of bin b)
+// contiguous; bins[nbins + b] is the start of bin b, which the scatter
+// leaves in place: it places each point by its rank within the bin)
 __device__ __forceinline__ int tc_snap(const uint32_t *bins, int nbins, int r, int x, int s_end) {
   const int b0 = kNumBins + r * kTcBinsPerPiece;
   int a = 0, b = kTcBinsPerPiece;  // find the smallest i with start(b0 + i) >= x
   while (a < b) {
     const int m = (a + b) >> 1;
-    if ((int)bins[nbins + b0 + m - 1] >= x)
+    if ((int)bins[nbins + b0 + m] >= x)
       b = m;
     else
       a = m + 1;
   }
-  return a < kTcBinsPerPiece ? min((int)bins[nbins + b0 + a - 1], s_end) : s_end;
+  return a < kTcBinsPerPiece ? min((int)bins[nbins + b0 + a], s_end) : s_end;
 }
 
 // one warp per group: bounds, spread check, tilt, block range
@@ -592,7 +595,37 @@ __global__ void __launch_bounds__(256) k_tc_plan_c(const TcGroup *__restrict__ g
 }
 
 // ---------------------------------------------------------------------------
-// per tile: tau^i; per tile point (one thread each): u = w / tau, the Z'
+// per tile, one warp: tau = 2^c (as tmant 2^tf, tmant in [0.5, 1)), lane i
+// tau^i, lane 0 1 / tau, lane 1 tau^32 (all lanes at once)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tc_tau(const TcTile *__restrict__ tiles, TcTau *__restrict__ taus,
+                                                const uint32_t *cnt) {
+  const int ntiles = (int)cnt[kCntTcTiles], lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nw) {
+    const double tau = exp2(tiles[t].c);
+    const int tf = frexp_exp(tau);
+    const double tmant = scale2(tau, -tf);
+    xint ti = xint_norm((u128)1 << 126, 0, 0, 0, 0);
+    if (lane > 0) {
+      ti = xint_pow_unit(tmant, 0.0, lane);
+      ti.e += (long long)tf * lane;
+    }
+    taus[t].tm[lane] = (unsigned long long)(ti.x >> 63);  // in [2^63, 2^64)
+    taus[t].te[lane] = (int)(ti.e - 63);
+    if (lane == 0) {
+      xint inv = recip_xint(tmant, 0.0);
+      inv.e -= tf;
+      taus[t].inv = inv;
+    } else if (lane == 1) {
+      xint t32 = xint_pow_unit(tmant, 0.0, kTB);
+      t32.e += (long long)tf * kTB;
+      taus[t].tau32 = t32;
+    }
+  }
+}
+
+// per tile point (one thread each): u = w / tau, the Z'
 // slices of u^i (i < 32) written straight to global memory in the layout
 // k_tc_sum copies into shared memory (for each slice and term, the 64
 // points' values are one 128-B row, so a warp's stores are contiguous),
@@ -600,38 +633,11 @@ __global__ void __launch_bounds__(256) k_tc_plan_c(const TcGroup *__restrict__ g
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
                                                       const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
-                                                      TcTau *__restrict__ taus, uint16_t *__restrict__ zglob,
+                                                      const TcTau *__restrict__ taus, uint16_t *__restrict__ zglob,
                                                       const uint32_t *cnt) {
-  __shared__ xint s_inv, s_tau32;
-  __shared__ double s_tmant;
-  __shared__ int s_tf;
   const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const TcTile T = tiles[t];
-    __syncthreads();  // the previous tile's shared values are read
-    if (p == 0) {  // tau = tmant 2^tf, tmant in [0.5, 1); 1 / tau; tau^32
-      const double tau = exp2(T.c);
-      const int tf = frexp_exp(tau);
-      const double tmant = scale2(tau, -tf);
-      xint inv = recip_xint(tmant, 0.0);
-      inv.e -= tf;
-      xint t32 = xint_pow_unit(tmant, 0.0, kTB);
-      t32.e += (long long)tf * kTB;
-      s_inv = inv;
-      s_tau32 = t32;
-      s_tmant = tmant;
-      s_tf = tf;
-    }
-    __syncthreads();
-    if (p < kTB) {
-      xint ti = xint_norm((u128)1 << 126, 0, 0, 0, 0);
-      if (p > 0) {
-        ti = xint_pow_unit(s_tmant, 0.0, p);
-        ti.e += (long long)s_tf * p;
-      }
-      taus[t].tm[p] = (unsigned long long)(ti.x >> 63);  // in [2^63, 2^64)
-      taus[t].te[p] = (int)(ti.e - 63);
-    }
     const bool valid = p < T.count;
     const xint zero = xint_norm(0, 0, 0, 0, 0);
     xint u = zero;
@@ -639,7 +645,7 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
     int eQ = 1;
     if (valid) {
       const PointRec r = rec[T.start + p];
-      u = xint_mul(xint_from_dd2(r.zr, 0.0, r.zi, 0.0, P.piece_beta[T.piece]), s_inv);
+      u = xint_mul(xint_from_dd2(r.zr, 0.0, r.zi, 0.0, P.piece_beta[T.piece]), taus[t].inv);
       uh = xh_from_xint(u);
       // every |component of u^i| (i < 32) is at most |u|^31 <= 2^(eQ - 1); |u| is
       // near 1, so log2|u| in FP32 (error far below the 1e-3 / 31 margin) suffices:
@@ -679,7 +685,7 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
       // (W^8)^tau of the Horner must not inherit the 64-bit powers' error
       xint u32 = u;
       for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
-      W = xint_mul(u32, s_tau32);
+      W = xint_mul(u32, taus[t].tau32);
     }
     o.W[0] = W;
     for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
@@ -876,20 +882,26 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
 // Per tile point: the sum over the tile's items, item c starting c chunks of
 // blocks after the first, i.e. sum_c V_c (W^chunk)^c; then z^(kb + v)
-// 2^rho(kb) with kb the first block's index, and the point's output.  Four
-// threads per point: thread q takes a contiguous quarter of the items by
-// Horner in Wc = W^chunk and scales it by Wc^(its first item); thread 1 also
-// computes z^(kb + v); the four parts are added by shuffles.
-constexpr int kFinLanes = 4;
-__global__ void __launch_bounds__(kFinLanes * kTcPoints)
+// 2^rho(kb) with kb the first block's index, and the point's output.  Tiles
+// of at most kFinOneLaneItems items take one thread per point (L = 1: most
+// tiles have one item, and the power z^(kb + v) is the thread's whole work);
+// longer ones four (L = 4): thread q takes a contiguous quarter of the items
+// by Horner in Wc = W^chunk and scales it by Wc^(its first item), thread 1
+// also computes z^(kb + v), and the four parts are added by shuffles.  Each
+// launch skips the other's tiles.
+constexpr int kFinOneLaneItems = 4;
+template <int L>
+__global__ void __launch_bounds__(L * kTcPoints)
     k_tc_finalize(DevPoly P, const PointRec *__restrict__ rec, const TcTile *__restrict__ tiles,
                   const int32_t *__restrict__ item_base, const uint32_t *cnt, const xint *__restrict__ slots,
                   fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
-  const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x / kFinLanes, q = threadIdx.x % kFinLanes;
+  const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x / L, q = threadIdx.x % L;
+  constexpr int qpow = L > 1 ? 1 : 0;  // the thread that computes z^(kb + v)
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int base = item_base[t], nit = item_base[t + 1] - base;
+    if ((L == 1) != (nit <= kFinOneLaneItems)) continue;  // the other launch's tile
     const TcTile T = tiles[t];
     const bool valid = p < T.count;
-    const int base = item_base[t], nit = item_base[t + 1] - base;
     const long long chunk = (long long)cnt[kCntTcChunk];
     const int j = T.piece;
     const xint zero = xint_norm(0, 0, 0, 0, 0);
@@ -897,7 +909,7 @@ __global__ void __launch_bounds__(kFinLanes * kTcPoints)
     r.zr = r.zi = 0.0;
     if (valid) r = rec[T.start + p];
     const int f = valid ? frexp_exp(fmax(fabs(r.zr), fabs(r.zi))) : 0;
-    const int per = (nit + kFinLanes - 1) / kFinLanes;
+    const int per = (nit + L - 1) / L;
     const int c0 = q * per, c1 = min(nit, c0 + per);
     xint V = zero, zp = zero;
     if (valid) {
@@ -918,18 +930,19 @@ __global__ void __launch_bounds__(kFinLanes * kTcPoints)
         }
         V = xint_mul(V, Wp);
       }
-      if (q == 1) {  // z^(kb + v), kb = k0 + 32 mlo
+      if (q == qpow) {  // z^(kb + v), kb = k0 + 32 mlo
         const long long kb = P.piece_k0[j] + kTB * T.mlo;
         zp = xint_pow_z(r.zr, r.zi, kb + P.v, f);
         zp.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (kb - P.piece_k0[j]);
       }
     }
-    // add the four parts (lanes 4p .. 4p + 3 of one warp)
-    for (int o = 1; o < kFinLanes; o <<= 1) {
-      const xint w = shfl_xint_tc(V, o);
-      V = xint_add(V, w);
+    if (L > 1) {  // add the L parts (lanes L p .. L p + L - 1 of one warp)
+      for (int o = 1; o < L; o <<= 1) {
+        const xint w = shfl_xint_tc(V, o);
+        V = xint_add(V, w);
+      }
+      zp = shfl_xint_tc(zp, qpow);  // thread 0 gets thread 1's power
     }
-    zp = shfl_xint_tc(zp, 1);  // thread 0 gets thread 1's power
     if (valid && q == 0) {
       if (V.x || V.y) V = xint_mul(V, zp);
       const fpe_xc64 o = xc64_from_xint(V);
@@ -1056,9 +1069,11 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
   }
   {
     ProfScope ps("k_tc_pre", st);
-    k_tc_pre<<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(
-        P->dev, w.rec, (const TcTile *)w.tc_tiles, (TcPoint *)w.tc_points, (TcTau *)w.tc_taus, (uint16_t *)w.tc_z,
-        cnt);
+    k_tc_tau<<<std::min((tm + 7) / 8, tc_num_sms() * 8), 256, 0, st>>>((const TcTile *)w.tc_tiles,
+                                                                       (TcTau *)w.tc_taus, cnt);
+    k_tc_pre<<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles,
+                                                                    (TcPoint *)w.tc_points,
+                                                                    (const TcTau *)w.tc_taus, (uint16_t *)w.tc_z, cnt);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core plan launch");
@@ -1079,8 +1094,12 @@ fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, 
   }
   {
     ProfScope ps("k_tc_finalize", st);
-    k_tc_finalize<<<std::min(tm, tc_num_sms() * 4), kFinLanes * kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt,
-                                             (const xint *)w.tc_slots, out, nterms, bits_lost);
+    k_tc_finalize<1><<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(
+        P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt, (const xint *)w.tc_slots, out, nterms,
+        bits_lost);
+    k_tc_finalize<4><<<std::min(tm, tc_num_sms() * 4), 4 * kTcPoints, 0, st>>>(
+        P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt, (const xint *)w.tc_slots, out, nterms,
+        bits_lost);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core sum launch");

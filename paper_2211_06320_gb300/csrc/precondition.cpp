@@ -172,7 +172,7 @@ fpe_status alloc_workspace(Workspace &w, int64_t n) {
   w.extra_cap = 0;
   const size_t xval = 40;  // extended double-double value
   const size_t sizes[] = {cap * sizeof(long long), cap * sizeof(long long), cap * sizeof(long long),
-                          cap * sizeof(double),    cap * sizeof(uint32_t),  cap * sizeof(PointRec),
+                          cap * sizeof(double),    2 * cap * sizeof(uint32_t), cap * sizeof(PointRec),
                           cap * sizeof(int32_t),   cap * sizeof(int32_t),   cap * sizeof(int32_t),
                           xcap * sizeof(int32_t),  xcap * sizeof(int32_t),  (cap + xcap) * xval,
                           (cap + xcap) * xval};
