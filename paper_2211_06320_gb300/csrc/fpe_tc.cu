@@ -880,23 +880,40 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   }
 }
 
+// b^n (n >= 1) by binary powering
+__device__ __forceinline__ xint xint_pow_x(xint b, long long n) {
+  xint r = b;
+  bool have = false;
+  for (; n > 0; n >>= 1) {
+    if (n & 1) {
+      r = have ? xint_mul(r, b) : b;
+      have = true;
+    }
+    if (n > 1) b = xint_sqr(b);
+  }
+  return r;
+}
+
 // Per tile point: the sum over the tile's items, item c starting c chunks of
 // blocks after the first, i.e. sum_c V_c (W^chunk)^c; then z^(kb + v)
-// 2^rho(kb) with kb the first block's index, and the point's output.  Tiles
-// of at most kFinOneLaneItems items take one thread per point (L = 1: most
-// tiles have one item, and the power z^(kb + v) is the thread's whole work);
-// longer ones four (L = 4): thread q takes a contiguous quarter of the items
-// by Horner in Wc = W^chunk and scales it by Wc^(its first item), thread 1
-// also computes z^(kb + v), and the four parts are added by shuffles.  Each
-// launch skips the other's tiles.
+// 2^rho(kb) with kb the first block's index, and the point's output.
+// W^chunk = (W^8)^(chunk / 8) from the powers k_tc_pre stored.  Tiles of at
+// most kFinOneLaneItems items take one thread per point (L = 1: most tiles
+// have one item, and the power z^(kb + v) is the thread's main work);
+// longer ones eight (L = 8): threads q < 7 take a contiguous seventh of the
+// items by Horner in W^chunk and scale it by (W^chunk)^(its first item),
+// thread 7 computes z^(kb + v) meanwhile, and the parts are added by
+// shuffles.  Each launch skips the other's tiles.
 constexpr int kFinOneLaneItems = 4;
 template <int L>
 __global__ void __launch_bounds__(L * kTcPoints)
     k_tc_finalize(DevPoly P, const PointRec *__restrict__ rec, const TcTile *__restrict__ tiles,
-                  const int32_t *__restrict__ item_base, const uint32_t *cnt, const xint *__restrict__ slots,
-                  fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
+                  const TcPoint *__restrict__ pts, const int32_t *__restrict__ item_base, const uint32_t *cnt,
+                  const xint *__restrict__ slots, fpe_xc64 *__restrict__ out, int32_t *nterms,
+                  int32_t *bits_lost) {
   const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x / L, q = threadIdx.x % L;
-  constexpr int qpow = L > 1 ? 1 : 0;  // the thread that computes z^(kb + v)
+  constexpr int qpow = L - 1;            // the thread that computes z^(kb + v)
+  constexpr int nh = L > 1 ? L - 1 : 1;  // threads that take items
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int base = item_base[t], nit = item_base[t + 1] - base;
     if ((L == 1) != (nit <= kFinOneLaneItems)) continue;  // the other launch's tile
@@ -909,26 +926,25 @@ __global__ void __launch_bounds__(L * kTcPoints)
     r.zr = r.zi = 0.0;
     if (valid) r = rec[T.start + p];
     const int f = valid ? frexp_exp(fmax(fabs(r.zr), fabs(r.zi))) : 0;
-    const int per = (nit + L - 1) / L;
-    const int c0 = q * per, c1 = min(nit, c0 + per);
+    const int per = (nit + nh - 1) / nh;
+    const int c0 = q * per, c1 = q < nh ? min(nit, c0 + per) : c0;
     xint V = zero, zp = zero;
     if (valid) {
-      xint Wc = zero;
-      if (nit > 1) {
-        Wc = xint_pow_z(r.zr, r.zi, kTB * chunk, f);
-        Wc.e += (long long)kTB * chunk * P.piece_beta[j];
-      }
-      for (int c = c1 - 1; c >= c0; --c) {
-        if (V.x || V.y) V = xint_mul(V, Wc);
-        V = xint_add(V, slots[(size_t)(base + c) * kTcPoints + p]);
-      }
-      if (c0 > 0 && c0 < nit && (V.x || V.y)) {  // times Wc^c0, c0 = q per
-        xint Wp = xint_norm((u128)1 << 126, 0, 0, 0, 0), b = Wc;
-        for (int e = c0; e > 0; e >>= 1) {
-          if (e & 1) Wp = xint_mul(Wp, b);
-          if (e > 1) b = xint_sqr(b);
+      if (c0 < c1) {
+        xint Wc = zero;
+        if (nit > 1) {  // W^chunk = w^(32 chunk)
+          if (chunk % 8 == 0) {
+            Wc = xint_pow_x(pts[(size_t)t * kTcPoints + p].W[3], chunk / 8);
+          } else {
+            Wc = xint_pow_z(r.zr, r.zi, kTB * chunk, f);
+            Wc.e += (long long)kTB * chunk * P.piece_beta[j];
+          }
         }
-        V = xint_mul(V, Wp);
+        for (int c = c1 - 1; c >= c0; --c) {
+          if (V.x || V.y) V = xint_mul(V, Wc);
+          V = xint_add(V, slots[(size_t)(base + c) * kTcPoints + p]);
+        }
+        if (c0 > 0 && (V.x || V.y)) V = xint_mul(V, xint_pow_x(Wc, c0));  // times Wc^c0
       }
       if (q == qpow) {  // z^(kb + v), kb = k0 + 32 mlo
         const long long kb = P.piece_k0[j] + kTB * T.mlo;
@@ -941,7 +957,7 @@ __global__ void __launch_bounds__(L * kTcPoints)
         const xint w = shfl_xint_tc(V, o);
         V = xint_add(V, w);
       }
-      zp = shfl_xint_tc(zp, qpow);  // thread 0 gets thread 1's power
+      zp = shfl_xint_tc(zp, qpow);  // thread 0 gets thread qpow's power
     }
     if (valid && q == 0) {
       if (V.x || V.y) V = xint_mul(V, zp);
@@ -1094,12 +1110,12 @@ fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, 
   }
   {
     ProfScope ps("k_tc_finalize", st);
+    k_tc_finalize<8><<<std::min(tm, tc_num_sms() * 2), 8 * kTcPoints, 0, st>>>(
+        P->dev, w.rec, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, w.tc_item_base, cnt,
+        (const xint *)w.tc_slots, out, nterms, bits_lost);
     k_tc_finalize<1><<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(
-        P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt, (const xint *)w.tc_slots, out, nterms,
-        bits_lost);
-    k_tc_finalize<4><<<std::min(tm, tc_num_sms() * 4), 4 * kTcPoints, 0, st>>>(
-        P->dev, w.rec, (const TcTile *)w.tc_tiles, w.tc_item_base, cnt, (const xint *)w.tc_slots, out, nterms,
-        bits_lost);
+        P->dev, w.rec, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, w.tc_item_base, cnt,
+        (const xint *)w.tc_slots, out, nterms, bits_lost);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core sum launch");
