@@ -73,7 +73,7 @@ struct Tuning {
 
 // Tensor-core window sums (fpe_tc.cu).  Windows of at least tc_min_window
 // terms that lie inside one long merged piece (an integer cover slope) are
-// summed as exact integer products of 7-bit slices on the bf16 tensor cores.
+// summed as exact integer products of 7-bit digits on the bf16 tensor cores.
 // Their points are bucketed separately: kTcBinsPerPiece bins per such piece
 // (at most kTcMaxPieces per polynomial), on a logarithmic scale of
 // mu = log2|z| + beta, so consecutive points have nearly equal windows.

@@ -770,7 +770,8 @@ __global__ void __launch_bounds__(L * kTcPoints)
     if (valid) {
       if (c0 < c1) {
         xint Wc = zero;
-        if (nit > 1) {  // W^chunk = w^(32 chunk)
+        if (nit > 1) {  // W^chunk = w^(32 chunk); k_tc_plan_b makes chunk a multiple of kSub = 8,
+                        // the power of z below only guards that invariant
           if (chunk % 8 == 0) {
             Wc = xint_pow_x(pts[(size_t)t * kTcPoints + p].W[3], chunk / 8);
           } else {
