@@ -385,10 +385,13 @@ const char *fpe_last_error(void);
 
 /*
  * Kernel timing (measurement support, no counterpart in the paper).  When
- * enabled, every kernel launch of this library records CUDA events around
- * itself on its launching stream; fpe_profile_read() synchronises with the
- * events and returns, for kernels whose name contains `name`, the total
- * device time in milliseconds and the number of launches since the last reset.
+ * enabled, every kernel launch of this library (or a short run of launches
+ * of one stage under one name: k_tc_plan = k_tc_plan_a, _b, _c; k_tc_pre =
+ * k_tc_tau, k_tc_pre; k_tc_finalize = its two launches) records CUDA events
+ * around itself on its launching stream; fpe_profile_read() synchronises
+ * with the events and returns, for names that contain `name`, the total
+ * device time in milliseconds and the number of kernel launches since the
+ * last reset.
  */
 void fpe_profile_enable(int on);
 void fpe_profile_reset(void);

@@ -18,13 +18,14 @@ namespace {
 struct ProfRec {
   std::string name;
   cudaEvent_t e0, e1;
+  int kernels;
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
 }  // namespace
 
-ProfScope::ProfScope(const char *n, cudaStream_t s) : name(n), st(s) {
+ProfScope::ProfScope(const char *n, cudaStream_t s, int k) : name(n), st(s), kernels(k) {
   if (!g_prof_on) return;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -34,7 +35,7 @@ ProfScope::~ProfScope() {
   if (!e0) return;
   cudaEventRecord(e1, st);
   std::lock_guard<std::mutex> g(g_prof_mu);
-  g_prof.push_back({name, e0, e1});
+  g_prof.push_back({name, e0, e1, kernels});
 }
 
 static fpe_status check_eval_args(fpe_poly_t P, const double *z_re, int64_t n, const void *out) {
@@ -620,7 +621,7 @@ fpe_status fpe_profile_read(const char *name, double *total_ms, int64_t *launche
     float ms = 0.f;
     cudaEventElapsedTime(&ms, r.e0, r.e1);
     tot += ms;
-    ++cnt;
+    cnt += r.kernels;
   }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = cnt;

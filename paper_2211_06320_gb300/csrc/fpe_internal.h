@@ -269,11 +269,12 @@ fpe_status launch_horner(fpe_poly_s *P, const double *z_re, const double *z_im, 
                          int compensated, cudaStream_t st);
 
 // kernel timing (api.cu)
-struct ProfScope {
+struct ProfScope {  // events around `kernels` consecutive kernel launches on st
   const char *name;
   cudaStream_t st;
+  int kernels;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  ProfScope(const char *name, cudaStream_t st);
+  ProfScope(const char *name, cudaStream_t st, int kernels = 1);
   ~ProfScope();
 };
 }  // namespace fpe

@@ -911,7 +911,7 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
   uint32_t *cnt = w.bins + 2 * w.nbins;
   const int tm = (int)tc_tiles_max(n), gm = (int)tc_groups_max(n);
   {
-    ProfScope ps("k_tc_plan", st);
+    ProfScope ps("k_tc_plan", st, 3);  // k_tc_plan_a, _b, _c
     TcPlanAcc *acc = (TcPlanAcc *)w.tc_plan;
     int32_t *g_nt = (int32_t *)(acc + 1), *g_tile0 = g_nt + gm, *g_item0 = g_tile0 + gm;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(TcPlanAcc), st);
@@ -923,7 +923,7 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
                                                   (TcTile *)w.tc_tiles, tm, w.tc_item_base, w.tc_item_tile);
   }
   {
-    ProfScope ps("k_tc_pre", st);
+    ProfScope ps("k_tc_pre", st, 2);  // k_tc_tau, k_tc_pre
     k_tc_tau<<<std::min((tm + 7) / 8, tc_num_sms() * 8), 256, 0, st>>>((const TcTile *)w.tc_tiles,
                                                                        (TcTau *)w.tc_taus, cnt);
     k_tc_pre<<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles,
@@ -948,7 +948,7 @@ fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, 
         (const uint4 *)w.tc_z, w.tc_item_base, w.tc_item_tile, cnt, (xint *)w.tc_slots);
   }
   {
-    ProfScope ps("k_tc_finalize", st);
+    ProfScope ps("k_tc_finalize", st, 2);  // eight- and one-thread launches
     k_tc_finalize<8><<<std::min(tm, tc_num_sms() * 2), 8 * kTcPoints, 0, st>>>(
         P->dev, w.rec, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, w.tc_item_base, cnt,
         (const xint *)w.tc_slots, out, nterms, bits_lost);
