@@ -32,7 +32,7 @@ the paper's notation:
                         (eq. reducedQlambda) in extended double-double.
 * ``fpe_eval``       -- Algorithm A_p end to end: windows, then window_sum.
 
-Readings where the paper is silent (also listed in the design doc):
+Readings where the paper is silent:
   p counts significand bits (53 for FP64, 24 for FP32); T = p + s(d) + 3 with
   d the index of the last nonzero coefficient; the cover is taken over the
   nonzero coefficients only, on [v, d] with v the first nonzero index; its
