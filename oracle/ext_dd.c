@@ -226,9 +226,11 @@ static void window_abs_sum(int64_t lo, int64_t hi, double az, const double *are,
   int fz;
   double mz = frexp(az, &fz);
   for (int64_t k = hi; k >= lo; --k) {
-    if (sm != 0.0) {
-      sm *= mz;
-      se += fz;
+    if (sm != 0.0) { /* s <- s |z|, renormalised at once: a run of skipped terms must not
+                        let the mantissa drift toward the subnormal range */
+      int f;
+      sm = frexp(sm * mz, &f);
+      se += fz + f;
     }
     if (good && !good[k]) continue;
     double ar = are[k] + (are_lo ? are_lo[k] : 0.0);
@@ -243,7 +245,7 @@ static void window_abs_sum(int64_t lo, int64_t hi, double az, const double *are,
       se = ea;
     } else {
       int64_t sh = ea - se;
-      if (sh > 1000) {
+      if (sh > 1000) { /* the sum so far is below 2^-999 of this term */
         sm = ma;
         se = ea;
       } else if (sh >= -1100) {
