@@ -145,7 +145,7 @@ fpe_status fpe_eval(fpe_poly_t P, const double *z_re, const double *z_im, int64_
  * and the device synchronisation it implies, a host program that gives the
  * library only the buffers it owns.  fpe_eval allocates its per-call scratch
  * on the handle; this call instead uses one built-in scratch array of
- * 9,036,032 bytes (8.6 MiB) in the library's device memory, which every GPU
+ * 9,429,248 bytes (about 9.0 MiB) in the library's device memory, which every GPU
  * that loads the library holds until the process exits.
  *
  *   Arguments and results as fpe_eval (device pointers, async on cuda_stream).

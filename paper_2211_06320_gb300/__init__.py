@@ -145,6 +145,47 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _points(z_re, z_im) -> int:
+    """Check the device points before any pointer reaches a kernel: float64,
+    one-dimensional, z_im (if given) of the same length and on the same device.
+    Returns n.  The kernels read n entries of each array, so a shorter or
+    narrower array would be read out of bounds."""
+    import torch
+    if not isinstance(z_re, torch.Tensor) or z_re.dtype != torch.float64 or z_re.dim() != 1:
+        raise ValueError("z_re must be a one-dimensional float64 CUDA tensor")
+    if z_im is not None:
+        if not isinstance(z_im, torch.Tensor) or z_im.dtype != torch.float64 or z_im.dim() != 1:
+            raise ValueError("z_im must be None or a one-dimensional float64 CUDA tensor")
+        if z_im.shape[0] != z_re.shape[0] or z_im.device != z_re.device:
+            raise ValueError("z_im must have z_re's length and device")
+    return int(z_re.shape[0])
+
+
+def _check_out(out, n: int, device):
+    """An (n, 3) float64 fpe_xc64 array on the points' device (the kernels write n rows)."""
+    import torch
+    if (not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or tuple(out.shape) != (n, 3)
+            or out.device != device):
+        raise ValueError(f"out must be an ({n}, 3) float64 tensor on {device}")
+
+
+def _check_vec(t, n: int, device, dtype, name: str):
+    """A per-point (or per-coefficient) array of n entries of dtype on device, or None."""
+    if t is None:
+        return
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or t.numel() != n or t.device != device:
+        raise ValueError(f"{name} must be a {dtype} tensor of {n} entries on {device}")
+
+
+def _check_poly_device(P, device):
+    """The handle's arrays live on the device it was preconditioned on."""
+    if device.type != "cuda":
+        raise ValueError("expected CUDA tensors")
+    if P.device is not None and device.index is not None and device.index != P.device:
+        raise ValueError(f"tensors are on {device}, the polynomial on cuda:{P.device}")
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -155,9 +196,10 @@ def _stream(stream):
 class Poly:
     """A preconditioned polynomial (owns an fpe_poly_t handle)."""
 
-    def __init__(self, handle: int, n_coef: int):
+    def __init__(self, handle: int, n_coef: int, device=None):
         self._h = ctypes.c_void_p(handle)
         self.n_coef = n_coef
+        self.device = device  # CUDA ordinal the handle's device arrays live on
 
     @property
     def handle(self):
@@ -181,7 +223,14 @@ def fpe_precondition(re, im=None, e2=None, p: int = 53, flags: int = 0) -> Poly:
     h = ctypes.c_void_p()
     _check(lib.fpe_precondition(_np_ptr(re), _np_ptr(im), _np_ptr(e2), re.shape[0], int(p), int(flags),
                                 ctypes.byref(h)), "fpe_precondition")
-    return Poly(h.value, re.shape[0])
+    dev = None
+    if not (int(flags) & FPE_HOST_ONLY):
+        try:
+            import torch
+            dev = torch.cuda.current_device()
+        except Exception:  # the handle was built, so a device was current; torch just cannot say which
+            dev = None
+    return Poly(h.value, re.shape[0], dev)
 
 
 def empty_out(n: int, device=None):
@@ -197,10 +246,21 @@ def split_xc64(out):
     return out[:, 0], out[:, 1], out[:, 2].contiguous().view(torch.int64)
 
 
+def _eval_args(P, z_re, z_im, out=None, nterms=None, bits_lost=None) -> int:
+    import torch
+    n = _points(z_re, z_im)
+    _check_poly_device(P, z_re.device)
+    if out is not None:
+        _check_out(out, n, z_re.device)
+    _check_vec(nterms, n, z_re.device, torch.int32, "nterms")
+    _check_vec(bits_lost, n, z_re.device, torch.int32, "bits_lost")
+    return n
+
+
 def fpe_eval(P: Poly, z_re, z_im=None, out=None, nterms=None, bits_lost=None, stream=None):
     """Evaluation (evaluation part of Alg. A_p, §5.2) at device points; returns the (n, 3) result tensor."""
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im, out, nterms, bits_lost)
     if out is None:
         out = empty_out(n, z_re.device)
     _check(lib.fpe_eval(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _dptr(nterms), _dptr(bits_lost),
@@ -231,7 +291,7 @@ def host_eval_raw(P: Poly, z_re_ptr: int, z_im_ptr: Optional[int], n: int, out_p
 
 def fpe_eval_deriv(P: Poly, z_re, z_im=None, out=None, stream=None):
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im, out)
     if out is None:
         out = empty_out(n, z_re.device)
     _check(lib.fpe_eval_deriv(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _stream(stream)), "fpe_eval_deriv")
@@ -244,6 +304,10 @@ def fpe_eval_batch(polys: Sequence[Poly], pt_offsets, z_re, z_im=None, out=None,
     hs = (ctypes.c_void_p * npoly)(*[p.handle.value for p in polys])
     offs = np.ascontiguousarray(pt_offsets, dtype=np.int64)
     n = int(offs[-1]) if npoly else 0
+    if _points(z_re, z_im) != n:
+        raise ValueError(f"the points must number pt_offsets[-1] = {n}")
+    if out is not None:
+        _check_out(out, n, z_re.device)
     if out is None:
         out = empty_out(n, z_re.device)
     _check(lib.fpe_eval_batch(hs, npoly, _np_ptr(offs), _dptr(z_re), _dptr(z_im), _dptr(out), _stream(stream)),
@@ -254,7 +318,7 @@ def fpe_eval_batch(polys: Sequence[Poly], pt_offsets, z_re, z_im=None, out=None,
 def fpe_horner(P: Poly, z_re, z_im=None, compensated: bool = False, out=None, stream=None):
     """GPU Horner over all d+1 terms (plain or compensated)."""
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im, out)
     if out is None:
         out = empty_out(n, z_re.device)
     _check(lib.fpe_horner(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), int(bool(compensated)),
@@ -290,9 +354,10 @@ def fpe_get_good(P: Poly):
 def fpe_get_windows(P: Poly, n: int, stream=None):
     import torch
     lib = _load()
-    l = torch.empty(n, dtype=torch.int64, device="cuda")
-    r = torch.empty(n, dtype=torch.int64, device="cuda")
-    N = torch.empty(n, dtype=torch.float64, device="cuda")
+    dev = torch.device("cuda", P.device) if P.device is not None else torch.device("cuda")
+    l = torch.empty(n, dtype=torch.int64, device=dev)
+    r = torch.empty(n, dtype=torch.int64, device=dev)
+    N = torch.empty(n, dtype=torch.float64, device=dev)
     _check(lib.fpe_get_windows(P.handle, n, _dptr(l), _dptr(r), _dptr(N), _stream(stream)), "fpe_get_windows")
     return l, r, N
 
@@ -336,7 +401,7 @@ def fpe_eval_noalloc(P: Poly, z_re, z_im=None, out=None, nterms=None, bits_lost=
     """fpe_eval without any device allocation (at most NOALLOC_MAX_POINTS points;
     calls share one built-in scratch array and must not overlap on the GPU)."""
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im, out, nterms, bits_lost)
     if out is None:
         out = empty_out(n, z_re.device)
     _check(lib.fpe_eval_noalloc(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(out), _dptr(nterms),
@@ -374,7 +439,13 @@ def fpe_batch_create(polys: Sequence[Poly], pt_offsets) -> Batch:
 
 
 def fpe_batch_eval(B: Batch, z_re, z_im=None, out=None, nterms=None, stream=None):
+    import torch
     lib = _load()
+    if _points(z_re, z_im) != B.n:
+        raise ValueError(f"the batch has {B.n} points")
+    if out is not None:
+        _check_out(out, B.n, z_re.device)
+    _check_vec(nterms, B.n, z_re.device, torch.int32, "nterms")
     if out is None:
         out = empty_out(B.n, z_re.device)
     _check(lib.fpe_batch_eval(B._h, _dptr(z_re), _dptr(z_im), _dptr(out), _dptr(nterms), _stream(stream)),
@@ -429,7 +500,8 @@ def fpe_autotune(P: Poly, z_re, z_im=None, stream=None) -> dict:
     """Time fpe_eval over the tuning grid on these device points; the fastest
     setting stays in the handle and is returned."""
     t = Tuning()
-    _check(_load().fpe_autotune(P.handle, _dptr(z_re), _dptr(z_im), int(z_re.shape[0]), _stream(stream),
+    n = _eval_args(P, z_re, z_im)
+    _check(_load().fpe_autotune(P.handle, _dptr(z_re), _dptr(z_im), n, _stream(stream),
                                 ctypes.byref(t)), "fpe_autotune")
     return t.as_dict()
 
@@ -441,6 +513,8 @@ def fpe_batch_set_tuning(B: Batch, long_window: int, lane_chunk: int):
 
 def fpe_batch_autotune(B: Batch, z_re, z_im=None, stream=None) -> dict:
     t = Tuning()
+    if _points(z_re, z_im) != B.n:
+        raise ValueError(f"the batch has {B.n} points")
     _check(_load().fpe_batch_autotune(B._h, _dptr(z_re), _dptr(z_im), _stream(stream), ctypes.byref(t)),
            "fpe_batch_autotune")
     return t.as_dict()
@@ -450,7 +524,9 @@ def fpe_newton(P: Poly, z_re, z_im=None, inc=None, z_next_re=None, z_next_im=Non
     """One Newton step: returns (inc as (n, 3) fpe_xc64, z_next_re, z_next_im)."""
     import torch
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im, inc)
+    _check_vec(z_next_re, n, z_re.device, torch.float64, "z_next_re")
+    _check_vec(z_next_im, n, z_re.device, torch.float64, "z_next_im")
     if inc is None:
         inc = empty_out(n, z_re.device)
     if z_next_re is None:
@@ -465,7 +541,11 @@ def fpe_newton(P: Poly, z_re, z_im=None, inc=None, z_next_re=None, z_next_im=Non
 def fpe_grad_points(P: Poly, z_re, z_im, g_re, g_im, stream=None):
     import torch
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im)
+    if g_re is None:
+        raise ValueError("g_re is required")
+    _check_vec(g_re, n, z_re.device, torch.float64, "g_re")
+    _check_vec(g_im, n, z_re.device, torch.float64, "g_im")
     gz_re = torch.empty_like(z_re)
     gz_im = torch.empty_like(z_re)
     _check(lib.fpe_grad_points(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(g_re), _dptr(g_im), _dptr(gz_re),
@@ -475,8 +555,15 @@ def fpe_grad_points(P: Poly, z_re, z_im, g_re, g_im, stream=None):
 
 def fpe_grad_coeffs(P: Poly, z_re, z_im, g_re, g_im, ga_re, ga_im=None, stream=None):
     """Adds dL/da_k into ga_re/ga_im (device float64, n_coef entries)."""
+    import torch
     lib = _load()
-    n = int(z_re.shape[0])
+    n = _eval_args(P, z_re, z_im)
+    if g_re is None or ga_re is None:
+        raise ValueError("g_re and ga_re are required")
+    _check_vec(g_re, n, z_re.device, torch.float64, "g_re")
+    _check_vec(g_im, n, z_re.device, torch.float64, "g_im")
+    _check_vec(ga_re, P.n_coef, z_re.device, torch.float64, "ga_re")
+    _check_vec(ga_im, P.n_coef, z_re.device, torch.float64, "ga_im")
     _check(lib.fpe_grad_coeffs(P.handle, _dptr(z_re), _dptr(z_im), n, _dptr(g_re), _dptr(g_im), _dptr(ga_re),
                                _dptr(ga_im), _stream(stream)), "fpe_grad_coeffs")
     return ga_re, ga_im
@@ -487,6 +574,7 @@ def fpe_to_complex(v, stream=None):
     import torch
     lib = _load()
     n = int(v.shape[0])
+    _check_out(v, n, v.device)
     re = torch.empty(n, dtype=torch.float64, device=v.device)
     im = torch.empty(n, dtype=torch.float64, device=v.device)
     _check(lib.fpe_to_complex(_dptr(v), n, _dptr(re), _dptr(im), _stream(stream)), "fpe_to_complex")

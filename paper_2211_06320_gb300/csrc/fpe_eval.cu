@@ -1441,6 +1441,8 @@ constexpr size_t kNaVal = kNaGroup + align256(kNoAllocExtra * sizeof(int32_t));
 constexpr size_t kNaCarry = kNaVal + align256((kNoAllocMaxPoints + kNoAllocExtra) * sizeof(xdd));
 constexpr size_t kNaBins = kNaCarry + align256((kNoAllocMaxPoints + kNoAllocExtra) * sizeof(xdd));
 constexpr size_t kNoAllocBytes = kNaBins + align256((2 * kNumBins + kNumCounters) * sizeof(uint32_t));
+// the figure fpe.h states for the built-in scratch (9,429,248 bytes, about 9.0 MiB)
+static_assert(kNoAllocBytes == 9429248, "fpe.h states the size of the built-in scratch: update it with this layout");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -1484,9 +1486,12 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
     return FPE_ERR_INVALID_ARG;
   }
   if (n == 0) return FPE_OK;
+  // the handle's device must be current before its symbol address is looked up
+  // (and cached under that device): check both calls
   int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != P->device) cudaSetDevice(P->device);
+  cudaError_t de = cudaGetDevice(&prev);
+  if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+  if (prev != P->device && (de = cudaSetDevice(P->device)) != cudaSuccess) return cuda_fail(de, "cudaSetDevice");
   unsigned char *base = nullptr;
   fpe_status s = noalloc_scratch(P->device, &base);
   if (s == FPE_OK) {
