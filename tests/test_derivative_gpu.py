@@ -120,6 +120,22 @@ def _dense_coeff_grad(z, g, n_coef):
     return G, A
 
 
+def _oracle_windows(coef, zre, zim, l_gpu=None, r_gpu=None):
+    """Each point's window [l, r] and G_p from the oracle (p = 53); z = 0 gets the
+    window {0} (P(0) = a_0).  When the GPU's windows are given they must be the
+    oracle's exactly (a point within 2^-30 of a boundary tie would take either)."""
+    pre = oracle.precondition(coef, 53)
+    lam = oracle.log2_abs(zre, zim)
+    _, _, L, R = oracle.windows(pre.hk, pre.hs, pre.T, lam)
+    zero = ~np.isfinite(lam)
+    L[zero], R[zero] = 0, 0
+    if l_gpu is not None:
+        fin = ~zero
+        assert np.array_equal(l_gpu[fin], L[fin]) and np.array_equal(r_gpu[fin], R[fin]), \
+            "GPU windows differ from the oracle's"
+    return L, R, pre.good
+
+
 def _dense_coeff_grad_windowed(z, g, n_coef, L, R, good):
     """sum_j g_j conj(z_j)^k over each point's kept terms only (L_j <= k <= R_j, k good)."""
     w = np.ones_like(z)
@@ -160,8 +176,8 @@ def test_coefficient_gradient_vs_dense(env, long_window):
     l, rr, _ = F.fpe_get_windows(P, z.size)
     F.fpe_sync(P)
     got = ga_re.cpu().numpy() + 1j * ga_im.cpu().numpy()
-    good = F.fpe_get_good(P)
-    Gw, Aw = _dense_coeff_grad_windowed(z, g, coef.n_coef, l.cpu().numpy(), rr.cpu().numpy(), good)
+    L, R, good = _oracle_windows(coef, z.real.copy(), z.imag.copy(), l.cpu().numpy(), rr.cpu().numpy())
+    Gw, Aw = _dense_coeff_grad_windowed(z, g, coef.n_coef, L, R, good)
     assert np.all(np.abs(got - Gw) <= 1e-12 * Aw + 1e-300)
     G, A = _dense_coeff_grad(z, g, coef.n_coef)
     _, _, l2M = oracle.horner_ref(coef, z.real.copy(), z.imag.copy())
@@ -188,9 +204,8 @@ def test_coefficient_gradient_real(env, long_window):
     F.fpe_eval(P, xr, None)
     l, rr, _ = F.fpe_get_windows(P, x.size)
     F.fpe_sync(P)
-    good = F.fpe_get_good(P)
-    L, R = l.cpu().numpy(), rr.cpu().numpy()
-    L[x == 0], R[x == 0] = 0, 0  # P(0) = a_0: the window of z = 0 is {0}
+    # the oracle's windows (z = 0: the window {0}, as P(0) = a_0)
+    L, R, good = _oracle_windows(coef, x.copy(), None, l.cpu().numpy(), rr.cpu().numpy())
     with np.errstate(over="ignore", invalid="ignore"):
         Gw, Aw = _dense_coeff_grad_windowed(x.astype(complex), g.astype(complex), coef.n_coef, L, R, good)
     got = ga.cpu().numpy()
@@ -270,8 +285,8 @@ def test_differentiation_workload_reduced(env):
     g = 2 * (Pv - t)
     F.fpe_eval(poly, zt.real.contiguous(), zt.imag.contiguous())
     l, rr, _ = F.fpe_get_windows(poly, z.size)
-    G, A = _dense_coeff_grad_windowed(z, g, wl.coeffs.n_coef, l.cpu().numpy(), rr.cpu().numpy(),
-                                      F.fpe_get_good(poly))
+    L, R, good = _oracle_windows(wl.coeffs, z.real.copy(), z.imag.copy(), l.cpu().numpy(), rr.cpu().numpy())
+    G, A = _dense_coeff_grad_windowed(z, g, wl.coeffs.n_coef, L, R, good)
     got = a.grad.detach().cpu().numpy()
     assert np.all(np.abs(got - G) <= 1e-10 * A + 1e-300)
     inc, _, _ = F.fpe_newton(poly, zt.real.contiguous(), zt.imag.contiguous())
