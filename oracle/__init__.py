@@ -9,9 +9,10 @@ of ``bench.py`` may import, call or link it.  It shares no code with the CUDA
 path and never imports it.
 """
 from .fpe_oracle import (NEG_INF, ExtValues, Preconditioned, concave_cover, cover_value, fpe_eval,
-                         good_mask, horner_ref, log2_abs, num_threads, offset_T, precondition, scale,
-                         scale_of_int, window_sum, windows, windows_bruteforce)
+                         fpe_eval_fp64, good_mask, horner_ref, log2_abs, num_threads, offset_T, precondition,
+                         scale, scale_of_int, set_threads, window_sum, window_sum_fp64, windows,
+                         windows_bruteforce)
 
-__all__ = ["NEG_INF", "ExtValues", "Preconditioned", "concave_cover", "cover_value", "fpe_eval",
+__all__ = ["NEG_INF", "ExtValues", "Preconditioned", "concave_cover", "cover_value", "fpe_eval", "fpe_eval_fp64",
            "good_mask", "horner_ref", "log2_abs", "num_threads", "offset_T", "precondition", "scale",
-           "scale_of_int", "window_sum", "windows", "windows_bruteforce"]
+           "scale_of_int", "set_threads", "window_sum", "window_sum_fp64", "windows", "windows_bruteforce"]

@@ -20,6 +20,14 @@
  *   oracle_window_sum  Q(z) = sum over k in [lo, hi] with good[k] of a_k z^k
  *                      (eq. reducedQlambda), evaluated as z^lo times a Horner sum
  *                      over the window, z^lo by repeated squaring (§8.2).
+ *   oracle_window_sum_fp64
+ *                      the same sum with the Horner steps in plain FP64 complex
+ *                      arithmetic and a 64-bit binary exponent (renormalised when
+ *                      the partial sum leaves [2^-400, 2^400]), z^lo by repeated
+ *                      squaring in double-double: Algorithm A_p's evaluation as a
+ *                      plain CPU program in hardware floats (the paper's p = 53
+ *                      runs, §8.3), timed as a CPU baseline.
+ *   oracle_set_threads the number of OpenMP threads of the calls above.
  *
  * Coefficients: a_k = ((are[k] + are_lo[k]) + i (aim[k] + aim_lo[k])) * 2^ae[k];
  * aim, are_lo, aim_lo, ae may be NULL (zero).  Points: zim may be NULL (real).
@@ -293,6 +301,64 @@ void oracle_window_sum(int64_t n_coef, const double *are, const double *aim, con
       S_e[j] = se;
     }
   }
+}
+
+/* the FP64 restatement: sum_{k in [lo, hi], good[k]} a_k z^k */
+void oracle_window_sum_fp64(int64_t n_coef, const double *are, const double *aim, const int64_t *ae,
+                            const uint8_t *good, int64_t npts, const double *zre, const double *zim,
+                            const int64_t *lo, const int64_t *hi, double *out, int64_t *oute) {
+  (void)n_coef;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t j = 0; j < npts; ++j) {
+    const double zr = zre[j], zi = zim ? zim[j] : 0.0;
+    double hr = 0.0, hm = 0.0;
+    int64_t E = 0; /* value = (hr + i hm) 2^E */
+    for (int64_t k = hi[j]; k >= lo[j] && hi[j] >= lo[j]; --k) {
+      const double nr = hr * zr - hm * zi, ni = hr * zi + hm * zr; /* h <- h z */
+      hr = nr;
+      hm = ni;
+      if (good && !good[k]) continue;
+      double br = are[k], bi = aim ? aim[k] : 0.0;
+      if (br == 0.0 && bi == 0.0) continue;
+      const int64_t e = ae ? ae[k] : 0;
+      if (hr == 0.0 && hm == 0.0) {
+        E = e; /* the first term sets the frame */
+      } else if (e - E > 300) { /* a term far above the frame moves the frame up to it */
+        const int64_t sh = E - e < -2000 ? -2000 : E - e;
+        hr = ldexp(hr, (int)sh);
+        hm = ldexp(hm, (int)sh);
+        E = e;
+      }
+      const int64_t d = e - E; /* <= 300: the coefficient in the frame 2^E */
+      if (d != 0) {
+        const int64_t dd_ = d < -2000 ? -2000 : d;
+        br = ldexp(br, (int)dd_);
+        bi = ldexp(bi, (int)dd_);
+      }
+      hr += br;
+      hm += bi;
+      const double m = fmax(fabs(hr), fabs(hm));
+      if (m != 0.0 && (m > 0x1p400 || m < 0x1p-400)) {
+        int f;
+        frexp(m, &f);
+        hr = ldexp(hr, -f);
+        hm = ldexp(hm, -f);
+        E += f;
+      }
+    }
+    xdd h = xdd_from(hr, 0.0, hm, 0.0, E);
+    xdd v = xdd_is_zero(h) ? h : xdd_mul(h, xdd_pow(xdd_from(zr, 0.0, zi, 0.0, 0), lo[j]));
+    store(v, j, out, oute);
+  }
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
 
 int oracle_num_threads(void) {

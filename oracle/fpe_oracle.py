@@ -31,6 +31,9 @@ the paper's notation:
 * ``window_sum``     -- Q_lambda(z) = sum_{k in G_p cap [l, r]} a_k z^k
                         (eq. reducedQlambda) in extended double-double.
 * ``fpe_eval``       -- Algorithm A_p end to end: windows, then window_sum.
+* ``window_sum_fp64``, ``fpe_eval_fp64`` -- the same with the window's Horner
+                        steps in plain FP64 (a CPU baseline for timing, pinned
+                        by exact sums, not a reference value).
 
 Readings where the paper is silent:
   p counts significand bits (53 for FP64, 24 for FP32); T = p + s(d) + 3 with
@@ -387,6 +390,10 @@ def _load():
         lib.oracle_horner.restype = None
         lib.oracle_window_sum.argtypes = [I, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P]
         lib.oracle_window_sum.restype = None
+        lib.oracle_window_sum_fp64.argtypes = [I, P, P, P, P, I, P, P, P, P, P, P]
+        lib.oracle_window_sum_fp64.restype = None
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = None
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -463,8 +470,34 @@ def window_sum(coef, good: Optional[np.ndarray], zre, zim, lo, hi, coef_lo=None,
     return ExtValues(out, oute)
 
 
+def window_sum_fp64(coef, good: Optional[np.ndarray], zre, zim, lo, hi):
+    """The same window sum with the Horner steps in plain FP64 (and a 64-bit
+    exponent), z^lo in double-double: Algorithm A_p as a CPU program in hardware
+    floats, for timing.  Its error is that of FP64 Horner over the window."""
+    lib = _load()
+    are = _c(coef.re, np.float64)
+    aim = _c(coef.im, np.float64)
+    ae = _c(coef.e2, np.int64)
+    g = _c(good, np.uint8)
+    zre = _c(zre, np.float64)
+    zim = _c(zim, np.float64)
+    lo = _c(lo, np.int64)
+    hi = _c(hi, np.int64)
+    n = zre.shape[0]
+    out = np.zeros((n, 4))
+    oute = np.zeros(n, dtype=np.int64)
+    lib.oracle_window_sum_fp64(are.shape[0], _ptr(are), _ptr(aim), _ptr(ae), _ptr(g), n, _ptr(zre), _ptr(zim),
+                               _ptr(lo), _ptr(hi), _ptr(out), _ptr(oute))
+    return ExtValues(out, oute)
+
+
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the C part uses from now on."""
+    _load().oracle_set_threads(int(n))
 
 
 # ----------------------------------------------------------------------------
@@ -490,6 +523,17 @@ class Preconditioned:
 
 def precondition(coef, p: int) -> Preconditioned:
     return Preconditioned(coef, p)
+
+
+def fpe_eval_fp64(pre: Preconditioned, zre, zim=None):
+    """Algorithm A_p evaluation with the window sums in plain FP64 (window_sum_fp64)."""
+    lam = log2_abs(np.asarray(zre, dtype=np.float64), None if zim is None else np.asarray(zim, dtype=np.float64))
+    kl, N, L, R = windows(pre.hk, pre.hs, pre.T, lam)
+    zero = ~np.isfinite(lam)
+    L2, R2 = L.copy(), R.copy()
+    L2[zero] = 0
+    R2[zero] = 0
+    return window_sum_fp64(pre.coef, pre.good, zre, zim, L2, R2), (kl, N, L, R)
 
 
 def fpe_eval(pre: Preconditioned, zre, zim=None, with_S: bool = False):

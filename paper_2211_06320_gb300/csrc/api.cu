@@ -572,6 +572,10 @@ fpe_status fpe_sync(fpe_poly_t P, void *cuda_stream) {
       set_error("non-finite evaluation point");
       return FPE_ERR_NONFINITE;
     }
+    if (h & kStatusTimeout) {
+      set_error("a bounded wait of the tensor-core window sums gave up (results are incomplete)");
+      return FPE_ERR_TIMEOUT;
+    }
     set_error("device status " + std::to_string(h));
     return FPE_ERR_CUDA;
   }

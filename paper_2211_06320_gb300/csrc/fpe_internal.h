@@ -81,7 +81,7 @@ constexpr int kTcMaxPieces = 4;
 constexpr int kTcBinsPerPiece = 16384;
 constexpr int kTcBins = kTcMaxPieces * kTcBinsPerPiece;
 constexpr int kTcMinPieceLen = 64;  // shorter pieces never get the tensor path
-constexpr int kTcPoints = 64;       // points per tile (one CTA)
+constexpr int kTcPoints = 128;      // points per tile: the M = 128 rows of one tcgen05 MMA
 constexpr int kTcItemsPerSm = 16;   // work items per SM the planner aims at (at least)
 constexpr int kTcMinChunk = 256;    // blocks (of 32 terms) per work item, at least
 
@@ -151,6 +151,7 @@ constexpr int32_t kPointTC = 4;  // summed by the tensor-core kernels
 
 // Device status word bits.
 constexpr int32_t kStatusNonFinite = 1;
+constexpr int32_t kStatusTimeout = 2;  // a bounded device-side wait gave up
 
 // Scratch memory of one handle, grown on demand.
 struct Workspace {

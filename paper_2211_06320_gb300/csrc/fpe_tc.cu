@@ -19,13 +19,13 @@
 //   2^(62 |mu - c|) of the block's largest term).
 //
 //   Slices.  Each component of A' (per block) and of Z' (per point) is a
-//   69-bit fixed-point number relative to a power of two above its block's or
-//   point's largest component, written as ten balanced base-128 digits d_0..d_9
-//   (|d| <= 64, exact in bf16).  A digit product is at most 2^12 in
-//   magnitude, a 64-long dot product of digits at most 2^18, and the at most
-//   ten digit pairs with the same s + s' = t add up below 2^22: fp32
-//   accumulation is exact.  Pairs with t <= 9 are kept (55 of 100); the
-//   dropped ones and the truncation leave an error below 2^-66 per product
+//   71-bit fixed-point number relative to a power of two above its block's or
+//   point's largest component, written as nine balanced base-256 digits
+//   d_0..d_8 (|d| <= 128, exact in bf16).  A digit product is at most 2^14 in
+//   magnitude, a 64-long dot product of digits at most 2^20, and the at most
+//   nine digit pairs with the same s + s' = t add up below 2^23.2: fp32
+//   accumulation is exact.  Pairs with t <= 9 are kept (53 of 81); the
+//   dropped ones and the truncation leave an error below 2^-70 per product
 //   relative to the scales.
 //
 //   Combination.  The ten integer accumulators of each (block, point) are
@@ -36,11 +36,20 @@
 // Error per window: below 2^-53.5 times S(z) for tiles with 31 |mu - c| <= 2,
 // which the planner enforces (other tiles go back to the FP64 kernels).
 //
-// MMA layout (m16n8k16, A row-major 16 x 16, B column 16 x 8): the 16 rows of
-// A are 8 blocks x (real part, imaginary part) of the output, the 8 columns
-// of B are 8 points, and the contraction index kappa runs over the 32 terms'
-// (real, imaginary) point powers:
-//   out_re = sum_i (A'_re Z'_re - A'_im Z'_im),  out_im = sum_i (A'_im Z'_re + A'_re Z'_im).
+// MMA layout (tcgen05.mma, kind::f16, M = 128, K = 16 per instruction,
+// operands in shared memory, fp32 accumulators in tensor memory): the 128
+// rows of A are the tile's 128 points, each row one digit slice of the point's
+// Z' over the contraction index kappa = the 32 terms' (real, imaginary)
+// powers (K = 64, four k-steps).  B stacks, for a sub-tile of 8 blocks, the
+// digit slices sa = 0..8 of A' (and one slice of zeros): row 16 sa + 2j + c is
+// block j's real row (c = 0) or imaginary row (c = 1) of slice sa,
+//   real row (A'_re | -A'_im),  imaginary row (A'_im | A'_re),
+// so that out_re = sum_i (A'_re Z'_re - A'_im Z'_im) and
+// out_im = sum_i (A'_im Z'_re + A'_re Z'_im).  One MMA takes Z' slice s as A
+// and the first N_s rows of B (all slices sa with s + sa <= 9, N_s = 16 (10 - s),
+// for s = 0 also the zero slice: N_0 = 160) into the accumulator columns
+// 16 (s + sa) + 2j + c: each column block t = s + sa collects exactly the digit
+// pairs of its diagonal, nine MMAs per k-step instead of one per pair.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,6 +57,7 @@
 
 #include "fpe_device.cuh"
 #include "fpe_internal.h"
+#include "fpe_tc05.cuh"
 #include "fpe_tc_arith.cuh"
 
 namespace fpe {
@@ -55,11 +65,21 @@ namespace fpe {
 namespace {
 
 constexpr int kTK = 2 * kTB;                 // contraction length (re, im per term)
-constexpr int kSub = 8;                      // blocks per MMA sub-tile (16 rows)
-constexpr int kTcWarps = kTcPoints / 8;      // one warp per 8 points (and per block of a sub-tile)
+constexpr int kSub = 8;                      // blocks per MMA sub-tile
+constexpr int kTcN = 2 * kSub;               // MMA columns: block j's real row 2j, imaginary row 2j + 1
+constexpr int kTcEpiWarps = 16;              // warps 0..15 read the accumulators (0..7 also write B's digits)
+constexpr int kTcWarps = kTcEpiWarps;        // four per SM sub-partition: 128 registers a thread
 constexpr int kTcThreads = 32 * kTcWarps;
-static_assert(kTcWarps == kSub, "the A' tile is built one block per warp");
+constexpr int kTcMmaWarp = kTcEpiWarps - 1;  // also issues the MMAs (converged, one elected lane)
+constexpr int kTcPerPoint = kTcEpiWarps / 4; // epilogue threads per point (warps w, w + 4, ... share TMEM lanes)
+constexpr int kTcBlkPerThr = kSub / kTcPerPoint;  // blocks of a sub-tile per epilogue thread (2)
+static_assert(kTcPoints == 128, "one tile is the M = 128 rows of the MMA");
+static_assert(kTK * 2 == 128, "one operand row is 128 bytes: one 128-byte swizzle row");
 constexpr double kTcTiltBits = 2.0;          // max 31 |mu - c| over a group's points
+constexpr uint32_t kTcPollLimit = 1u << 22;  // polls of an mbarrier before a wait gives up
+// every kTcFold sub-tiles a thread folds its 64-bit Horner value into a 128-bit
+// one (times W^(8 kTcFold)), so no 64-bit chain is longer than 4 kTcFold steps
+constexpr int kTcFold = 16;
 
 struct TcTile {
   int32_t start, count;  // bucketed positions [start, start + count)
@@ -70,10 +90,11 @@ struct TcTile {
   double c;              // tilt exponent
 };
 
-// Per tile point, computed once by k_tc_pre: W^(2^k) for k = 0..3 (W = w^32),
-// which combine blocks, and Z's scale exponent eq.
+// Per tile point, computed once by k_tc_pre: W^(2^k) for k = 0..3 (W = w^32)
+// and W^(8 kTcFold), which combine blocks, and Z's scale exponent eq.
 struct TcPoint {
   xint W[4];   // W, W^2, W^4, W^8
+  xint Wf;     // W^(8 kTcFold): between two folds
   int eq;
   int pad[3];
 };
@@ -86,53 +107,42 @@ struct TcTau {
   xint inv, tau32;
 };
 
-constexpr int kZBytes = kSl * kTcPoints * kTK * 2;  // one tile's Z' slices, as laid out in shared memory
-
-struct TcSmem {
-  uint16_t zq[kSl][kTK][kTcPoints];   // Z' slices (bf16 bits); rows kappa of the 64 points, chunks swizzled
-  uint16_t aq[kSl][2 * kSub][kTK];    // A' slices of the current sub-tile
-  xh w8[kTcPoints];                   // W^8 per point (64-bit mantissas)
-  xh w1[kTcPoints];                   // W per point (the final combination)
-  unsigned long long tm[kTB];         // tau^i = tm[i] 2^te[i]
-  int te[kTB];
-  int eq[kTcPoints];                  // Z' scale exponent per point
-  int er[kSub];                       // A' scale exponent per block of the sub-tile
-  int item, tile;
-};
-
-// Z' layout, per slice: 64 rows (kappa) of the 64 points' values (128 B), the
-// 16-B chunk (8 points) xor-ed by kappa & 7; B fragments are read transposed
-__device__ __forceinline__ int zswz(int kappa, int p) {
-  return kappa * kTcPoints + ((((p >> 3) ^ (kappa & 7)) << 3) | (p & 7));
+// K-major operands with the 128-byte swizzle: a row (one point of A, one
+// output row of B) is 128 bytes, the 16-byte chunk c of row r at position
+// c ^ (r & 7), eight rows to a 1024-byte atom.  Byte offset of element
+// (row r, kappa) in one slice:
+__host__ __device__ __forceinline__ int tc_swz(int r, int kappa) {
+  return r * 128 + ((((kappa >> 3) ^ (r & 7))) << 4) + ((kappa & 7) << 1);
 }
+constexpr int kASlice = kTcPoints * 128;           // 16 KB: one slice of A (the tile's Z' digits)
+constexpr int kBSlice = kTcN * 128;                // 2 KB: one slice of B (a sub-tile's A' digits)
+constexpr int kBBuf = (kSl + 1) * kBSlice;         // B buffer: the nine slices and one of zeros (160 rows)
+constexpr int kZBytes = kSl * kASlice;             // one tile's Z' image (144 KB), as laid out in shared memory
+
+// shared memory of k_tc_sum (offsets from a 1024-byte aligned base)
+constexpr int kSmA = 0;                                 // A: 10 slices
+constexpr int kSmB = kSmA + kZBytes;                    // B: two buffers of 9 slices + one of zeros
+constexpr int kSmW1 = kSmB + 2 * kBBuf;                 // per point W and W^8 (xh), the final exchange
+constexpr int kSmW8 = kSmW1 + kTcPoints * (int)sizeof(xh);
+constexpr int kSmHx = kSmW8 + kTcPoints * (int)sizeof(xh);  // (kTcPerPoint - 1) values per point
+constexpr int kSmTm = kSmHx + (kTcPerPoint - 1) * kTcPoints * (int)sizeof(xh);  // tau^i mantissas
+constexpr int kSmTe = kSmTm + kTB * 8;                      // and exponents
+constexpr int kSmEq = kSmTe + kTB * 4;                      // Z' scale exponent per point
+constexpr int kSmEr = kSmEq + kTcPoints * 4;                // A' scale exponent per block, two buffers
+constexpr int kSmBar = kSmEr + 2 * kSub * 4;                // mbarriers: MMA done (2), Z' loaded
+constexpr int kSmMisc = kSmBar + 3 * 8;                     // TMEM address, item, tile, abort flag
+constexpr int kSmEnd = kSmMisc + 16;
+constexpr int kTcSmemBytes = kSmEnd + 1024;                 // + slack for the 1024-byte alignment
+static_assert(kSmBar % 8 == 0, "mbarriers are 8-byte aligned");
+static_assert(kTcSmemBytes <= 232448, "within the 227 KB of shared memory a block may use");
+constexpr uint32_t kTmemCols = 512;          // two buffers of 10 accumulators x 16 columns (320 used)
+constexpr int kTmemBuf = kAcc * kTcN;        // columns per buffer
 
 // a 128-bit value across lane ^ 1
 __device__ __forceinline__ u128 shfl_u128_x1(u128 v) {
   const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, 1);
   const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), 1);
   return ((u128)hi << 64) | lo;
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // xor-shuffle of an xint across the warp
@@ -463,15 +473,17 @@ __global__ void __launch_bounds__(256) k_tc_tau(const TcTile *__restrict__ tiles
   }
 }
 
-// per tile point (one thread each): u = w / tau, the Z'
-// slices of u^i (i < 32) written straight to global memory in the layout
-// k_tc_sum copies into shared memory (for each slice and term, the 64
-// points' values are one 128-B row, so a warp's stores are contiguous),
-// W^(2^k) = (u^32 tau^32)^(2^k), and Z's scale exponent.
+// per tile point (one thread each): u = w / tau, and the Z' slices of u^i
+// (i < 32) written to global memory in exactly the layout k_tc_sum copies
+// into shared memory as the MMA's A operand: per slice, the point's row of
+// 128 bytes (kappa = i for the real part of u^i, 32 + i for the imaginary
+// part), as 16-byte chunks at their swizzled positions (eight powers at a
+// time, one chunk per slice and component); W^(2^k) = (u^32 tau^32)^(2^k),
+// and Z's scale exponent.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
                                                       const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
-                                                      const TcTau *__restrict__ taus, uint16_t *__restrict__ zglob,
+                                                      const TcTau *__restrict__ taus, unsigned char *__restrict__ zglob,
                                                       const uint32_t *cnt) {
   const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -495,104 +507,179 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
       cur = xh_norm(1ull << 63, 0, 0, 0, 0);  // 1
     }
     // powers u^i in 64-bit mantissas: each product truncates at 2^-63, so u^31
-    // is within 2^-58 of its value relative to itself.  Lane pairs (points
-    // p even, p + 1) share the stores: the even lane writes both points' real
-    // parts, the odd lane both imaginary parts, each as bf16 pairs.
-    const int odd = p & 1, pb = p & ~1;
-    uint32_t *zt = reinterpret_cast<uint32_t *>(zglob + (size_t)t * (kZBytes / 2));
-    for (int i = 0; i < kTB; ++i) {
-      if (i > 0 && valid) cur = xh_mul(cur, uh);
-      // x 2^(e - 63) 2^(70 - (eQ + 1)) = x 2^-sr: fixed point below 2^69 (components <= 2^(eQ - 1))
-      const int sr = eQ + 1 - 7 - (int)cur.e;
-      const u128 fr = valid ? shift_to70((u128)cur.x, sr) : (u128)0;
-      const u128 fi = valid ? shift_to70((u128)cur.y, sr) : (u128)0;
-      const u128 mine = odd ? fi : fr, recv = shfl_u128_x1(odd ? fr : fi);
-      const uint32_t nmine = (uint32_t)(odd ? cur.sy : cur.sx);
-      const uint32_t nrecv = __shfl_xor_sync(0xffffffffu, (uint32_t)(odd ? cur.sx : cur.sy), 1);
-      uint32_t xa[kSl], xb[kSl];  // point pb, point pb + 1
-      bchunks70(odd ? recv : mine, xa);
-      bchunks70(odd ? mine : recv, xb);
-      const DigitSign sa = digit_sign(odd ? nrecv : nmine), sb = digit_sign(odd ? nmine : nrecv);
-      const int c = zswz(odd ? kTB + i : i, pb) >> 1;
+    // is within 2^-58 of its value relative to itself
+    unsigned char *zt = zglob + (size_t)t * kZBytes;
+#pragma unroll 1
+    for (int g = 0; g < kTB / 8; ++g) {
+      uint32_t wr[kSl][4], wi[kSl][4];  // bf16 pairs of powers 8g + 2q, 8g + 2q + 1
 #pragma unroll
-      for (int s = 0; s < kSl; ++s) zt[s * (kTK * kTcPoints / 2) + c] = bf16_pair(xa[s], sa, xb[s], sb);
+      for (int q = 0; q < 4; ++q) {
+        uint32_t xr[2][kSl], xi[2][kSl];
+        DigitSign sr[2], si[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if ((g | q | h) != 0 && valid) cur = xh_mul(cur, uh);
+          // x 2^(e - 63) 2^(72 - eq) = x 2^-sh with eq = eQ + 1: fixed point below
+          // 2^70 (components <= 2^(eQ - 1))
+          const int sh = eQ + 1 + 63 - 72 - (int)cur.e;
+          bchunks72(valid ? shift_to72((u128)cur.x, sh) : (u128)0, xr[h]);
+          bchunks72(valid ? shift_to72((u128)cur.y, sh) : (u128)0, xi[h]);
+          sr[h] = digit_sign((uint32_t)cur.sx);
+          si[h] = digit_sign((uint32_t)cur.sy);
+        }
+#pragma unroll
+        for (int s = 0; s < kSl; ++s) {
+          wr[s][q] = bf16_pair(xr[0][s], sr[0], xr[1][s], sr[1]);
+          wi[s][q] = bf16_pair(xi[0][s], si[0], xi[1][s], si[1]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < kSl; ++s) {
+        *reinterpret_cast<uint4 *>(zt + s * kASlice + tc_swz(p, 8 * g)) =
+            make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+        *reinterpret_cast<uint4 *>(zt + s * kASlice + tc_swz(p, kTB + 8 * g)) =
+            make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+      }
     }
     TcPoint o;
     xint W = zero;
     if (valid) {  // W = u^32 tau^32 = w^32 from the 128-bit u: the block weights W^g and
-      // (W^8)^tau of the Horner must not inherit the 64-bit powers' error
+      // the Horner multipliers must not inherit the 64-bit powers' error
       xint u32 = u;
       for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
       W = xint_mul(u32, taus[t].tau32);
     }
     o.W[0] = W;
     for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
-    o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
+    o.Wf = o.W[3];
+    for (int q = 1; (1 << q) <= kTcFold; ++q) o.Wf = xint_sqr(o.Wf);
+    o.eq = eQ + 1;  // Z' = F 2^(eq - 72)
     o.pad[0] = o.pad[1] = o.pad[2] = 0;
     pts[(size_t)t * kTcPoints + p] = o;
   }
 }
 
 // ---------------------------------------------------------------------------
-// the window sums: persistent CTAs of 8 warps (two per SM) take work items (a
-// tile and a run of at most `chunk` blocks) from a counter; each item's
-// value per point, sum over its blocks m of C_m W^(m - first), goes to a slot
+// the window sums on the tensor cores.  One persistent CTA per SM (16 warps) takes work
+// items (a tile and a run of at most `chunk` blocks) from a counter.  Per
+// item, the tile's Z' image (the A operand, 144 KB) arrives by nine bulk
+// copies on an mbarrier; then, sub-tile by sub-tile of 8 blocks from the top
+// down, in a two-stage pipeline:
+//   warps 0-7 write B's digits for sub-tile s (one term per thread) into one
+//     of two buffers; warps 0-15 then read the accumulators of sub-tile s + 1;
+//   warp 15 (converged, one elected lane) issues the 36 MMAs of sub-tile s
+//     (9 Z' slices x 4 k-steps, each against the stacked A' slices) into one
+//     of two sets of ten TMEM accumulators and commits them to that set's
+//     mbarrier.
+// Thread w 32 + l of warps 0-15 is TMEM lane 32 (w % 4) + l, i.e. point
+// p = 32 (w % 4) + l, and takes blocks 2 h, 2 h + 1 (h = w / 4) of each
+// sub-tile: it joins each block's ten fp32 accumulators (real and imaginary
+// columns, one per diagonal) into 128-bit integers and runs Horner's scheme
+// over its sub-tiles in 64-bit mantissas, H <- H W^8 + C_1 W + C_0, folded
+// every kTcFold sub-tiles into a 128-bit value.  At the end of the item the
+// four parts of each point are joined, V = A_0 + W^2 (A_1 + W^2 (A_2 + W^2 A_3)),
+// and the value goes to the item's slot.  Every mbarrier wait is bounded; a wait
+// that gives up sets FPE_ERR_TIMEOUT's status bit and the CTA stops.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_sum(DevPoly P, const TcTile *__restrict__ tiles, const TcPoint *__restrict__ pts,
-             const TcTau *__restrict__ taus, const uint4 *__restrict__ zglob, const int32_t *__restrict__ item_base,
-             const int32_t *__restrict__ item_tile, uint32_t *cnt, xint *__restrict__ slots) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+             const TcTau *__restrict__ taus, const unsigned char *__restrict__ zglob,
+             const int32_t *__restrict__ item_base, const int32_t *__restrict__ item_tile, uint32_t *cnt,
+             xint *__restrict__ slots, int32_t *status) {
+  using namespace tc05;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // swizzle atoms: 1024-aligned
+  xh *sW1 = reinterpret_cast<xh *>(sm + kSmW1);
+  xh *sW8 = reinterpret_cast<xh *>(sm + kSmW8), *sHx = reinterpret_cast<xh *>(sm + kSmHx);
+  unsigned long long *sTm = reinterpret_cast<unsigned long long *>(sm + kSmTm);
+  int *sTe = reinterpret_cast<int *>(sm + kSmTe), *sEq = reinterpret_cast<int *>(sm + kSmEq);
+  int *sEr = reinterpret_cast<int *>(sm + kSmEr);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);  // [0], [1]: MMAs done per buffer; [2]: Z' loaded
+  volatile int *misc = reinterpret_cast<volatile int *>(sm + kSmMisc);  // TMEM address, item, tile
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool mma_thread = tid == kTcMmaWarp * 32;  // issues the bulk copies
   const uint32_t nitems = *(volatile uint32_t *)&cnt[kCntTcItems];
   const long long chunk = (long long)*(volatile uint32_t *)&cnt[kCntTcChunk];
   const xint zero = xint_norm(0, 0, 0, 0, 0);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
+    fence_mbar_init();
+  }
+  if (wid == kTcMmaWarp) {
+    tmem_alloc(reinterpret_cast<uint32_t *>(sm + kSmMisc), kTmemCols);
+    tmem_relinquish();
+  }
+  // the zero slice after the nine A' slices of each B buffer (read by the first MMA of a sub-tile)
+  for (int i = tid; i < 2 * kBSlice / 16; i += kTcThreads) {
+    const int b = i / (kBSlice / 16), q = i % (kBSlice / 16);
+    reinterpret_cast<uint4 *>(sm + kSmB + b * kBBuf + kSl * kBSlice)[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  fence_proxy_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tbase = (uint32_t)misc[0];
+  const uint32_t aaddr = smem_u32(sm + kSmA), baddr = smem_u32(sm + kSmB);
+  const uint64_t adesc0 = desc_sw128_kmajor(aaddr);
+  uint32_t ph_mma[2] = {0u, 0u}, ph_z = 0u;  // parity of the next phase each mbarrier completes
+  int abort = 0;                             // this thread saw a wait give up
+  // epilogue thread: point p, blocks 2 h, 2 h + 1 of each sub-tile
+  const int p = 32 * (wid & 3) + lane, h = (wid >> 2) & 3;
+
   while (true) {
     if (tid == 0) {
       const uint32_t it = atomicAdd(&cnt[kCntTcWork], 1u);
-      S.item = (int)it;
-      S.tile = it < nitems ? item_tile[it] : -1;
+      misc[1] = (int)it;
+      misc[2] = it < nitems ? item_tile[it] : -1;
     }
     __syncthreads();
-    const int item = S.item, t = S.tile;
+    const int item = misc[1], t = misc[2];
     if (t < 0) break;
     const TcTile T = tiles[t];
     const int j = T.piece;
     const long long k0 = P.piece_k0[j], k1 = (long long)P.piece_k0[j + 1] - 1;
     const long long mb = T.mlo + (long long)(item - item_base[t]) * chunk;
     const long long me = min((long long)(T.mlo + T.nblk), mb + chunk);
+    const int nsub = (int)((me - mb + kSub - 1) / kSub);
     const TcPoint *tp = pts + (size_t)t * kTcPoints;
 
-    // ---- setup: the tile's Z' slices, tau^i, W^8 and Z's scales into shared memory
-    {
-      const uint4 *src = zglob + (size_t)t * (kZBytes / 16);
-      uint4 *dst = reinterpret_cast<uint4 *>(&S.zq[0][0][0]);
-      for (int i = tid; i < kZBytes / 16; i += kTcThreads) dst[i] = src[i];
-      if (tid < kTB) {
-        S.tm[tid] = taus[t].tm[tid];
-        S.te[tid] = taus[t].te[tid];
-      }
-      if (tid < kTcPoints) {
-        const bool v = tid < T.count;
-        S.w8[tid] = xh_from_xint(v ? tp[tid].W[3] : zero);
-        S.eq[tid] = v ? tp[tid].eq : 1;
-        S.w1[tid] = xh_from_xint(v ? tp[tid].W[0] : zero);
-      }
+    // ---- setup: the Z' image by bulk copies; tau^i and the points' multipliers
+    if (mma_thread) {
+      mbar_arrive_expect_tx(&bar[2], (uint32_t)kZBytes);
+      const unsigned char *src = zglob + (size_t)t * kZBytes;
+#pragma unroll 1
+      for (int s = 0; s < kSl; ++s) bulk_g2s(sm + kSmA + s * kASlice, src + s * kASlice, kASlice, &bar[2]);
     }
-    __syncthreads();
+    if (tid < kTcPoints) {
+      const bool v = tid < T.count;
+      sW1[tid] = xh_from_xint(v ? tp[tid].W[0] : zero);
+      sW8[tid] = xh_from_xint(v ? tp[tid].W[3] : zero);
+      sEq[tid] = v ? tp[tid].eq : 1;
+    } else if (tid < kTcPoints + kTB) {
+      sTm[tid - kTcPoints] = taus[t].tm[tid - kTcPoints];
+      sTe[tid - kTcPoints] = taus[t].te[tid - kTcPoints];
+    }
+    if (!mbar_wait(&bar[2], ph_z, kTcPollLimit)) {
+      abort = 1;
+      atomicOr(status, kStatusTimeout);
+    }
+    ph_z ^= 1u;
+    if (__syncthreads_or(abort)) break;
 
-    // ---- sub-tiles of 8 blocks, from the top down (Horner in W^8 per lane)
-    const int g = lane >> 2, tq = lane & 3;
-    const int p0 = 8 * wid + 2 * tq;
-    xh H0 = xh_norm(0, 0, 0, 0, 0), H1 = H0;
-    const int nsub = (int)((me - mb + kSub - 1) / kSub);
-    // coefficient of this lane in block mb + 8 ts + wid (0 outside the item or the piece)
+    // ---- sub-tiles of 8 blocks, from the top down
+    const xh w1 = sW1[p], w8 = sW8[p];
+    const int eqp = sEq[p];
+    xh H = xh_norm(0, 0, 0, 0, 0);
+    xint Acc = zero;  // the folded 128-bit value
+    int e_prev[kTcBlkPerThr] = {0, 0}, e_cur[kTcBlkPerThr] = {0, 0};
+    // coefficient of this thread's term in block mb + 8 ts + wid (0 outside the item or the piece)
     auto load_b = [&](int ts_) -> double2 {
       const long long m = mb + (long long)kSub * ts_ + wid;
       const long long k = k0 + kTB * m + lane;
       double2 c = make_double2(0.0, 0.0);
-      if (ts_ >= 0 && m < me && k <= k1) {
+      if (wid < kSub && ts_ >= 0 && m < me && k <= k1) {
         if (P.complex_coef)
           c = __ldg(reinterpret_cast<const double2 *>(P.b) + k);
         else
@@ -601,13 +688,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       return c;
     };
     double2 bnext = load_b(nsub - 1);
-    for (int ts = nsub - 1; ts >= 0; --ts) {
-      const long long m0 = mb + (long long)kSub * ts;
-      {  // A' for block m0 + wid, lane = term i
+    for (int it = 0; it <= nsub; ++it) {
+      const int ts = nsub - 1 - it;  // the sub-tile whose digits and MMAs this iteration makes
+      const int buf = it & 1;
+      if (it < nsub && wid < kSub) {  // B's digits for block mb + 8 ts + wid, thread = term
         const double br = bnext.x, bi = bnext.y;
-        bnext = load_b(ts - 1);  // in flight during this sub-tile's MMAs
-        const unsigned long long tmi = S.tm[lane];
-        const int tei = S.te[lane];
+        bnext = load_b(ts - 1);  // in flight during this sub-tile
+        const unsigned long long tmi = sTm[lane];
+        const int tei = sTe[lane];
         u128 pr = 0, pi = 0;
         int er_ = 0, ei_ = 0, top = INT_MIN;
         auto prod = [&](double x, u128 &pp, int &E) {
@@ -623,99 +711,143 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         prod(br, pr, er_);
         prod(bi, pi, ei_);
         for (int o = 16; o >= 1; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
-        const int eR = top == INT_MIN ? 0 : top + 2;  // every |component| < 2^(eR - 1): below 2^69 in F
-        const u128 fr = pr ? shift_to70(pr, eR - 70 - er_) : (u128)0;
-        const u128 fi = pi ? shift_to70(pi, eR - 70 - ei_) : (u128)0;
+        const int eR = top == INT_MIN ? 0 : top + 2;  // every |component| < 2^(eR - 1): below 2^71 in F
+        const u128 fr = pr ? shift_to72(pr, eR - 72 - er_) : (u128)0;
+        const u128 fi = pi ? shift_to72(pi, eR - 72 - ei_) : (u128)0;
         const uint32_t nr = br < 0.0, ni = bi < 0.0;
-        // lane pairs (terms i even, i + 1) share the stores: the even lane
-        // takes both terms' real parts, the odd lane both imaginary parts
+        // lane pairs (terms i even, i + 1) share the stores: the even lane takes
+        // both terms' real parts, the odd lane both imaginary parts
         const int odd = lane & 1, ib = lane & ~1;
         const u128 mine = odd ? fi : fr, recv = shfl_u128_x1(odd ? fr : fi);
         const uint32_t nmine = odd ? ni : nr, nrecv = __shfl_xor_sync(0xffffffffu, odd ? nr : ni, 1);
         uint32_t xa[kSl], xb[kSl];  // term ib, term ib + 1
-        bchunks70(odd ? recv : mine, xa);
-        bchunks70(odd ? mine : recv, xb);
+        bchunks72(odd ? recv : mine, xa);
+        bchunks72(odd ? mine : recv, xb);
         const DigitSign sa = digit_sign(odd ? nrecv : nmine), sb = digit_sign(odd ? nmine : nrecv);
-        // out_re row (wid): ( A'_re | -A'_im ), out_im row (8 + wid): ( A'_im | A'_re ).
-        // Even lane: the A'_re pair at (re row, low half) and (im row, high
-        // half); odd lane: -A'_im at (re row, high half), A'_im at (im row, low half).
-        const int c_lo = ((ib >> 3) ^ wid) << 3 | (ib & 7), c_hi = ((4 + (ib >> 3)) ^ wid) << 3 | (ib & 7);
-        const int o_re = (wid * kTK + (odd ? c_hi : c_lo)) >> 1;
-        const int o_im = ((kSub + wid) * kTK + (odd ? c_lo : c_hi)) >> 1;
+        // in slice s, real row 16 s + 2 wid = (A'_re | -A'_im) and imaginary row
+        // 16 s + 2 wid + 1 = (A'_im | A'_re): the even lane puts its A'_re pair at
+        // (real row, kappa ib) and (imaginary row, kappa 32 + ib); the odd lane
+        // -A'_im at (real row, 32 + ib) and A'_im at (imaginary row, ib).  A slice
+        // is 16 rows, two whole 8-row swizzle atoms, so the row's swizzle phase
+        // does not depend on s.
+        const int o1 = odd ? tc_swz(2 * wid, kTB + ib) : tc_swz(2 * wid, ib);
+        const int o2 = odd ? tc_swz(2 * wid + 1, ib) : tc_swz(2 * wid + 1, kTB + ib);
         const uint32_t flip = odd ? 0x80008000u : 0u;
-        uint32_t *a32 = reinterpret_cast<uint32_t *>(&S.aq[0][0][0]);
+        unsigned char *Bb = sm + kSmB + buf * kBBuf;
 #pragma unroll
         for (int s = 0; s < kSl; ++s) {
           const uint32_t w = bf16_pair(xa[s], sa, xb[s], sb);
-          a32[s * (kSub * kTK) + o_re] = w ^ flip;
-          a32[s * (kSub * kTK) + o_im] = w;
+          *reinterpret_cast<uint32_t *>(Bb + s * kBSlice + o1) = w ^ flip;
+          *reinterpret_cast<uint32_t *>(Bb + s * kBSlice + o2) = w;
         }
-        if (lane == 0) S.er[wid] = eR;
+        if (lane == 0) sEr[buf * kSub + wid] = eR;
       }
-      __syncthreads();
-      float acc[kSl][4];
+      // B (written by the generic proxy) becomes visible to the tensor core; the
+      // epilogue's TMEM reads of this buffer's previous use are ordered before
+      // the MMAs that overwrite it
+      fence_proxy_async_smem();
+      fence_before_sync();
+      if (__syncthreads_or(abort)) break;
+      fence_after_sync();
+      if (it < nsub) {
 #pragma unroll
-      for (int s = 0; s < kSl; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.0f;
+        for (int q = 0; q < kTcBlkPerThr; ++q) e_cur[q] = sEr[buf * kSub + kTcBlkPerThr * h + q];
+        if (wid == kTcMmaWarp) {  // the MMA warp, converged; one elected lane issues
+          // for Z' slice s: D[cols 16 s ..] (+)= A(slice s) B(rows 0 .. N_s - 1)^T, N_s as above;
+          // the first MMA (s = 0, k-step 0) covers every column and starts the sums
+          const uint32_t dcol = tbase + (uint32_t)(buf * kTmemBuf);
+          const uint64_t bdesc0 = desc_sw128_kmajor(baddr + (uint32_t)(buf * kBBuf));
+          if (elect_one()) {
 #pragma unroll
-      for (int kp = 0; kp < 2; ++kp) {
-        uint32_t bq[kSl][4];
-        {  // rows kappa = 32 kp + lane (8 per matrix), the warp's 8 points
-          const int row = 32 * kp + lane;
+            for (int ks = 0; ks < 4; ++ks) {
 #pragma unroll
-          for (int s = 0; s < kSl; ++s)
-            ldsm_x4_t(bq[s], &S.zq[s][0][0] + row * kTcPoints + ((wid ^ (row & 7)) << 3));
+              for (int sz = 0; sz < kSl; ++sz) {
+                const int ncol = sz == 0 ? kTcN * (kSl + 1) : kTcN * (kAcc - sz);
+                const uint32_t d = dcol + (uint32_t)(kTcN * sz);
+                const uint64_t a = adesc0 + (uint64_t)((sz * kASlice + 32 * ks) >> 4);
+                const uint64_t b = bdesc0 + (uint64_t)((32 * ks) >> 4);
+                if (ks == 0 && sz == 0)
+                  mma_bf16_set(d, a, b, idesc_bf16_f32(kTcPoints, ncol));
+                else
+                  mma_bf16_acc(d, a, b, idesc_bf16_f32(kTcPoints, ncol));
+              }
+            }
+            mma_commit(&bar[buf]);
+          }
+          __syncwarp();
         }
+      }
+      if (it > 0 && wid < kTcEpiWarps) {  // epilogue of the previous sub-tile
+        const int pb = (it - 1) & 1;
+        const bool ok = mbar_wait(&bar[pb], ph_mma[pb], kTcPollLimit);
+        ph_mma[pb] ^= 1u;
+        if (!ok) {
+          abort = 1;
+          atomicOr(status, kStatusTimeout);
+        } else {
+          fence_after_sync();
+          uint32_t v[kAcc][4];  // columns 4 h .. 4 h + 3: blocks 2 h, 2 h + 1 (real, imaginary)
+          const uint32_t ta = tbase + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)(pb * kTmemBuf + 4 * h);
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const int ks = 2 * kp + kk;
-          const int row = (lane & 7) + 8 * ((lane >> 3) & 1), ch = 2 * ks + (lane >> 4);
+          for (int tt = 0; tt < kAcc; ++tt) tmem_ld4(ta + (uint32_t)(kTcN * tt), v[tt]);
+          tmem_ld_wait();
+          const long long m0 = mb + (long long)kSub * (ts + 1);  // the previous sub-tile's first block
+          xh C[kTcBlkPerThr];
 #pragma unroll
-          for (int sa = 0; sa < kSl; ++sa) {
-            uint32_t a[4];
-            ldsm_x4(a, &S.aq[sa][0][0] + row * kTK + ((ch ^ (row & 7)) << 3));
+          for (int jj = 0; jj < kTcBlkPerThr; ++jj) {
+            C[jj] = xh_norm(0, 0, 0, 0, 0);
+            if (m0 + kTcBlkPerThr * h + jj < me && p < T.count) {
+              float ar[kAcc], ai[kAcc];
 #pragma unroll
-            for (int sz = 0; sz < kSl - sa; ++sz) mma_bf16(acc[sa + sz], a, bq[sz][2 * kk], bq[sz][2 * kk + 1]);
+              for (int tt = 0; tt < kAcc; ++tt) {
+                ar[tt] = __uint_as_float(v[tt][2 * jj]);
+                ai[tt] = __uint_as_float(v[tt][2 * jj + 1]);
+              }
+              u128 xr, xi;
+              int sr, si;
+              join_vals(ar, xr, sr);
+              join_vals(ai, xi, si);
+              // A' = F 2^(eR - 72), Z' = F 2^(eq - 72), and the kept pairs are
+              // 256^7 X: C = X 2^(eR + eq - 88) = X 2^(e - 126) with e = eR + eq + 38
+              C[jj] = xh_from128(xr, sr, xi, si, 38 + (long long)e_prev[jj] + eqp);
+            }
+          }
+          // H (relative to block 2 h of the sub-tile above, 8 blocks up) <- H W^8 + C_1 W + C_0:
+          // the two products are independent
+          xh T1 = C[1];
+          if (T1.x || T1.y) T1 = xh_mul(T1, w1);
+          if (H.x || H.y) H = xh_mul(H, w8);
+          H = xh_add(xh_add(H, T1), C[0]);
+          if ((ts + 1) % kTcFold == 0) {  // fold: Acc = Acc W^(8 kTcFold) + H (the folds are that far apart)
+            if (Acc.x || Acc.y) Acc = xint_mul(Acc, tp[p].Wf);
+            Acc = xint_add(Acc, xint_from_xh(H));
+            H = xh_norm(0, 0, 0, 0, 0);
           }
         }
+        fence_before_sync();
       }
-      __syncthreads();  // the A' tile is free for the next sub-tile
-      // combine: lane holds block m0 + g at points p0, p0 + 1
-      const bool inblk = m0 + g < me;
-      const int eRg = S.er[g];
 #pragma unroll
-      for (int pp = 0; pp < 2; ++pp) {
-        const int p = p0 + pp;
-        xh C = xh_norm(0, 0, 0, 0, 0);
-        if (inblk && p < T.count) {
-          u128 xr, xi;
-          int sr, si;
-          join_acc(acc, pp, xr, sr);
-          join_acc(acc, 2 + pp, xi, si);
-          C = xh_from128(xr, sr, xi, si, 49 + (long long)eRg + S.eq[p]);
-        }
-        xh &H = pp ? H1 : H0;
-        if (H.x || H.y) H = xh_mul(H, S.w8[p]);
-        H = xh_add(H, C);
-      }
+      for (int q = 0; q < kTcBlkPerThr; ++q) e_prev[q] = e_cur[q];
     }
-    // ---- V = sum_g W^g H_g: the lanes' H into shared memory (over the Z'
-    // tiles, no longer read), then one thread per point, Horner over g in
-    // 64-bit mantissas (seven steps: within 2^-57 of the terms' sum)
-    xh *hs = reinterpret_cast<xh *>(&S.zq[0][0][0]);  // [point][g]
-    hs[p0 * kSub + g] = H0;
-    hs[(p0 + 1) * kSub + g] = H1;
+    if (__syncthreads_or(abort)) break;
+    // ---- V = A_0 + W^2 (A_1 + W^2 (A_2 + W^2 A_3)) per point (the last sub-tile, 0,
+    // ended with a fold), into the item's slot
+    if (wid < kTcEpiWarps && h > 0) sHx[(h - 1) * kTcPoints + p] = xh_from_xint(Acc);
     __syncthreads();
-    if (tid < T.count) {
-      const xh W = S.w1[tid];
-      xh V = hs[tid * kSub + kSub - 1];
-      for (int gg = kSub - 2; gg >= 0; --gg) {
-        if (V.x || V.y) V = xh_mul(V, W);
-        V = xh_add(V, hs[tid * kSub + gg]);
+    if (wid < kTcEpiWarps && h == 0 && p < T.count) {
+      const xint W2 = tp[p].W[1];
+      xint V = xint_from_xh(sHx[(kTcPerPoint - 2) * kTcPoints + p]);
+      for (int q = kTcPerPoint - 2; q >= 0; --q) {
+        if (V.x || V.y) V = xint_mul(V, W2);
+        V = xint_add(V, q > 0 ? xint_from_xh(sHx[(q - 1) * kTcPoints + p]) : Acc);
       }
-      slots[(size_t)item * kTcPoints + tid] = xint_from_xh(V);
+      slots[(size_t)item * kTcPoints + p] = V;
     }
     __syncthreads();  // shared memory is reused by the next item
   }
+  fence_before_sync();
+  __syncthreads();
+  if (wid == kTcMmaWarp) tmem_dealloc(tbase, kTmemCols);
 }
 
 // b^n (n >= 1) by binary powering
@@ -738,21 +870,24 @@ __device__ __forceinline__ xint xint_pow_x(xint b, long long n) {
 // W^chunk = (W^8)^(chunk / 8) from the powers k_tc_pre stored.  Tiles of at
 // most kFinOneLaneItems items take one thread per point (L = 1: most tiles
 // have one item, and the power z^(kb + v) is the thread's main work);
-// longer ones eight (L = 8): threads q < 7 take a contiguous seventh of the
+// longer ones eight (L = 8, blocks of half a tile): threads q < 7 take a contiguous seventh of the
 // items by Horner in W^chunk and scale it by (W^chunk)^(its first item),
 // thread 7 computes z^(kb + v) meanwhile, and the parts are added by
 // shuffles.  Each launch skips the other's tiles.
 constexpr int kFinOneLaneItems = 4;
-template <int L>
-__global__ void __launch_bounds__(L * kTcPoints)
+// A block takes PPB points of a tile (kTcPoints / PPB blocks per tile).
+template <int L, int PPB>
+__global__ void __launch_bounds__(L * PPB)
     k_tc_finalize(DevPoly P, const PointRec *__restrict__ rec, const TcTile *__restrict__ tiles,
                   const TcPoint *__restrict__ pts, const int32_t *__restrict__ item_base, const uint32_t *cnt,
                   const xint *__restrict__ slots, fpe_xc64 *__restrict__ out, int32_t *nterms,
                   int32_t *bits_lost) {
-  const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x / L, q = threadIdx.x % L;
+  constexpr int kParts = kTcPoints / PPB;
+  const int ntiles = (int)cnt[kCntTcTiles], q = threadIdx.x % L;
   constexpr int qpow = L - 1;            // the thread that computes z^(kb + v)
   constexpr int nh = L > 1 ? L - 1 : 1;  // threads that take items
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int u = blockIdx.x; u < ntiles * kParts; u += gridDim.x) {
+    const int t = u / kParts, p = (u % kParts) * PPB + (int)threadIdx.x / L;
     const int base = item_base[t], nit = item_base[t + 1] - base;
     if ((L == 1) != (nit <= kFinOneLaneItems)) continue;  // the other launch's tile
     const TcTile T = tiles[t];
@@ -824,7 +959,6 @@ static int tc_num_sms() {
 static int64_t tc_groups_max(int64_t n) { return (n + kTcPoints - 1) / kTcPoints + kTcMaxPieces; }
 static int64_t tc_tiles_max(int64_t n) { return (n + kTcPoints - 1) / kTcPoints + tc_groups_max(n); }
 static int64_t tc_items_cap(int64_t n) { return tc_tiles_max(n) + (int64_t)tc_num_sms() * kTcItemsPerSm; }
-constexpr int kTcCtasPerSm = 2;
 
 bool tc_enabled(const fpe_poly_s *P, bool complex_points) {
   (void)complex_points;
@@ -880,7 +1014,7 @@ static fpe_status tc_set_smem_attrs() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_tc_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tc_sum, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tensor-core kernels)");
@@ -928,7 +1062,7 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
                                                                        (TcTau *)w.tc_taus, cnt);
     k_tc_pre<<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles,
                                                                     (TcPoint *)w.tc_points,
-                                                                    (const TcTau *)w.tc_taus, (uint16_t *)w.tc_z, cnt);
+                                                                    (const TcTau *)w.tc_taus, (unsigned char *)w.tc_z, cnt);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FPE_OK : cuda_fail(e, "tensor-core plan launch");
@@ -943,16 +1077,16 @@ fpe_status launch_tc_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, 
   if (s != FPE_OK) return s;
   {
     ProfScope ps("k_tc_sum", st);
-    k_tc_sum<<<tc_num_sms() * kTcCtasPerSm, kTcThreads, sizeof(TcSmem), st>>>(
+    k_tc_sum<<<tc_num_sms(), kTcThreads, kTcSmemBytes, st>>>(
         P->dev, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, (const TcTau *)w.tc_taus,
-        (const uint4 *)w.tc_z, w.tc_item_base, w.tc_item_tile, cnt, (xint *)w.tc_slots);
+        (const unsigned char *)w.tc_z, w.tc_item_base, w.tc_item_tile, cnt, (xint *)w.tc_slots, P->d_status);
   }
   {
     ProfScope ps("k_tc_finalize", st, 2);  // eight- and one-thread launches
-    k_tc_finalize<8><<<std::min(tm, tc_num_sms() * 2), 8 * kTcPoints, 0, st>>>(
+    k_tc_finalize<8, kTcPoints / 2><<<std::min(2 * tm, tc_num_sms() * 4), 8 * (kTcPoints / 2), 0, st>>>(
         P->dev, w.rec, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, w.tc_item_base, cnt,
         (const xint *)w.tc_slots, out, nterms, bits_lost);
-    k_tc_finalize<1><<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(
+    k_tc_finalize<1, kTcPoints><<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(
         P->dev, w.rec, (const TcTile *)w.tc_tiles, (const TcPoint *)w.tc_points, w.tc_item_base, cnt,
         (const xint *)w.tc_slots, out, nterms, bits_lost);
   }

@@ -28,16 +28,21 @@ xint pow_x(xint b, long long n) {  // b^n, n >= 1, by binary powering (as the ke
   return r;
 }
 
+constexpr int kFold = 16;  // sub-tiles between the 128-bit folds of a thread's Horner value
+
+constexpr int kPer = 4;  // threads per point, each taking blocks 2 h, 2 h + 1 of a sub-tile of 8
+
 struct Point {
   int sd_re[kTB][kSl], sd_im[kTB][kSl];  // signed Z' digits of u^i
-  int eq;                                // Z' = F 2^(eq - 70)
+  int eq;                                // Z' = F 2^(eq - 72)
   xint W[4];
   xh w1, w8;
+  xint wf;  // W^(8 kFold)
 };
 
 void digits(u128 F, int neg, int (&d)[kSl]) {
   uint32_t x[kSl];
-  bchunks70(F, x);
+  bchunks72(F, x);
   const DigitSign s = digit_sign((uint32_t)neg);
   for (int j = 0; j < kSl; ++j) d[j] = (int)fmaf(tc_bitsf(x[j]), s.s, s.k);
 }
@@ -82,9 +87,9 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
     xh cur = xh_norm(1ull << 63, 0, 0, 0, 0);
     for (int i = 0; i < kTB; ++i) {
       if (i > 0) cur = xh_mul(cur, uh);
-      const int sr = eQ + 1 - 7 - (int)cur.e;
-      digits(shift_to70((u128)cur.x, sr), cur.sx, P.sd_re[i]);
-      digits(shift_to70((u128)cur.y, sr), cur.sy, P.sd_im[i]);
+      const int sr = eQ + 1 + 63 - 72 - (int)cur.e;
+      digits(shift_to72((u128)cur.x, sr), cur.sx, P.sd_re[i]);
+      digits(shift_to72((u128)cur.y, sr), cur.sy, P.sd_im[i]);
     }
     xint u32 = u;
     for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
@@ -93,19 +98,30 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
     P.eq = eQ + 1;
     P.w1 = xh_from_xint(P.W[0]);
     P.w8 = xh_from_xint(P.W[3]);
+    P.wf = P.W[3];
+    for (int q = 1; (1 << q) <= kFold; ++q) P.wf = xint_sqr(P.wf);
   }
 
-  // k_tc_sum, one work item at a time
+  // k_tc_sum, one work item at a time: per point four threads h = 0..3, each
+  // taking blocks 2 h, 2 h + 1 of every sub-tile of 8, from the top down, by
+  // H <- H W^8 + C_1 W + C_0 in 64-bit mantissas, folded into a 128-bit value
+  // every kFold sub-tiles; V = A_0 + W^2 (A_1 + W^2 (A_2 + W^2 A_3))
   const long long nit = (nblk + chunk - 1) / chunk;
   xint *slot = new xint[nit * npts];
+  const xint zero0 = xint_norm(0, 0, 0, 0, 0);
   for (long long it = 0; it < nit; ++it) {
     const long long mb = mlo + it * chunk, me = std::min(mlo + nblk, mb + chunk);
     const int nsub = (int)((me - mb + kSub - 1) / kSub);
-    xh *H = new xh[npts * kSub];
-    for (int q = 0; q < npts * kSub; ++q) H[q] = xh_norm(0, 0, 0, 0, 0);
+    xh *H = new xh[npts * kPer];
+    xint *A = new xint[npts * kPer];
+    xh *Cb = new xh[npts * kSub];  // the current sub-tile's block values
+    for (int q = 0; q < npts * kPer; ++q) {
+      H[q] = xh_norm(0, 0, 0, 0, 0);
+      A[q] = zero0;
+    }
     for (int ts = nsub - 1; ts >= 0; --ts) {
       const long long m0 = mb + (long long)kSub * ts;
-      for (int g = 0; g < kSub; ++g) {
+      for (int g = kSub - 1; g >= 0; --g) {
         const long long m = m0 + g;
         // A' digits of block m: lane i = term k = 32 m + i
         int ad_re[kTB][kSl], ad_im[kTB][kSl];
@@ -136,54 +152,68 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
         }
         const int eR = top == INT_MIN ? 0 : top + 2;
         for (int i = 0; i < kTB; ++i) {
-          digits(pr[i] ? shift_to70(pr[i], eR - 70 - er_[i]) : (u128)0, brs[i] < 0.0, ad_re[i]);
-          digits(pi[i] ? shift_to70(pi[i], eR - 70 - ei_[i]) : (u128)0, bis[i] < 0.0, ad_im[i]);
+          digits(pr[i] ? shift_to72(pr[i], eR - 72 - er_[i]) : (u128)0, brs[i] < 0.0, ad_re[i]);
+          digits(pi[i] ? shift_to72(pi[i], eR - 72 - ei_[i]) : (u128)0, bis[i] < 0.0, ad_im[i]);
         }
         for (int p = 0; p < npts; ++p) {
           const Point &P = pts[p];
           // out_re = sum_i A'_re Z'_re - A'_im Z'_im, out_im = sum_i A'_im Z'_re + A'_re Z'_im, per digit pair
-          float acc_re[kSl][4], acc_im[kSl][4];
-          for (int t = 0; t < kSl; ++t)
-            for (int q = 0; q < 4; ++q) acc_re[t][q] = acc_im[t][q] = 0.0f;
-          for (int t = 0; t < kSl; ++t) {
+          float acc_re[kAcc], acc_im[kAcc];
+          for (int t = 0; t < kAcc; ++t) {
             long long sre = 0, sim = 0;
-            for (int s = 0; s <= t; ++s)
+            for (int s = 0; s <= t; ++s) {
+              if (s >= kSl || t - s >= kSl) continue;
               for (int i = 0; i < kTB; ++i) {
                 sre += (long long)ad_re[i][s] * P.sd_re[i][t - s] - (long long)ad_im[i][s] * P.sd_im[i][t - s];
                 sim += (long long)ad_im[i][s] * P.sd_re[i][t - s] + (long long)ad_re[i][s] * P.sd_im[i][t - s];
               }
-            acc_re[t][0] = (float)sre;  // exact: below 2^22
-            acc_im[t][0] = (float)sim;
+            }
+            acc_re[t] = (float)sre;  // exact: below 2^23.2
+            acc_im[t] = (float)sim;
           }
           xh C = xh_norm(0, 0, 0, 0, 0);
           if (m < me) {
             u128 xr, xi;
             int sr, si;
-            join_acc(acc_re, 0, xr, sr);
-            join_acc(acc_im, 0, xi, si);
-            C = xh_from128(xr, sr, xi, si, 49 + (long long)eR + P.eq);
+            join_vals(acc_re, xr, sr);
+            join_vals(acc_im, xi, si);
+            C = xh_from128(xr, sr, xi, si, 38 + (long long)eR + P.eq);
           }
-          xh &h = H[p * kSub + g];
-          if (h.x || h.y) h = xh_mul(h, P.w8);
-          h = xh_add(h, C);
+          Cb[p * kSub + g] = C;
         }
       }
+      for (int p = 0; p < npts; ++p)
+        for (int hh = 0; hh < kPer; ++hh) {
+          xh &h = H[p * kPer + hh];
+          xh T1 = Cb[p * kSub + 2 * hh + 1];
+          if (T1.x || T1.y) T1 = xh_mul(T1, pts[p].w1);
+          if (h.x || h.y) h = xh_mul(h, pts[p].w8);
+          h = xh_add(xh_add(h, T1), Cb[p * kSub + 2 * hh]);
+          if (ts % kFold == 0) {  // fold
+            xint &a = A[p * kPer + hh];
+            if (a.x || a.y) a = xint_mul(a, pts[p].wf);
+            a = xint_add(a, xint_from_xh(h));
+            h = xh_norm(0, 0, 0, 0, 0);
+          }
+        }
     }
-    for (int p = 0; p < npts; ++p) {  // V = sum_g W^g H_g
-      xh V = H[p * kSub + kSub - 1];
-      for (int g = kSub - 2; g >= 0; --g) {
-        if (V.x || V.y) V = xh_mul(V, pts[p].w1);
-        V = xh_add(V, H[p * kSub + g]);
+    for (int p = 0; p < npts; ++p) {  // V = A_0 + W^2 (A_1 + W^2 (A_2 + W^2 A_3)), A_1..3 passed in 64 bits
+      xint V = xint_from_xh(xh_from_xint(A[p * kPer + kPer - 1]));
+      for (int q = kPer - 2; q >= 0; --q) {
+        if (V.x || V.y) V = xint_mul(V, pts[p].W[1]);
+        V = xint_add(V, q > 0 ? xint_from_xh(xh_from_xint(A[p * kPer + q])) : A[p * kPer]);
       }
-      slot[it * npts + p] = xint_from_xh(V);
+      slot[it * npts + p] = V;
     }
     delete[] H;
+    delete[] A;
+    delete[] Cb;
   }
 
-  // k_tc_finalize: one thread per point up to 4 items, else 7 item threads + a butterfly over 8
+  // k_tc_finalize: one thread per point up to 4 items, else 3 item threads + a butterfly over 4
   const xint zero = xint_norm(0, 0, 0, 0, 0);
   for (int p = 0; p < npts; ++p) {
-    const int L = nit <= 4 ? 1 : 8, nh = L > 1 ? L - 1 : 1;
+    const int L = nit <= 4 ? 1 : 4, nh = L > 1 ? L - 1 : 1;
     const long long per = (nit + nh - 1) / nh;
     const xint Wc = nit > 1 ? pow_x(pts[p].W[3], chunk / 8) : zero;
     xint part[8];
