@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "polynomial evaluations/s at d=2^20 (FPE vs GPU Horner, same accuracy), % of roofline"
+TC_FLOPS_PER_SUBTILE = 2.0 * 128 * 64 * 880
 UNIT = "evals/s"
 
 
@@ -150,20 +151,84 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def oracle_cpu_baseline(wl, n_sample: int):
-    """Algorithm A_p restated by the CPU oracle on a bounded sample of points."""
+def oracle_cpu_baseline(wl, n_sample: int, variants: bool = False):
+    """Algorithm A_p restated by the CPU oracle on a bounded sample of points, on
+    all host cores.  With variants, also on one core, and the plain FP64
+    restatement of the window sums (hardware floats, the paper's p = 53 runs)
+    on all cores and on one core."""
     import oracle
     t0 = time.perf_counter()
     pre = oracle.precondition(wl.coeffs, wl.p)
     t_pre = time.perf_counter() - t0
     zr, zi = wl.points.re[:n_sample], wl.points.im[:n_sample]
     oracle.fpe_eval(pre, zr[:16], zi[:16])  # warm-up (builds the C part)
-    t0 = time.perf_counter()
-    oracle.fpe_eval(pre, zr, zi)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n_sample} of the workload's points (Alg. A_p windows + extended double-double "
-                      f"window sums); preconditioning {t_pre:.2f} s not included"}
+    cores = oracle.num_threads()
+
+    def timed(fn, n):
+        t = time.perf_counter()
+        fn(pre, zr[:n], zi[:n])
+        return n / (time.perf_counter() - t)
+
+    res = {"value": timed(oracle.fpe_eval, n_sample), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n_sample} of the workload's points (Alg. A_p windows + extended double-double "
+                     f"window sums); preconditioning {t_pre:.2f} s not included"}
+    if variants:
+        n1 = max(64, n_sample // max(cores, 1))
+        oracle.set_threads(1)
+        try:
+            res["single_core"] = {"value": timed(oracle.fpe_eval, n1), "cores": 1, "sample": f"{n1} points"}
+            res["fp64_restatement_single_core"] = {
+                "value": timed(oracle.fpe_eval_fp64, n1), "cores": 1, "sample": f"{n1} points",
+                "kind": "plain FP64 CPU restatement of Alg. A_p (FP64 Horner over each window, z^l in "
+                        "double-double)"}
+        finally:
+            oracle.set_threads(cores)
+        res["fp64_restatement"] = {"value": timed(oracle.fpe_eval_fp64, n_sample), "cores": cores,
+                                   "sample": f"{n_sample} points", "kind": "plain FP64 CPU restatement of Alg. A_p"}
+    return res
+
+
+def workload_legs(F, torch, st):
+    """Evaluations/s on the benchmark's other workload shapes (the default
+    configuration of fpe_eval; the d = 1000 one also with the tensor path off)."""
+    import workloads as W
+    legs = {}
+    for name, make in (("unit_square_d1000", lambda: W.unit_square_d1000()),
+                       ("inverse_factorial_d1e5", lambda: W.inverse_factorial_d1e5(n_points=1 << 20)),
+                       ("sparse_d2pow22", lambda: W.sparse_d2pow22(n_points=1 << 20))):
+        wl = make()
+        t0 = time.perf_counter()
+        P = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, wl.coeffs.e2, wl.p)
+        t_pre = time.perf_counter() - t0
+        zr = torch.from_numpy(wl.points.re).cuda()
+        zi = None if wl.points.im is None else torch.from_numpy(wl.points.im).cuda()
+        n = wl.points.n
+        out = F.empty_out(n)
+        nt = torch.empty(n, dtype=torch.int32, device="cuda")
+        res = {"degree": wl.coeffs.n_coef - 1, "points": n, "precondition_ms": t_pre * 1e3}
+        for label, thr in (("default", None), ("tensor_off", 0)):
+            if thr is not None and name != "unit_square_d1000":
+                continue
+            if thr is not None:
+                F.fpe_set_tensor_path(P, thr)
+            for _ in range(2):
+                F.fpe_eval(P, zr, zi, out, nt)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            a.record(st)
+            for _ in range(reps):
+                F.fpe_eval(P, zr, zi, out, nt)
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            res[label] = {"evals_per_s": n / (ms * 1e-3), "ms_per_eval": ms,
+                          "avg_kept_terms": float(nt.double().mean().item()),
+                          "tensor_stats": F.fpe_tensor_stats(P)}
+        F.fpe_sync(P)
+        legs[name] = res
+        del P, zr, zi, out, nt
+    return legs
 
 
 def batched_leg(F, torch, st):
@@ -361,17 +426,16 @@ def main():
         fl_tc_alg = 8.0 * float(nt[tc_mask].sum())
         fma_peak = F.fpe_measure_fma_peak(64, 5)
         fp64_peak_tflops = 2.0 * fma_peak / 1e12
-        mma_peak_tflops = F.fpe_measure_mma_peak(5) / 1e12
         bf16_peak, bf16_src = measured_bf16_peak()
-        # the tensor-core kernel's own work: each MMA sub-tile is 8 warps x 220
-        # mma.sync m16n8k16 (4096 flop each) of exact 7-bit slice products
-        fl_tc = float(tcs["subtiles"]) * 8 * 220 * 4096
+        # the tensor-core kernel's own work: an MMA sub-tile (8 blocks of 32 terms by a
+        # tile's 128 point rows) is 4 k-steps x 10 tcgen05.mma, M = 128, K = 16,
+        # N = 16 (10 - s) for Z' digit slice s: 2 x 128 x 64 x 880 flop of exact
+        # 7-bit digit products
+        fl_tc = float(tcs["subtiles"]) * TC_FLOPS_PER_SUBTILE
         kern = {"k_sum_short": (k_short / max(n_short, 1), fl_short),
                 "k_sum_groups": (k_long / max(n_long, 1), fl_long),
                 "k_tc_sum": (k_tc / max(n_tc, 1), fl_tc)}
         dom = max(kern, key=lambda k: kern[k][0])
-        ms, fl = kern[dom]
-        traffic, traffic_note = measured_traffic(dom)
         share = {k: (v[0] * args.steps) / max(k_all, 1e-9) for k, v in kern.items()}
         step_s = float(step_ms.mean()) * 1e-3
         fp64_equiv = {"algorithmic_flops_per_step": fl_short + fl_long + fl_tc_alg,
@@ -380,29 +444,42 @@ def main():
                       "frac_of_fp64_peak": (fl_short + fl_long + fl_tc_alg) / step_s / 1e12 / fp64_peak_tflops,
                       "note": "8 flop per kept complex term (the paper's count) over the whole step, against the "
                               "measured FP64 FMA peak; above 1 because the long windows run on the tensor cores"}
-        if dom == "k_tc_sum":
-            achieved = fl / (ms * 1e-3) / 1e12
-            roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": bf16_peak,
-                        "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": traffic,
-                        "traffic_source": traffic_note, "peak_source": bf16_src,
-                        "mma_sync_peak": mma_peak_tflops, "frac_of_mma_sync_peak": achieved / mma_peak_tflops,
-                        "mma_sync_peak_source": "measured: fpe_measure_mma_peak on this GPU in this run",
-                        "share": share, "flops_per_launch": fl, "launch_ms": ms,
-                        "algorithmic_flops": "bf16 tensor flops of the exact slice products: 55 slice pairs x "
-                                             "4 real products per complex term, 2 flop per multiply-add, over "
-                                             "the union of each tile's windows (tensor_stats.subtiles x 7.2e6)",
-                        "tensor_stats": tcs, "fp64_equivalent": fp64_equiv}
-        else:
-            achieved = fl / (ms * 1e-3) / 1e12
-            roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak_tflops,
-                        "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
-                        "traffic_source": traffic_note,
-                        "peak_source": "measured: fpe_measure_fma_peak(64) on this GPU in this run (FP64 FMA x2)",
-                        "share": share, "flops_per_launch": fl, "launch_ms": ms,
-                        "algorithmic_flops": "8 per kept complex term (4 FMA: one complex multiply-add of "
-                                             "Horner's scheme on G_p cap [l, r])",
-                        "fma_issued_per_term": "4 at or above the peak term, 5 below it (blocks of four)",
-                        "fp64_equivalent": fp64_equiv}
+
+        def tensor_entry():
+            ms, fl = kern["k_tc_sum"]
+            traffic, traffic_note = measured_traffic("k_tc_sum")
+            achieved = fl / max(ms * 1e-3, 1e-12) / 1e12
+            return {"bound": "tensor", "kernel": "k_tc_sum", "achieved": achieved, "peak": bf16_peak,
+                    "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": traffic,
+                    "traffic_source": traffic_note, "peak_source": bf16_src, "share": share,
+                    "flops_per_launch": fl, "launch_ms": ms,
+                    "algorithmic_flops": "bf16 tensor flops of the exact digit products as issued: per MMA "
+                                         "sub-tile 40 tcgen05.mma (M 128, K 16, N 16 (10 - s)), "
+                                         "tensor_stats.subtiles x %.4g" % TC_FLOPS_PER_SUBTILE,
+                    "method_work": {"flops_per_launch": fl_tc_alg,
+                                    "tflops": fl_tc_alg / max(ms * 1e-3, 1e-12) / 1e12,
+                                    "frac_of_fp64_peak": fl_tc_alg / max(ms * 1e-3, 1e-12) / 1e12 / fp64_peak_tflops,
+                                    "note": "the paper's 8 flop per kept complex term of the points this kernel "
+                                            "sums, per launch time, against the measured FP64 FMA peak"},
+                    "tensor_stats": tcs}
+
+        def fp64_entry(name):
+            ms, fl = kern[name]
+            traffic, traffic_note = measured_traffic(name)
+            achieved = fl / max(ms * 1e-3, 1e-12) / 1e12
+            return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": fp64_peak_tflops,
+                    "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": traffic,
+                    "traffic_source": traffic_note,
+                    "peak_source": "measured: fpe_measure_fma_peak(64) on this GPU in this run (FP64 FMA x2)",
+                    "share": share, "flops_per_launch": fl, "launch_ms": ms,
+                    "algorithmic_flops": "8 per kept complex term (4 FMA: one complex multiply-add of "
+                                         "Horner's scheme on G_p cap [l, r])",
+                    "fma_issued_per_term": "4 at or above the peak term, 5 below it (blocks of four)"}
+
+        roofline = tensor_entry() if dom == "k_tc_sum" else fp64_entry(dom)
+        roofline["fp64_equivalent"] = fp64_equiv
+        if dom != "k_tc_sum" and n_tc:
+            extras["roofline_tensor_kernel"] = tensor_entry()
         extras["roofline"] = roofline
         extras["gpu_launches"] = int(launches)
         extras["avg_kept_terms"] = float(nt.mean())
@@ -427,19 +504,27 @@ def main():
                          "d2h_bytes_per_step": 24 * n}
 
         if not args.no_extras:
-            # GPU Horner baselines over all d+1 terms (subset of points: per-point work is fixed)
-            for comp, m in ((False, 1 << 14), (True, 1 << 12)):
+            # GPU Horner baselines over all d+1 terms, one thread per point, on enough
+            # points to occupy every SM (per-point work is fixed, so evaluations/s
+            # do not depend on how many points are timed)
+            for comp, m in ((False, 1 << 17), (True, 1 << 15)):
                 sub_r, sub_i = zr[:m].contiguous(), zi[:m].contiguous()
                 o2 = F.empty_out(m)
-                F.fpe_horner(P, sub_r, sub_i, compensated=comp, out=o2)
+                F.fpe_horner(P, sub_r[:4096].contiguous(), sub_i[:4096].contiguous(), compensated=comp,
+                             out=o2[:4096])
                 torch.cuda.synchronize()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(st)
                 F.fpe_horner(P, sub_r, sub_i, compensated=comp, out=o2)
                 b.record(st)
                 torch.cuda.synchronize()
-                extras["horner_compensated_evals_per_s" if comp else "horner_plain_evals_per_s"] = \
-                    m / (a.elapsed_time(b) * 1e-3)
+                sec = a.elapsed_time(b) * 1e-3
+                key = "horner_compensated" if comp else "horner_plain"
+                extras[key + "_evals_per_s"] = m / sec
+                # the plain scheme's count: 8 flop per complex term, d + 1 terms per point
+                fl = 8.0 * (args.degree + 1) * m
+                extras[key + "_fp64"] = {"points": m, "seconds": sec, "flops_8_per_term": fl,
+                                         "frac_of_fp64_peak": fl / sec / 1e12 / fp64_peak_tflops}
             # accuracy on a sample against the oracle's extended-precision Horner
             import oracle
             sample = np.unique(np.concatenate([np.arange(48), np.argsort(-L)[:16]]))
@@ -473,7 +558,8 @@ def main():
             torch.cuda.synchronize()
             extras["fpe_fp32_p24_evals_per_s"] = n / (a.elapsed_time(b) * 1e-3)
             extras["fpe_fp32_p24_avg_kept_terms"] = float(nt32.double().mean().item())
-            extras["cpu_baseline"] = oracle_cpu_baseline(wl, 4096)
+            extras["cpu_baseline"] = oracle_cpu_baseline(wl, 4096, variants=True)
+            extras["workloads"] = workload_legs(F, torch, st)
             extras["batched"] = batched_leg(F, torch, st)
             extras["differentiation"] = differentiation_leg(F, torch, st)
 

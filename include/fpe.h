@@ -260,11 +260,13 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
  * counterpart).  In the FP64 default mode (not FPE_FP32, not FPE_ACCURATE),
  * fpe_eval sums every window of at least min_window terms that lies inside
  * one of the polynomial's longest (up to four) coefficient pieces with an
- * integer cover slope on the bf16 tensor cores: coefficients and point
- * powers are cut into exact 7-bit digits whose products are added exactly,
- * and blocks of 32 terms are combined in 64-bit (within a work item) and
- * 128-bit (across work items) fixed point.  Points are grouped up to 64 at
- * a time by log2|z|; a group also sums the terms of its neighbours' windows
+ * integer cover slope on the bf16 tensor cores (tcgen05.mma with fp32
+ * accumulators in tensor memory): coefficients and point powers are cut into
+ * exact 7-bit digits whose products are added exactly, and blocks of 32
+ * terms are combined in 64-bit mantissas (folded into 128 bits every 128
+ * blocks) and 128-bit fixed point across work items.  Points are grouped
+ * about 112 at a time by log2|z| into tiles of up to 128; a group also sums
+ * the terms of its neighbours' windows
  * (all of them below the window threshold), and a group whose |z| spread is
  * too wide for one shared scaling goes back to the FP64 kernels.  The error
  * stays below 2^-53.5 sum |a_k||z|^k.
@@ -282,10 +284,11 @@ fpe_status fpe_set_tensor_path(fpe_poly_t P, int64_t min_window);
 fpe_status fpe_get_tensor_path(fpe_poly_t P, int64_t *min_window, int32_t *n_pieces);
 /*
  * fpe_tensor_stats: what the tensor-core path did in the handle's last
- *   fpe_eval, in stats[0..5]: points it summed, tiles (up to 64 points that
+ *   fpe_eval, in stats[0..5]: points it summed, tiles (up to 128 points that
  *   share a tilt and a block range), work items, MMA sub-tiles (8 blocks of
- *   32 terms by a tile's points; each is 8 warps x 220 mma.sync of
- *   m16n8k16, i.e. 7.2e6 bf16 flop), blocks per work item, and the points
+ *   32 terms by a tile's 128 point rows; each is 40 tcgen05.mma of M 128,
+ *   K 16, N 16 (10 - s) for digit slice s, i.e. 1.44e7 bf16 flop), blocks
+ *   per work item, and the points
  *   handed back to the FP64 kernels (their group's |z| spread too wide).
  *   All zero when the path did not run.  Waits for the work queued on
  *   cuda_stream.  FPE_ERR_INVALID_ARG for NULL arguments or n < 6.

@@ -146,8 +146,8 @@ __device__ __forceinline__ uint32_t bucket_of(double lam, int flags) {
 // Bucket of a point whose window [lo, hi] (trimmed) qualifies for the
 // tensor-core sums: at least tc_min_window terms inside one tensor-core piece
 // r.  Bins kNumBins + r kTcBinsPerPiece + [0, kTcBinsPerPiece) order mu =
-// lambda + beta logarithmically (256 bins per binade of |mu| over
-// [2^-24, 2^8], negative mu first), so consecutive points share windows.
+// lambda + beta logarithmically (kTcBinsPerBinade bins per binade of |mu|
+// over [2^-24, 2^8], negative mu first), so consecutive points share windows.
 __device__ __forceinline__ bool tc_bucket(const DevPoly &P, long long lo, long long hi, double lam,
                                           long long tc_min_window, uint32_t &key) {
   if (hi - lo + 1 < tc_min_window) return false;
@@ -161,7 +161,7 @@ __device__ __forceinline__ bool tc_bucket(const DevPoly &P, long long lo, long l
   const double mu = lam + (double)P.piece_beta[j];
   const float a = (float)fabs(mu);
   int h = 0;
-  if (a >= 0x1p-24f) h = min((int)((log2f(a) + 24.0f) * 256.0f), kTcBinsPerPiece / 2 - 1);
+  if (a >= 0x1p-24f) h = min((int)((log2f(a) + 24.0f) * (float)kTcBinsPerBinade), kTcBinsPerPiece / 2 - 1);
   const int b = mu < 0.0 ? kTcBinsPerPiece / 2 - 1 - h : kTcBinsPerPiece / 2 + h;
   key = (uint32_t)(kNumBins + r * kTcBinsPerPiece + b);
   return true;

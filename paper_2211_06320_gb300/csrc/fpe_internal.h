@@ -78,7 +78,9 @@ struct Tuning {
 // (at most kTcMaxPieces per polynomial), on a logarithmic scale of
 // mu = log2|z| + beta, so consecutive points have nearly equal windows.
 constexpr int kTcMaxPieces = 4;
-constexpr int kTcBinsPerPiece = 16384;
+constexpr int kTcBinsPerPiece = 32768;
+constexpr int kTcBinsPerBinade = 512;  // over |mu| in [2^-24, 2^8], negative mu first
+static_assert(32 * kTcBinsPerBinade <= kTcBinsPerPiece / 2, "32 binades of |mu| on each side of 0");
 constexpr int kTcBins = kTcMaxPieces * kTcBinsPerPiece;
 constexpr int kTcMinPieceLen = 64;  // shorter pieces never get the tensor path
 constexpr int kTcPoints = 128;      // points per tile: the M = 128 rows of one tcgen05 MMA

@@ -19,14 +19,15 @@
 //   2^(62 |mu - c|) of the block's largest term).
 //
 //   Slices.  Each component of A' (per block) and of Z' (per point) is a
-//   71-bit fixed-point number relative to a power of two above its block's or
-//   point's largest component, written as nine balanced base-256 digits
-//   d_0..d_8 (|d| <= 128, exact in bf16).  A digit product is at most 2^14 in
-//   magnitude, a 64-long dot product of digits at most 2^20, and the at most
-//   nine digit pairs with the same s + s' = t add up below 2^23.2: fp32
-//   accumulation is exact.  Pairs with t <= 9 are kept (53 of 81); the
-//   dropped ones and the truncation leave an error below 2^-70 per product
-//   relative to the scales.
+//   69-bit fixed-point number relative to a power of two above its block's or
+//   point's largest component, written as ten balanced base-128 digits d_0..d_9
+//   (|d| <= 64, exact in bf16).  A digit product is at most 2^12 in
+//   magnitude, a 64-long dot product of digits at most 2^18, and the at most
+//   ten digit pairs with the same s + s' = t add up below 2^22: fp32
+//   accumulation is exact, and adding 1.5 2^23 reads an accumulator back as
+//   an integer.  Pairs with t <= 9 are kept (55 of 100); the dropped ones and
+//   the truncation leave an error below 2^-66 per product relative to the
+//   scales.
 //
 //   Combination.  The ten integer accumulators of each (block, point) are
 //   joined into a 128-bit integer; the blocks of a work item are combined by
@@ -41,15 +42,15 @@
 // rows of A are the tile's 128 points, each row one digit slice of the point's
 // Z' over the contraction index kappa = the 32 terms' (real, imaginary)
 // powers (K = 64, four k-steps).  B stacks, for a sub-tile of 8 blocks, the
-// digit slices sa = 0..8 of A' (and one slice of zeros): row 16 sa + 2j + c is
-// block j's real row (c = 0) or imaginary row (c = 1) of slice sa,
+// digit slices sa = 0..9 of A': row 16 sa + 2j + c is block j's real row
+// (c = 0) or imaginary row (c = 1) of slice sa,
 //   real row (A'_re | -A'_im),  imaginary row (A'_im | A'_re),
 // so that out_re = sum_i (A'_re Z'_re - A'_im Z'_im) and
 // out_im = sum_i (A'_im Z'_re + A'_re Z'_im).  One MMA takes Z' slice s as A
-// and the first N_s rows of B (all slices sa with s + sa <= 9, N_s = 16 (10 - s),
-// for s = 0 also the zero slice: N_0 = 160) into the accumulator columns
-// 16 (s + sa) + 2j + c: each column block t = s + sa collects exactly the digit
-// pairs of its diagonal, nine MMAs per k-step instead of one per pair.
+// and the first N_s = 16 (10 - s) rows of B (the slices sa with s + sa <= 9)
+// into the accumulator columns 16 (s + sa) + 2j + c: each column block
+// t = s + sa collects exactly the digit pairs of its diagonal, ten MMAs per
+// k-step instead of one per pair.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,15 +68,20 @@ namespace {
 constexpr int kTK = 2 * kTB;                 // contraction length (re, im per term)
 constexpr int kSub = 8;                      // blocks per MMA sub-tile
 constexpr int kTcN = 2 * kSub;               // MMA columns: block j's real row 2j, imaginary row 2j + 1
-constexpr int kTcEpiWarps = 16;              // warps 0..15 read the accumulators (0..7 also write B's digits)
-constexpr int kTcWarps = kTcEpiWarps;        // four per SM sub-partition: 128 registers a thread
+constexpr int kTcEpiWarps = 16;              // warps 0..15 write B's digits and read the accumulators
+constexpr int kTcWarps = kTcEpiWarps + 1;    // warp 16 issues the MMAs
 constexpr int kTcThreads = 32 * kTcWarps;
-constexpr int kTcMmaWarp = kTcEpiWarps - 1;  // also issues the MMAs (converged, one elected lane)
+constexpr int kTcMmaWarp = kTcEpiWarps;
 constexpr int kTcPerPoint = kTcEpiWarps / 4; // epilogue threads per point (warps w, w + 4, ... share TMEM lanes)
 constexpr int kTcBlkPerThr = kSub / kTcPerPoint;  // blocks of a sub-tile per epilogue thread (2)
 static_assert(kTcPoints == 128, "one tile is the M = 128 rows of the MMA");
 static_assert(kTK * 2 == 128, "one operand row is 128 bytes: one 128-byte swizzle row");
 constexpr double kTcTiltBits = 2.0;          // max 31 |mu - c| over a group's points
+// A group takes the bins whose first point lies in a range of kTcGroupSpan
+// bucketed positions, so it holds about that many points plus part of a bin:
+// a span a little below the tile size lets most groups fill one tile instead
+// of spilling a few points into a nearly empty second one.
+constexpr int kTcGroupSpan = 112;
 constexpr uint32_t kTcPollLimit = 1u << 22;  // polls of an mbarrier before a wait gives up
 // every kTcFold sub-tiles a thread folds its 64-bit Horner value into a 128-bit
 // one (times W^(8 kTcFold)), so no 64-bit chain is longer than 4 kTcFold steps
@@ -116,12 +122,12 @@ __host__ __device__ __forceinline__ int tc_swz(int r, int kappa) {
 }
 constexpr int kASlice = kTcPoints * 128;           // 16 KB: one slice of A (the tile's Z' digits)
 constexpr int kBSlice = kTcN * 128;                // 2 KB: one slice of B (a sub-tile's A' digits)
-constexpr int kBBuf = (kSl + 1) * kBSlice;         // B buffer: the nine slices and one of zeros (160 rows)
-constexpr int kZBytes = kSl * kASlice;             // one tile's Z' image (144 KB), as laid out in shared memory
+constexpr int kBBuf = kSl * kBSlice;               // B buffer: the ten slices (160 rows)
+constexpr int kZBytes = kSl * kASlice;             // one tile's Z' image (160 KB), as laid out in shared memory
 
 // shared memory of k_tc_sum (offsets from a 1024-byte aligned base)
 constexpr int kSmA = 0;                                 // A: 10 slices
-constexpr int kSmB = kSmA + kZBytes;                    // B: two buffers of 9 slices + one of zeros
+constexpr int kSmB = kSmA + kZBytes;                    // B: two buffers of 10 slices
 constexpr int kSmW1 = kSmB + 2 * kBBuf;                 // per point W and W^8 (xh), the final exchange
 constexpr int kSmW8 = kSmW1 + kTcPoints * (int)sizeof(xh);
 constexpr int kSmHx = kSmW8 + kTcPoints * (int)sizeof(xh);  // (kTcPerPoint - 1) values per point
@@ -137,13 +143,6 @@ static_assert(kSmBar % 8 == 0, "mbarriers are 8-byte aligned");
 static_assert(kTcSmemBytes <= 232448, "within the 227 KB of shared memory a block may use");
 constexpr uint32_t kTmemCols = 512;          // two buffers of 10 accumulators x 16 columns (320 used)
 constexpr int kTmemBuf = kAcc * kTcN;        // columns per buffer
-
-// a 128-bit value across lane ^ 1
-__device__ __forceinline__ u128 shfl_u128_x1(u128 v) {
-  const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, 1);
-  const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), 1);
-  return ((u128)hi << 64) | lo;
-}
 
 // xor-shuffle of an xint across the warp
 __device__ __forceinline__ xint shfl_xint_tc(const xint &v, int m) {
@@ -182,8 +181,8 @@ __device__ __forceinline__ void tc_write_diag(const DevPoly &P, const PointRec &
 // ---------------------------------------------------------------------------
 // groups and tiles.  The bucketed points of tensor-core piece r occupy
 // [s_r, s_r+1); group q of the piece holds the whole bins whose first point
-// lies in [s_r + 64 q, s_r + 64 (q + 1)), so a group has about 64 points, or
-// one bin with more.  A group's tilt, the union of its points' windows and
+// lies in [s_r + S q, s_r + S (q + 1)) (S = kTcGroupSpan), so a group has
+// about S points, or one bin with more.  A group's tilt, the union of its points' windows and
 // its work-item boundaries are computed over all its points, and its points
 // are cut into tiles of kTcPoints in bucketed order.  Which point of a group
 // lands in which tile depends on the scatter's atomics, but nothing a point's
@@ -227,7 +226,7 @@ __global__ void k_tc_groups(DevPoly P, PointRec *__restrict__ rec, const uint32_
   for (int q = 0; q <= kTcMaxPieces; ++q) s[q] = (int)cnt[kCntTcStart + q];
   int r = -1, lg = 0, cum = 0;
   for (int q = 0; q < P.n_tc && q < kTcMaxPieces; ++q) {
-    const int ng = (s[q + 1] - s[q] + kTcPoints - 1) / kTcPoints;
+    const int ng = (s[q + 1] - s[q] + kTcGroupSpan - 1) / kTcGroupSpan;
     if (r < 0 && gw < cum + ng) {
       r = q;
       lg = gw - cum;
@@ -242,7 +241,7 @@ __global__ void k_tc_groups(DevPoly P, PointRec *__restrict__ rec, const uint32_
     if (lane == 0) groups[gw] = G;
     return;
   }
-  const int x0 = s[r] + kTcPoints * lg, x1 = x0 + kTcPoints;
+  const int x0 = s[r] + kTcGroupSpan * lg, x1 = x0 + kTcGroupSpan;
   const int start = tc_snap(bins, nbins, r, x0, s[r + 1]);
   const int end = x1 >= s[r + 1] ? s[r + 1] : tc_snap(bins, nbins, r, x1, s[r + 1]);
   const int count = end - start;
@@ -479,7 +478,7 @@ __global__ void __launch_bounds__(256) k_tc_tau(const TcTile *__restrict__ tiles
 // 128 bytes (kappa = i for the real part of u^i, 32 + i for the imaginary
 // part), as 16-byte chunks at their swizzled positions (eight powers at a
 // time, one chunk per slice and component); W^(2^k) = (u^32 tau^32)^(2^k),
-// and Z's scale exponent.
+// W^(8 kTcFold), and Z's scale exponent.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
                                                       const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
@@ -519,11 +518,11 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if ((g | q | h) != 0 && valid) cur = xh_mul(cur, uh);
-          // x 2^(e - 63) 2^(72 - eq) = x 2^-sh with eq = eQ + 1: fixed point below
-          // 2^70 (components <= 2^(eQ - 1))
-          const int sh = eQ + 1 + 63 - 72 - (int)cur.e;
-          bchunks72(valid ? shift_to72((u128)cur.x, sh) : (u128)0, xr[h]);
-          bchunks72(valid ? shift_to72((u128)cur.y, sh) : (u128)0, xi[h]);
+          // x 2^(e - 63) 2^(70 - eq) = x 2^-sh with eq = eQ + 1: fixed point below
+          // 2^69 (components <= 2^(eQ - 1))
+          const int sh = eQ + 1 + 63 - 70 - (int)cur.e;
+          bchunks70(valid ? shift_to70((u128)cur.x, sh) : (u128)0, xr[h]);
+          bchunks70(valid ? shift_to70((u128)cur.y, sh) : (u128)0, xi[h]);
           sr[h] = digit_sign((uint32_t)cur.sx);
           si[h] = digit_sign((uint32_t)cur.sy);
         }
@@ -553,22 +552,22 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
     for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
     o.Wf = o.W[3];
     for (int q = 1; (1 << q) <= kTcFold; ++q) o.Wf = xint_sqr(o.Wf);
-    o.eq = eQ + 1;  // Z' = F 2^(eq - 72)
+    o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
     o.pad[0] = o.pad[1] = o.pad[2] = 0;
     pts[(size_t)t * kTcPoints + p] = o;
   }
 }
 
 // ---------------------------------------------------------------------------
-// the window sums on the tensor cores.  One persistent CTA per SM (16 warps) takes work
+// the window sums on the tensor cores.  One persistent CTA per SM (17 warps) takes work
 // items (a tile and a run of at most `chunk` blocks) from a counter.  Per
-// item, the tile's Z' image (the A operand, 144 KB) arrives by nine bulk
+// item, the tile's Z' image (the A operand, 160 KB) arrives by ten bulk
 // copies on an mbarrier; then, sub-tile by sub-tile of 8 blocks from the top
 // down, in a two-stage pipeline:
-//   warps 0-7 write B's digits for sub-tile s (one term per thread) into one
-//     of two buffers; warps 0-15 then read the accumulators of sub-tile s + 1;
-//   warp 15 (converged, one elected lane) issues the 36 MMAs of sub-tile s
-//     (9 Z' slices x 4 k-steps, each against the stacked A' slices) into one
+//   warps 0-15 write B's digits for sub-tile s (one component of one term per
+//     thread) into one of two buffers, then read the accumulators of sub-tile s + 1;
+//   warp 16 (converged, one elected lane) issues the 40 MMAs of sub-tile s
+//     (10 Z' slices x 4 k-steps, each against the stacked A' slices) into one
 //     of two sets of ten TMEM accumulators and commits them to that set's
 //     mbarrier.
 // Thread w 32 + l of warps 0-15 is TMEM lane 32 (w % 4) + l, i.e. point
@@ -611,12 +610,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_alloc(reinterpret_cast<uint32_t *>(sm + kSmMisc), kTmemCols);
     tmem_relinquish();
   }
-  // the zero slice after the nine A' slices of each B buffer (read by the first MMA of a sub-tile)
-  for (int i = tid; i < 2 * kBSlice / 16; i += kTcThreads) {
-    const int b = i / (kBSlice / 16), q = i % (kBSlice / 16);
-    reinterpret_cast<uint4 *>(sm + kSmB + b * kBBuf + kSl * kBSlice)[q] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  fence_proxy_async_smem();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -674,12 +667,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     xh H = xh_norm(0, 0, 0, 0, 0);
     xint Acc = zero;  // the folded 128-bit value
     int e_prev[kTcBlkPerThr] = {0, 0}, e_cur[kTcBlkPerThr] = {0, 0};
-    // coefficient of this thread's term in block mb + 8 ts + wid (0 outside the item or the piece)
+    // coefficient of this thread's term in block mb + 8 ts + (wid % 8) (0 outside the item or the piece)
     auto load_b = [&](int ts_) -> double2 {
-      const long long m = mb + (long long)kSub * ts_ + wid;
+      const long long m = mb + (long long)kSub * ts_ + (wid & (kSub - 1));
       const long long k = k0 + kTB * m + lane;
       double2 c = make_double2(0.0, 0.0);
-      if (wid < kSub && ts_ >= 0 && m < me && k <= k1) {
+      if (ts_ >= 0 && m < me && k <= k1) {
         if (P.complex_coef)
           c = __ldg(reinterpret_cast<const double2 *>(P.b) + k);
         else
@@ -691,11 +684,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int it = 0; it <= nsub; ++it) {
       const int ts = nsub - 1 - it;  // the sub-tile whose digits and MMAs this iteration makes
       const int buf = it & 1;
-      if (it < nsub && wid < kSub) {  // B's digits for block mb + 8 ts + wid, thread = term
+      if (it < nsub && wid < kTcEpiWarps) {  // B's digits: warp w takes block w % 8, component w / 8, lane = term
+        const int jb = wid & (kSub - 1), comp = wid >> 3;
         const double br = bnext.x, bi = bnext.y;
         bnext = load_b(ts - 1);  // in flight during this sub-tile
         const unsigned long long tmi = sTm[lane];
         const int tei = sTe[lane];
+        // both components' products give the block's scale; the digits are this thread's component's
         u128 pr = 0, pi = 0;
         int er_ = 0, ei_ = 0, top = INT_MIN;
         auto prod = [&](double x, u128 &pp, int &E) {
@@ -711,36 +706,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         prod(br, pr, er_);
         prod(bi, pi, ei_);
         for (int o = 16; o >= 1; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
-        const int eR = top == INT_MIN ? 0 : top + 2;  // every |component| < 2^(eR - 1): below 2^71 in F
-        const u128 fr = pr ? shift_to72(pr, eR - 72 - er_) : (u128)0;
-        const u128 fi = pi ? shift_to72(pi, eR - 72 - ei_) : (u128)0;
-        const uint32_t nr = br < 0.0, ni = bi < 0.0;
-        // lane pairs (terms i even, i + 1) share the stores: the even lane takes
-        // both terms' real parts, the odd lane both imaginary parts
-        const int odd = lane & 1, ib = lane & ~1;
-        const u128 mine = odd ? fi : fr, recv = shfl_u128_x1(odd ? fr : fi);
-        const uint32_t nmine = odd ? ni : nr, nrecv = __shfl_xor_sync(0xffffffffu, odd ? nr : ni, 1);
-        uint32_t xa[kSl], xb[kSl];  // term ib, term ib + 1
-        bchunks72(odd ? recv : mine, xa);
-        bchunks72(odd ? mine : recv, xb);
-        const DigitSign sa = digit_sign(odd ? nrecv : nmine), sb = digit_sign(odd ? nmine : nrecv);
-        // in slice s, real row 16 s + 2 wid = (A'_re | -A'_im) and imaginary row
-        // 16 s + 2 wid + 1 = (A'_im | A'_re): the even lane puts its A'_re pair at
-        // (real row, kappa ib) and (imaginary row, kappa 32 + ib); the odd lane
-        // -A'_im at (real row, 32 + ib) and A'_im at (imaginary row, ib).  A slice
-        // is 16 rows, two whole 8-row swizzle atoms, so the row's swizzle phase
-        // does not depend on s.
-        const int o1 = odd ? tc_swz(2 * wid, kTB + ib) : tc_swz(2 * wid, ib);
-        const int o2 = odd ? tc_swz(2 * wid + 1, ib) : tc_swz(2 * wid + 1, kTB + ib);
-        const uint32_t flip = odd ? 0x80008000u : 0u;
+        const int eR = top == INT_MIN ? 0 : top + 2;  // every |component| < 2^(eR - 1): below 2^69 in F
+        const u128 pc = comp ? pi : pr;
+        const u128 F = pc ? shift_to70(pc, eR - 70 - (comp ? ei_ : er_)) : (u128)0;
+        uint32_t x[kSl];
+        bchunks70(F, x);
+        const DigitSign sg = digit_sign((uint32_t)((comp ? bi : br) < 0.0));
+        // in slice s, real row 16 s + 2 jb = (A'_re | -A'_im) and imaginary row
+        // 16 s + 2 jb + 1 = (A'_im | A'_re): a real part goes to (real row, kappa i)
+        // and (imaginary row, 32 + i), an imaginary part negated to (real row, 32 + i)
+        // and as it is to (imaginary row, i).  A slice is 16 rows, two whole 8-row
+        // swizzle atoms, so the row's swizzle phase does not depend on s.
+        const int o1 = comp ? tc_swz(2 * jb, kTB + lane) : tc_swz(2 * jb, lane);
+        const int o2 = comp ? tc_swz(2 * jb + 1, lane) : tc_swz(2 * jb + 1, kTB + lane);
+        const uint16_t flip = comp ? 0x8000u : 0u;
         unsigned char *Bb = sm + kSmB + buf * kBBuf;
 #pragma unroll
         for (int s = 0; s < kSl; ++s) {
-          const uint32_t w = bf16_pair(xa[s], sa, xb[s], sb);
-          *reinterpret_cast<uint32_t *>(Bb + s * kBSlice + o1) = w ^ flip;
-          *reinterpret_cast<uint32_t *>(Bb + s * kBSlice + o2) = w;
+          const uint16_t d = (uint16_t)(tc_fbits(fmaf(tc_bitsf(x[s]), sg.s, sg.k)) >> 16);  // bf16 of the digit
+          *reinterpret_cast<uint16_t *>(Bb + s * kBSlice + o1) = d ^ flip;
+          *reinterpret_cast<uint16_t *>(Bb + s * kBSlice + o2) = d;
         }
-        if (lane == 0) sEr[buf * kSub + wid] = eR;
+        if (lane == 0 && comp == 0) sEr[buf * kSub + jb] = eR;
       }
       // B (written by the generic proxy) becomes visible to the tensor core; the
       // epilogue's TMEM reads of this buffer's previous use are ordered before
@@ -762,7 +749,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int ks = 0; ks < 4; ++ks) {
 #pragma unroll
               for (int sz = 0; sz < kSl; ++sz) {
-                const int ncol = sz == 0 ? kTcN * (kSl + 1) : kTcN * (kAcc - sz);
+                const int ncol = kTcN * (kAcc - sz);
                 const uint32_t d = dcol + (uint32_t)(kTcN * sz);
                 const uint64_t a = adesc0 + (uint64_t)((sz * kASlice + 32 * ks) >> 4);
                 const uint64_t b = bdesc0 + (uint64_t)((32 * ks) >> 4);
@@ -786,30 +773,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           atomicOr(status, kStatusTimeout);
         } else {
           fence_after_sync();
-          uint32_t v[kAcc][4];  // columns 4 h .. 4 h + 3: blocks 2 h, 2 h + 1 (real, imaginary)
+          // block 2 h + jj of the sub-tile: columns 16 t + 2 (2 h + jj) + (0 real, 1 imaginary)
           const uint32_t ta = tbase + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)(pb * kTmemBuf + 4 * h);
-#pragma unroll
-          for (int tt = 0; tt < kAcc; ++tt) tmem_ld4(ta + (uint32_t)(kTcN * tt), v[tt]);
-          tmem_ld_wait();
           const long long m0 = mb + (long long)kSub * (ts + 1);  // the previous sub-tile's first block
           xh C[kTcBlkPerThr];
 #pragma unroll
-          for (int jj = 0; jj < kTcBlkPerThr; ++jj) {
+          for (int jj = kTcBlkPerThr - 1; jj >= 0; --jj) {
+            uint32_t v[kAcc][2];
+#pragma unroll
+            for (int tt = 0; tt < kAcc; ++tt) tmem_ld2(ta + (uint32_t)(kTcN * tt + 2 * jj), v[tt]);
+            tmem_ld_wait();
             C[jj] = xh_norm(0, 0, 0, 0, 0);
             if (m0 + kTcBlkPerThr * h + jj < me && p < T.count) {
               float ar[kAcc], ai[kAcc];
 #pragma unroll
               for (int tt = 0; tt < kAcc; ++tt) {
-                ar[tt] = __uint_as_float(v[tt][2 * jj]);
-                ai[tt] = __uint_as_float(v[tt][2 * jj + 1]);
+                ar[tt] = __uint_as_float(v[tt][0]);
+                ai[tt] = __uint_as_float(v[tt][1]);
               }
               u128 xr, xi;
               int sr, si;
               join_vals(ar, xr, sr);
               join_vals(ai, xi, si);
-              // A' = F 2^(eR - 72), Z' = F 2^(eq - 72), and the kept pairs are
-              // 256^7 X: C = X 2^(eR + eq - 88) = X 2^(e - 126) with e = eR + eq + 38
-              C[jj] = xh_from128(xr, sr, xi, si, 38 + (long long)e_prev[jj] + eqp);
+              // A' = F 2^(eR - 70), Z' = F 2^(eq - 70), and the kept pairs are
+              // 128^9 X: C = X 2^(eR + eq - 77) = X 2^(e - 126) with e = eR + eq + 49
+              C[jj] = xh_from128(xr, sr, xi, si, 49 + (long long)e_prev[jj] + eqp);
             }
           }
           // H (relative to block 2 h of the sub-tile above, 8 blocks up) <- H W^8 + C_1 W + C_0:
@@ -956,7 +944,7 @@ static int tc_num_sms() {
   return sms;
 }
 
-static int64_t tc_groups_max(int64_t n) { return (n + kTcPoints - 1) / kTcPoints + kTcMaxPieces; }
+static int64_t tc_groups_max(int64_t n) { return (n + kTcGroupSpan - 1) / kTcGroupSpan + kTcMaxPieces; }
 static int64_t tc_tiles_max(int64_t n) { return (n + kTcPoints - 1) / kTcPoints + tc_groups_max(n); }
 static int64_t tc_items_cap(int64_t n) { return tc_tiles_max(n) + (int64_t)tc_num_sms() * kTcItemsPerSm; }
 

@@ -1,6 +1,6 @@
 // Integer arithmetic of the tensor-core window sums (fpe_tc.cu), kept apart
 // so that the host test (tests/native/tc_arith_host.cu) compiles the same
-// code: the balanced base-256 digits of the 71-bit fixed-point operands and
+// code: the balanced base-128 digits of the 69-bit fixed-point operands and
 // their bf16 encoding, the join of the ten exact fp32 accumulators (one per
 // kept digit-pair diagonal) into one 128-bit integer, and the 64-bit-mantissa
 // complex values (xh) in which a work item's blocks are combined by Horner's
@@ -15,7 +15,7 @@
 namespace fpe {
 
 constexpr int kTB = 32;   // terms per block
-constexpr int kSl = 9;    // 8-bit digits per operand (slices)
+constexpr int kSl = 10;   // 7-bit digits per operand (slices)
 constexpr int kAcc = 10;  // kept digit-pair diagonals t = s + s' <= 9, one fp32 accumulator each
 
 __host__ __device__ __forceinline__ uint32_t tc_fbits(float x) {
@@ -144,34 +144,33 @@ __host__ __device__ __forceinline__ xh xh_add(const xh &a, const xh &b) {
 }
 
 // ---------------------------------------------------------------------------
-// Digits.  Balanced base-256 digits of F < 2^71: F = sum_j d_j 256^(8 - j)
-// (j = 0..8) with d_j in [-128, 127] for j > 0 and d_0 in [0, 128].  Adding
-// B = sum_j 128 256^j (j = 0..8) makes them plain chunks c_j = d_j + 128 of
-// G = F + B (8 bits each; the top one, everything above bit 63, at most
-// 256).  Each chunk is returned as the bits of the float 2^23 + c_j, from
-// which one fused multiply-add by +-1 gives +-d_j exactly (bf16_pair): the
-// digits are integers of at most 8 significant bits, exact in bf16.  A
-// product of two digits is at most 2^14 in magnitude; a 64-long dot product
-// at most 2^20; the at most nine digit pairs on one diagonal s + s' = t add
-// up below 9 2^20 < 2^23.2: fp32 accumulation is exact.
+// Digits.  Balanced base-128 digits of F < 2^69: F = sum_j d_j 128^(9 - j)
+// with d_j in [-64, 63] for j > 0 and d_0 in [0, 64].  Adding
+// B = sum_j 64 128^j makes them plain chunks c_j = d_j + 64 of G = F + B
+// (7 bits each; the top one, everything above bit 63, at most 128).  Each
+// chunk is returned as the bits of the float 2^23 + c_j, from which one
+// fused multiply-add by +-1 gives +-d_j exactly (bf16_pair).  Products of
+// two digits stay within 2^12, and the ten slice pairs of one accumulator
+// over a 64-long dot product within 10 x 2^18 < 2^22: fp32 accumulation is
+// exact with room to spare.
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ void bchunks72(u128 F, uint32_t (&x)[kSl]) {
-  const u128 G = F + (((u128)128 << 64) | 0x8080808080808080ull);
-  const unsigned long long lo = (unsigned long long)G;
-  x[0] = 0x4B000000u | (uint32_t)(G >> 64);
+__host__ __device__ __forceinline__ void bchunks70(u128 F, uint32_t (&x)[kSl]) {
+  const u128 G = F + (((u128)0x20 << 64) | 0x4081020408102040ull);
+  const unsigned long long lo = (unsigned long long)G, hi = (unsigned long long)(G >> 64);
+  x[0] = 0x4B000000u | (uint32_t)((hi << 1) | (lo >> 63));
 #pragma unroll
-  for (int j = 1; j < kSl; ++j) x[j] = 0x4B000000u | ((uint32_t)(lo >> (8 * (kSl - 1 - j))) & 255u);
+  for (int j = 1; j < kSl; ++j) x[j] = 0x4B000000u | ((uint32_t)(lo >> (7 * (kSl - 1 - j))) & 127u);
 }
 
 // the multiplier and addend that turn a chunk's float 2^23 + c into
-// (-1)^neg (c - 128), exactly
+// (-1)^neg (c - 64), exactly
 struct DigitSign {
   float s, k;
 };
 __host__ __device__ __forceinline__ DigitSign digit_sign(uint32_t neg) {
   DigitSign r;
   r.s = neg ? -1.0f : 1.0f;
-  r.k = neg ? 8388736.0f : -8388736.0f;
+  r.k = neg ? 8388672.0f : -8388672.0f;
   return r;
 }
 
@@ -188,38 +187,36 @@ __host__ __device__ __forceinline__ uint32_t bf16_pair(uint32_t xa, DigitSign sa
 #endif
 }
 
-// X 2^-sr (sr may be negative), saturated below 2^71
-__host__ __device__ __forceinline__ u128 shift_to72(u128 X, int sr) {
-  const u128 cap = ((u128)1 << 71) - 1;
+// X 2^-sr (sr may be negative), saturated below 2^70
+__host__ __device__ __forceinline__ u128 shift_to70(u128 X, int sr) {
+  const u128 cap = ((u128)1 << 70) - 1;
   if (sr >= 128) return 0;
   if (sr >= 0) {
     const u128 F = X >> sr;
     return F > cap ? cap : F;
   }
-  if (sr <= -71 || (X >> (71 + sr)) != 0) return cap;
+  if (sr <= -70 || (X >> (70 + sr)) != 0) return cap;
   return X << (-sr);
 }
 
-// an fp32 accumulator holding an exact integer (below 2^24 in magnitude) as an int
-__host__ __device__ __forceinline__ int acc_int(float v) {
-#ifdef __CUDA_ARCH__
-  return __float2int_rn(v);
-#else
-  return (int)v;
-#endif
-}
-
-// X = sum_t v_t 256^(9 - t) over the ten accumulators v_t of one output (t =
+// X = sum_t v_t 128^(9 - t) over the ten accumulators v_t of one output (t =
 // the digit-pair diagonal), as a 128-bit magnitude and a sign.  Each v_t is
-// an integer below 2^23.2 in magnitude, so the upper five and the lower five
-// terms each fit a 64-bit integer: X = hi 2^40 + lo.
+// an integer below 2^22 in magnitude held exactly in fp32; adding 1.5 2^23
+// puts it in the low mantissa bits, so the float's bits are
+// w_t = v_t + 0x4B400000.  The pairs v_2j 128 + v_2j+1 (below 2^29.1) come
+// from the w's in wrap-around 32-bit arithmetic, and three 32 x 32 + 64-bit
+// products join them.
 __host__ __device__ __forceinline__ void join_vals(const float (&v)[kAcc], u128 &mag, int &neg) {
-  long long hi = 0, lo = 0;
+  int pr[kAcc / 2];
 #pragma unroll
-  for (int t = 0; t < 5; ++t) hi = hi * 256 + acc_int(v[t]);
-#pragma unroll
-  for (int t = 5; t < kAcc; ++t) lo = lo * 256 + acc_int(v[t]);
-  const __int128 X = ((__int128)hi << 40) + (__int128)lo;
+  for (int j = 0; j < kAcc / 2; ++j) {
+    const uint32_t wa = tc_fbits(v[2 * j] + 12582912.0f);
+    const uint32_t wb = tc_fbits(v[2 * j + 1] + 12582912.0f);
+    pr[j] = (int)(wa * 128u + wb - 129u * 0x4B400000u);
+  }
+  const long long lo = (long long)pr[2] * (1ll << 28) + (long long)pr[3] * (1ll << 14) + pr[4];
+  const long long hi = (long long)pr[0] * (1ll << 14) + pr[1];
+  const __int128 X = ((__int128)hi << 42) + (__int128)lo;
   neg = X < 0;
   mag = (u128)(neg ? -X : X);
 }

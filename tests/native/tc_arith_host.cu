@@ -6,10 +6,10 @@ using namespace fpe;
 
 static u128 mk(const unsigned long long *w) { return ((u128)w[1] << 64) | w[0]; }
 
-// the nine bf16 digits of F (< 2^71) with sign neg, and the same pair word's high half
+// the ten bf16 digits of F (< 2^69) with sign neg, and the same pair word's high half
 extern "C" void t_digits(const unsigned long long *f, unsigned neg, unsigned short *lo, unsigned short *hi) {
   uint32_t x[kSl];
-  bchunks72(mk(f), x);
+  bchunks70(mk(f), x);
   const DigitSign s = digit_sign(neg);
   for (int j = 0; j < kSl; ++j) {
     const uint32_t w = bf16_pair(x[j], s, x[j], s);
@@ -18,7 +18,7 @@ extern "C" void t_digits(const unsigned long long *f, unsigned neg, unsigned sho
   }
 }
 
-// sum_t v_t 256^(9 - t) from ten fp32 accumulators (exact integers)
+// sum_t v_t 128^(9 - t) from ten fp32 accumulators (exact integers)
 extern "C" void t_join(const float *v, unsigned long long *mag, int *neg) {
   float acc[kAcc];
   for (int t = 0; t < kAcc; ++t) acc[t] = v[t];
@@ -32,7 +32,7 @@ extern "C" void t_join(const float *v, unsigned long long *mag, int *neg) {
 // of A' row digits with Z' column digits, the digit pairs (s, s') with
 // s + s' = t <= 9 added into accumulator t in fp32 (the order below; the
 // tensor core's differs, which is harmless while every partial sum is an
-// exact integer), then joined.  a[k], z[k] (k < 64) are 71-bit magnitudes
+// exact integer), then joined.  a[k], z[k] (k < 64) are 69-bit magnitudes
 // (two words each) with signs; exact[t] receives the same sums in 64-bit
 // integers, so the caller can check that fp32 lost nothing.
 extern "C" void t_row(const unsigned long long *a, const int *as, const unsigned long long *z, const int *zs,
@@ -45,8 +45,8 @@ extern "C" void t_row(const unsigned long long *a, const int *as, const unsigned
   }
   for (int k = 0; k < 2 * kTB; ++k) {
     uint32_t xa[kSl], xz[kSl];
-    bchunks72(mk(a + 2 * k), xa);
-    bchunks72(mk(z + 2 * k), xz);
+    bchunks70(mk(a + 2 * k), xa);
+    bchunks70(mk(z + 2 * k), xz);
     const DigitSign sa = digit_sign((uint32_t)as[k]), sz = digit_sign((uint32_t)zs[k]);
     float da[kSl], dz[kSl];
     for (int j = 0; j < kSl; ++j) {
@@ -54,17 +54,17 @@ extern "C" void t_row(const unsigned long long *a, const int *as, const unsigned
       dz[j] = fmaf(tc_bitsf(xz[j]), sz.s, sz.k);
     }
     for (int s = 0; s < kSl; ++s)
-      for (int s2 = 0; s2 < kSl && s + s2 < kAcc; ++s2) {
+      for (int s2 = 0; s2 < kSl - s; ++s2) {
         acc[s + s2] += da[s] * dz[s2];  // a product of two digits is exact in fp32
         ex[s + s2] += (long long)da[s] * (long long)dz[s2];
       }
   }
-  for (int t = 0; t < kAcc; ++t) exact[t] = ex[t];
+  for (int t = 0; t < kSl; ++t) exact[t] = ex[t];
   u128 m;
   join_vals(acc, m, *neg);
   mag[0] = (unsigned long long)m;
   mag[1] = (unsigned long long)(m >> 64);
-  for (int t = 0; t < kAcc; ++t) exact[kAcc + t] = (long long)acc[t];
+  for (int t = 0; t < kSl; ++t) exact[kSl + t] = (long long)acc[t];
 }
 
 static void put_xh(const xh &v, unsigned long long *m, int *s, long long *e) {

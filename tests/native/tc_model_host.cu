@@ -34,7 +34,7 @@ constexpr int kPer = 4;  // threads per point, each taking blocks 2 h, 2 h + 1 o
 
 struct Point {
   int sd_re[kTB][kSl], sd_im[kTB][kSl];  // signed Z' digits of u^i
-  int eq;                                // Z' = F 2^(eq - 72)
+  int eq;                                // Z' = F 2^(eq - 70)
   xint W[4];
   xh w1, w8;
   xint wf;  // W^(8 kFold)
@@ -42,7 +42,7 @@ struct Point {
 
 void digits(u128 F, int neg, int (&d)[kSl]) {
   uint32_t x[kSl];
-  bchunks72(F, x);
+  bchunks70(F, x);
   const DigitSign s = digit_sign((uint32_t)neg);
   for (int j = 0; j < kSl; ++j) d[j] = (int)fmaf(tc_bitsf(x[j]), s.s, s.k);
 }
@@ -87,19 +87,19 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
     xh cur = xh_norm(1ull << 63, 0, 0, 0, 0);
     for (int i = 0; i < kTB; ++i) {
       if (i > 0) cur = xh_mul(cur, uh);
-      const int sr = eQ + 1 + 63 - 72 - (int)cur.e;
-      digits(shift_to72((u128)cur.x, sr), cur.sx, P.sd_re[i]);
-      digits(shift_to72((u128)cur.y, sr), cur.sy, P.sd_im[i]);
+      const int sr = eQ + 1 + 63 - 70 - (int)cur.e;
+      digits(shift_to70((u128)cur.x, sr), cur.sx, P.sd_re[i]);
+      digits(shift_to70((u128)cur.y, sr), cur.sy, P.sd_im[i]);
     }
     xint u32 = u;
     for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
     P.W[0] = xint_mul(u32, t32);
     for (int k = 1; k < 4; ++k) P.W[k] = xint_sqr(P.W[k - 1]);
+    P.wf = P.W[3];
+    for (int q = 1; (1 << q) <= kFold; ++q) P.wf = xint_sqr(P.wf);
     P.eq = eQ + 1;
     P.w1 = xh_from_xint(P.W[0]);
     P.w8 = xh_from_xint(P.W[3]);
-    P.wf = P.W[3];
-    for (int q = 1; (1 << q) <= kFold; ++q) P.wf = xint_sqr(P.wf);
   }
 
   // k_tc_sum, one work item at a time: per point four threads h = 0..3, each
@@ -152,8 +152,8 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
         }
         const int eR = top == INT_MIN ? 0 : top + 2;
         for (int i = 0; i < kTB; ++i) {
-          digits(pr[i] ? shift_to72(pr[i], eR - 72 - er_[i]) : (u128)0, brs[i] < 0.0, ad_re[i]);
-          digits(pi[i] ? shift_to72(pi[i], eR - 72 - ei_[i]) : (u128)0, bis[i] < 0.0, ad_im[i]);
+          digits(pr[i] ? shift_to70(pr[i], eR - 70 - er_[i]) : (u128)0, brs[i] < 0.0, ad_re[i]);
+          digits(pi[i] ? shift_to70(pi[i], eR - 70 - ei_[i]) : (u128)0, bis[i] < 0.0, ad_im[i]);
         }
         for (int p = 0; p < npts; ++p) {
           const Point &P = pts[p];
@@ -168,7 +168,7 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
                 sim += (long long)ad_im[i][s] * P.sd_re[i][t - s] + (long long)ad_re[i][s] * P.sd_im[i][t - s];
               }
             }
-            acc_re[t] = (float)sre;  // exact: below 2^23.2
+            acc_re[t] = (float)sre;  // exact: below 2^22
             acc_im[t] = (float)sim;
           }
           xh C = xh_norm(0, 0, 0, 0, 0);
@@ -177,7 +177,7 @@ extern "C" void t_tile(const double *b, long long mlo, long long nblk, const dou
             int sr, si;
             join_vals(acc_re, xr, sr);
             join_vals(acc_im, xi, si);
-            C = xh_from128(xr, sr, xi, si, 38 + (long long)eR + P.eq);
+            C = xh_from128(xr, sr, xi, si, 49 + (long long)eR + P.eq);
           }
           Cb[p * kSub + g] = C;
         }

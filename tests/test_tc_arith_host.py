@@ -1,14 +1,13 @@
 """Integer arithmetic of the tensor-core window sums (fpe_tc_arith.cuh),
 compiled as host code, against exact integers and rationals:
 
-- the balanced base-256 digits of a 71-bit operand and their bf16 encoding
+- the balanced base-128 digits of a 69-bit operand and their bf16 encoding
   reconstruct the operand exactly, within the stated digit ranges;
-- the join of ten fp32 accumulators is the exact sum_t v_t 256^(9 - t);
+- the join of ten fp32 accumulators is the exact sum_t v_t 128^(9 - t);
 - one MMA output row (64 digit products per pair, pairs s + s' <= 9): every
-  fp32 accumulator is the exact integer sum and stays below 2^23.2 (fp32 holds
-  integers exactly up to 2^24) even for digits at their extremes, the join
-  equals the kept pairs' sum, and the dropped pairs stay below 2^-70 of the
-  product scale per product;
+  fp32 accumulator is the exact integer sum and stays below 2^22 even for
+  digits at their extremes, the join equals the kept pairs' sum, and the
+  dropped pairs stay below 2^-66 of the product scale per product;
 - the 64-bit-mantissa complex product and sum (xh) are within 2^-60 of the
   exact values relative to their operands, the conversion from 128 bits
   within 2^-63.
@@ -26,10 +25,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 U64 = ctypes.c_uint64
 K = 64  # contraction length of one MMA row (32 terms x re, im)
-SL = 9    # digits per operand
-ACC = 10  # kept diagonals t = s + s' <= 9
-BASE = 256
-FBITS = 71
+SL = 10
 
 
 @pytest.fixture(scope="module")
@@ -72,45 +68,44 @@ def _digits(lib, F, neg):
 
 
 def _extreme_operands(rng):
-    """71-bit operands whose balanced digits sit at +-128 (the largest digit products)."""
+    """69-bit operands whose balanced digits sit at +-64 (the largest digit products)."""
     out = []
     for _ in range(8):
-        ds = [128] + [rng.choice((-128, 127)) for _ in range(SL - 1)]
+        ds = [64] + [rng.choice((-64, 63)) for _ in range(SL - 1)]
         v = 0
         for d in ds:
-            v = v * BASE + d
-        if 0 <= v < 2**FBITS:
+            v = v * 128 + d
+        if 0 <= v < 2**69:
             out.append(v)
-    out.append(2**FBITS - 1)
+    out.append(2**69 - 1)
     return out
 
 
 def test_digits_reconstruct(lib):
     rng = random.Random(1)
-    cases = [0, 1, 127, 128, 255, 256, 2**63, 2**64 - 1, 2**FBITS - 1, 2**FBITS - 2**62] + _extreme_operands(rng)
-    cases += [rng.getrandbits(FBITS) for _ in range(3000)]
-    cases += [rng.getrandbits(rng.randint(1, FBITS)) for _ in range(1000)]
+    cases = [0, 1, 63, 64, 127, 128, 2**63, 2**69 - 1, 2**69 - 2**62] + _extreme_operands(rng)
+    cases += [rng.getrandbits(69) for _ in range(3000)] + [rng.getrandbits(rng.randint(1, 69)) for _ in range(1000)]
     for F in cases:
         for neg in (0, 1):
             d = _digits(lib, F, neg)
             sgn = -1 if neg else 1
-            assert sum(x * BASE ** (SL - 1 - j) for j, x in enumerate(d)) == sgn * F, (F, neg, d)
+            assert sum(x * 128 ** (SL - 1 - j) for j, x in enumerate(d)) == sgn * F, (F, neg, d)
             u = [sgn * x for x in d]
-            assert 0 <= u[0] <= 128
-            assert all(-128 <= x <= 127 for x in u[1:])
+            assert 0 <= u[0] <= 64
+            assert all(-64 <= x <= 63 for x in u[1:])
 
 
 def test_join_exact(lib):
     rng = random.Random(2)
     mag = (U64 * 2)()
     neg = ctypes.c_int()
-    lim = 2**24  # every integer of magnitude up to 2^24 is exact in fp32
-    vecs = [[lim - 1] * ACC, [-lim] * ACC, [0] * ACC, [1] + [0] * (ACC - 1), [0] * (ACC - 1) + [-1]]
-    vecs += [[rng.randint(-lim, lim - 1) for _ in range(ACC)] for _ in range(5000)]
+    lim = 2**22
+    vecs = [[lim - 1] * SL, [-lim] * SL, [0] * SL, [1] + [0] * 9, [0] * 9 + [-1]]
+    vecs += [[rng.randint(-lim, lim - 1) for _ in range(SL)] for _ in range(5000)]
     for v in vecs:
-        lib.t_join((ctypes.c_float * ACC)(*v), mag, ctypes.byref(neg))
+        lib.t_join((ctypes.c_float * SL)(*v), mag, ctypes.byref(neg))
         X = (mag[0] | (mag[1] << 64)) * (-1 if neg.value else 1)
-        assert X == sum(x * BASE ** (ACC - 1 - t) for t, x in enumerate(v)), v
+        assert X == sum(x * 128 ** (SL - 1 - t) for t, x in enumerate(v)), v
 
 
 def _row(lib, a, asg, z, zsg):
@@ -118,38 +113,36 @@ def _row(lib, a, asg, z, zsg):
     Z = (U64 * (2 * K))(*[w for v in z for w in (v & (2**64 - 1), v >> 64)])
     mag = (U64 * 2)()
     neg = ctypes.c_int()
-    ex = (ctypes.c_longlong * (2 * ACC))()
+    ex = (ctypes.c_longlong * (2 * SL))()
     lib.t_row(A, (ctypes.c_int * K)(*asg), Z, (ctypes.c_int * K)(*zsg), mag, ctypes.byref(neg), ex)
     X = (mag[0] | (mag[1] << 64)) * (-1 if neg.value else 1)
-    return X, list(ex[:ACC]), list(ex[ACC:])
+    return X, list(ex[:SL]), list(ex[SL:])
 
 
 def _balanced(F):
     d = []
     for _ in range(SL):
-        r = F % BASE
-        if r >= BASE // 2:
-            r -= BASE
+        r = F % 128
+        if r >= 64:
+            r -= 128
         d.append(r)
-        F = (F - r) // BASE
+        F = (F - r) // 128
     d.reverse()
-    d[0] += F * BASE if F else 0
+    d[0] += F * 128 if F else 0
     return d
 
 
 def test_mma_row_exact(lib):
-    """Accumulators exact and below 2^23.2; join = kept pairs; dropped pairs tiny."""
+    """Accumulators exact and below 2^22; join = kept pairs; dropped pairs tiny."""
     rng = random.Random(3)
     ext = _extreme_operands(rng)
-    # the largest possible dropped-pair sum with |digits| <= 128, per product,
-    # in the join's units (X counts 256^7 of the product F_a F_z)
-    pairs = lambda t: sum(1 for s in range(SL) if 0 <= t - s < SL)
-    drop = sum(pairs(t) * 128 * 128 * Fraction(1, BASE ** (t - (ACC - 1))) for t in range(ACC, 2 * SL - 1))
-    scale = Fraction(2**FBITS * 2**FBITS, BASE ** (2 * SL - 2 - (ACC - 1)))  # largest product in the join's units
-    assert drop / scale < Fraction(1, 2**70)
+    # the largest possible dropped-pair sum with |digits| <= 64, per product
+    drop = sum((2 * SL - 1 - t) * 64 * 64 * Fraction(1, 128 ** (t - (SL - 1))) for t in range(SL, 2 * SL - 1))
+    scale = Fraction(2**69 * 2**69, 128 ** (SL - 1))  # largest product in the join's units
+    assert drop / scale < Fraction(1, 2**66)
     for trial in range(60):
-        if trial == 0:  # every digit 127: every product +16129, the largest accumulators
-            a = z = [sum(127 * BASE**j for j in range(SL - 1))] * K
+        if trial == 0:  # every digit 63: every product +3969, the largest accumulators
+            a = z = [sum(63 * 128**j for j in range(SL))] * K
             asg = zsg = [0] * K
         elif trial < 20:  # digits at their extremes
             a = [rng.choice(ext) for _ in range(K)]
@@ -157,24 +150,25 @@ def test_mma_row_exact(lib):
             asg = [rng.randint(0, 1)] * K
             zsg = [rng.randint(0, 1)] * K
         else:
-            a = [rng.getrandbits(FBITS) for _ in range(K)]
-            z = [rng.getrandbits(rng.choice((FBITS, 60, 40))) for _ in range(K)]
+            a = [rng.getrandbits(69) for _ in range(K)]
+            z = [rng.getrandbits(rng.choice((69, 60, 40))) for _ in range(K)]
             asg = [rng.randint(0, 1) for _ in range(K)]
             zsg = [rng.randint(0, 1) for _ in range(K)]
         X, ex, acc = _row(lib, a, asg, z, zsg)
         assert acc == ex, "an fp32 accumulator was rounded"
-        assert max(abs(v) for v in ex) < 9 * 2**20  # 2^23.17
+        assert max(abs(v) for v in ex) < 2**22
+        if trial == 0:
+            assert ex[SL - 1] == SL * K * 63 * 63  # 2^21.3
         # kept pairs from Python's own balanced digits
         kept = 0
         for k in range(K):
             da = [(-x if asg[k] else x) for x in _balanced(a[k])]
             dz = [(-x if zsg[k] else x) for x in _balanced(z[k])]
             for s in range(SL):
-                for s2 in range(SL):
-                    if s + s2 < ACC:
-                        kept += da[s] * dz[s2] * BASE ** (ACC - 1 - s - s2)
+                for s2 in range(SL - s):
+                    kept += da[s] * dz[s2] * 128 ** (SL - 1 - s - s2)
         assert X == kept
-        exact = Fraction(sum((-1) ** (asg[k] ^ zsg[k]) * a[k] * z[k] for k in range(K)), BASE ** (2 * SL - 2 - (ACC - 1)))
+        exact = Fraction(sum((-1) ** (asg[k] ^ zsg[k]) * a[k] * z[k] for k in range(K)), 128 ** (SL - 1))
         assert abs(exact - X) <= K * drop
 
 
