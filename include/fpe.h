@@ -273,9 +273,11 @@ fpe_status fpe_batch_autotune(fpe_batch_t B, const double *z_re, const double *z
  *
  * fpe_set_tensor_path: min_window in {0} or [32, 2^30]; 0 turns the path
  *   off.  Default 384 (below a few hundred terms the FP64 kernels are
- *   cheaper than building a point's slices).  Applies to later fpe_eval
- *   calls of that handle (not to fpe_eval_noalloc, the batch or the gradient
- *   paths).
+ *   cheaper than building a point's slices), and by default only on calls
+ *   of at least 32768 points (the path's planning is a fixed cost of about
+ *   ten launches); a value set here applies to calls of every size.
+ *   Applies to later fpe_eval calls of that handle (not to fpe_eval_noalloc,
+ *   the batch or the gradient paths).
  *   FPE_ERR_INVALID_ARG for a NULL handle or a value out of range.
  * fpe_get_tensor_path: the handle's current min_window, and in *n_pieces the
  *   number of its pieces that qualify (0: the path never runs for it).

@@ -347,6 +347,7 @@ fpe_status fpe_set_tensor_path(fpe_poly_t P, int64_t min_window) {
     return FPE_ERR_INVALID_ARG;
   }
   P->tune.tc_min_window = min_window;
+  P->tune.tc_min_points = 0;  // an explicit setting applies to calls of every size
   return FPE_OK;
 }
 

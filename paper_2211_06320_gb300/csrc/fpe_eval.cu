@@ -1191,7 +1191,7 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
   const int n = (int)n64;
   Workspace &w = P->ws;
   const bool cz = z_im != nullptr;
-  const bool tc = allow_tc && tc_enabled(P, cz);
+  const bool tc = allow_tc && tc_enabled(P, cz, n64);
   if (tc && (s = ensure_tc_workspace(P, n64)) != FPE_OK) return s;
   w.nbins = tc ? kNumBins + P->dev.n_tc * kTcBinsPerPiece : kNumBins;  // bins of the pieces that exist
   const long long tcw = tc ? (long long)P->tune.tc_min_window : 0;

@@ -68,6 +68,7 @@ struct Tuning {
   int64_t long_window = kLongWindow;
   int64_t lane_chunk = kMaxLaneChunk;
   int64_t tc_min_window = 384;  // tensor-core window sums for windows of at least this many terms (0: off)
+  int64_t tc_min_points = 32768;  // ... on calls of at least this many points (0 once set explicitly)
   int64_t group_span() const { return 32 * lane_chunk; }
 };
 
@@ -250,7 +251,7 @@ fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, 
                         cudaStream_t st);
 // fpe_tc.cu: the tensor-core window sums of the points launch_front marked kPointTC
 // (tc_plan runs before the other window kernels: it hands back tiles it rejects)
-bool tc_enabled(const fpe_poly_s *P, bool complex_points);
+bool tc_enabled(const fpe_poly_s *P, bool complex_points, int64_t n);
 fpe_status ensure_tc_workspace(fpe_poly_s *P, int64_t n);
 fpe_status launch_tc_groups(fpe_poly_s *P, int n, cudaStream_t st);
 fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st);

@@ -88,13 +88,19 @@ def test_sphere_points_unit_disk(env):
 
 
 def test_default_threshold(env):
-    """The default setting (windows of 384 terms or more) on sphere points."""
+    """The default setting (windows of 384 terms or more) on sphere points;
+    a call below 32768 points leaves the path off unless it was set."""
     torch, F = env
     rng = np.random.default_rng(108)
     coef = _flat_disk(1 << 16, rng)
     pts = W.sphere_points(1 << 14, rng)
     P = F.fpe_precondition(coef.re, coef.im)
     assert F.fpe_get_tensor_path(P)["min_window"] == 384
+    _, _, st = _eval(env, P, pts.re, pts.im)
+    assert st["points"] == 0  # 2^14 points: below the default's size rule
+    big = W.sphere_points(1 << 15, rng)
+    _, _, st = _eval(env, P, big.re, big.im)
+    assert st["points"] > 0
     _check(env, coef, pts.re, pts.im, min_tc_points=512, min_window=384)
 
 
@@ -106,6 +112,7 @@ def test_reproducible_and_same_as_fp64_path(env):
     coef = _flat_disk(3000, rng)
     pts = W.sphere_points(20000, rng)
     P = F.fpe_precondition(coef.re, coef.im)
+    F.fpe_set_tensor_path(P, 384)  # the default threshold, on a call below the default's 32768 points
     a, nta, st = _eval(env, P, pts.re, pts.im)
     b, _, _ = _eval(env, P, pts.re, pts.im)
     assert st["points"] > 0
