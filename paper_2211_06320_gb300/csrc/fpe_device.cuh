@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <limits.h>
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -15,11 +16,20 @@
 namespace fpe {
 
 // 2^k for k in [-1022, 1023], built from the exponent field (no FP64 op).
-__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+__host__ __device__ __forceinline__ double pow2i(int k) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)(k + 1023) << 52);
+#else
+  const unsigned long long u = (unsigned long long)(k + 1023) << 52;
+  double d;
+  memcpy(&d, &u, 8);
+  return d;
+#endif
+}
 
 // x * 2^k, exact whenever the result is a normal double; saturates to 0 or
 // inf beyond the range (one multiply in the common case, at most three).
-__device__ __forceinline__ double scale2(double x, int k) {
+__host__ __device__ __forceinline__ double scale2(double x, int k) {
   if (k >= -1022 && k <= 1023) return x * pow2i(k);
   k = max(-3000, min(3000, k));
   int k1 = k / 3, k2 = (k - k1) / 2, k3 = k - k1 - k2;
@@ -35,6 +45,118 @@ __device__ __forceinline__ int frexp_exp(double x) {
   frexp(x, &f);
   return f;
 }
+
+// ---------------------------------------------------------------------------
+// Rounding-error certificates of the FP64 window sums (a posteriori, rigorous).
+//
+// Each FP64 Horner pass with an exact multiplier w runs, beside the value, two
+// FP32 recurrences on pipes the FP64-bound loops leave idle:
+//   E <- |w| E + sum over the step's rounded results r of 2^e(r)   (rounded up)
+//   S <- |w| S + |b_k|                                             (rounded down)
+// with e(r) = floor(log2 |r|), both scaled by 2^kMagOff.  A rounding to
+// nearest that returns r errs by at most 2^(e(r) - 53), and the errors of
+// step k reach the result multiplied by w^(k - lo) exactly, so
+//   |computed - exact| <= 2^-53 2^-kMagOff E   and   S <= 2^kMagOff sum |b_k| |w|^(k - lo).
+// Magnitudes come from the upper word of a double by integer operations:
+// err_mag(r) = 2^(e(r) + kMagOff) with floor 2^-126 (a bound for every
+// smaller or zero result) and +inf above the FP32 range; mag_lo(x) <= |x|
+// 2^kMagOff <= mag_up(x) (mantissa cut to 20 bits, and one unit added for
+// mag_up; 0 or 2^-126 below the FP32 range).  A window
+// whose values leave the FP32 window [2^-186, 2^68] fails its certificate
+// and is summed again exactly.
+// ---------------------------------------------------------------------------
+constexpr int kMagOff = 60;
+constexpr int kMagBias = (1023 - 127 - kMagOff) << 20;  // double exponent field -> float exponent field
+
+__host__ __device__ __forceinline__ int dbl_hi(double x) {
+#ifdef __CUDA_ARCH__
+  return __double2hiint(x);
+#else
+  unsigned long long u;
+  memcpy(&u, &x, 8);
+  return (int)(u >> 32);
+#endif
+}
+__host__ __device__ __forceinline__ float bits_float(int b) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ float err_mag(double r) {
+  const int t = (dbl_hi(r) & 0x7ff00000) - kMagBias;
+  return bits_float(min(max(t, 1 << 20), 255 << 20) << 3);
+}
+// upper bound of |x| 2^kMagOff (mantissa cut to 20 bits plus one unit; floor
+// 2^-126, +inf above the FP32 range)
+__host__ __device__ __forceinline__ float mag_up(double x) {
+  const int t = (dbl_hi(x) & 0x7fffffff) - kMagBias;
+  return bits_float((min(max(t, (1 << 20) - 1), (255 << 20) - 1) + 1) << 3);
+}
+__host__ __device__ __forceinline__ int hi_abs(double x) { return dbl_hi(x) & 0x7fffffff; }
+__host__ __device__ __forceinline__ float mag_lo_hi(int habs) {
+  const int t = habs - kMagBias;
+  return bits_float(min(max(t, 0), (254 << 20) | 0xfffff) << 3);
+}
+// lower bound of |br + i bi| 2^kMagOff: max(|br|, |bi|)
+__host__ __device__ __forceinline__ float mag_lo2(double br, double bi) {
+  return mag_lo_hi(max(hi_abs(br), hi_abs(bi)));
+}
+
+// FP32 operations rounded up / down (device: the rounding-mode instructions;
+// host: round to nearest, then one step outward)
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ float add_up(float a, float b) { return __fadd_ru(a, b); }
+__device__ __forceinline__ float fma_up(float a, float b, float c) { return __fmaf_ru(a, b, c); }
+__device__ __forceinline__ float fma_dn(float a, float b, float c) { return __fmaf_rd(a, b, c); }
+__device__ __forceinline__ float mul_up(float a, float b) { return __fmul_ru(a, b); }
+__device__ __forceinline__ float mul_dn(float a, float b) { return __fmul_rd(a, b); }
+__device__ __forceinline__ float sqrt_up(float a) { return __fsqrt_ru(a); }
+__device__ __forceinline__ float sqrt_dn(float a) { return __fsqrt_rd(a); }
+__device__ __forceinline__ float f_up(double x) { return __double2float_ru(x); }
+__device__ __forceinline__ float f_dn(double x) { return __double2float_rd(x); }
+#else
+inline float add_up(float a, float b) { return nextafterf(a + b, INFINITY); }
+inline float fma_up(float a, float b, float c) { return nextafterf(fmaf(a, b, c), INFINITY); }
+inline float fma_dn(float a, float b, float c) { return fmaxf(0.0f, nextafterf(fmaf(a, b, c), -INFINITY)); }
+inline float mul_up(float a, float b) { return nextafterf(a * b, INFINITY); }
+inline float mul_dn(float a, float b) { return fmaxf(0.0f, nextafterf(a * b, -INFINITY)); }
+inline float sqrt_up(float a) { return nextafterf(sqrtf(a), INFINITY); }
+inline float sqrt_dn(float a) { return fmaxf(0.0f, nextafterf(sqrtf(a), -INFINITY)); }
+inline float f_up(double x) {
+  float f = (float)x;
+  return (double)f < x ? nextafterf(f, INFINITY) : f;
+}
+inline float f_dn(double x) {
+  float f = (float)x;
+  return (double)f > x ? nextafterf(f, -INFINITY) : f;
+}
+#endif
+
+// bounds of |xr + i xi| (no scaling; x a multiplier of moderate size)
+__host__ __device__ __forceinline__ float cabs_up(double xr, double xi) {
+  const float a = f_up(fabs(xr)), b = f_up(fabs(xi));
+  return sqrt_up(fma_up(a, a, mul_up(b, b)));
+}
+__host__ __device__ __forceinline__ float cabs_dn(double xr, double xi) {
+  const float a = f_dn(fabs(xr)), b = f_dn(fabs(xi));
+  return sqrt_dn(fma_dn(a, a, mul_dn(b, b)));
+}
+// bounds of |(hr + lr) + i (hi + li)| for a double-double complex multiplier
+__host__ __device__ __forceinline__ float cabs_up_dd(double hr, double lr, double hi, double li) {
+  const float a = add_up(f_up(fabs(hr)), f_up(fabs(lr))), b = add_up(f_up(fabs(hi)), f_up(fabs(li)));
+  return sqrt_up(fma_up(a, a, mul_up(b, b)));
+}
+__host__ __device__ __forceinline__ float cabs_dn_dd(double hr, double lr, double hi, double li) {
+  const float a = fmaxf(fma_dn(-1.0f, f_up(fabs(lr)), f_dn(fabs(hr))), 0.0f);
+  const float b = fmaxf(fma_dn(-1.0f, f_up(fabs(li)), f_dn(fabs(hi))), 0.0f);
+  return sqrt_dn(fma_dn(a, a, mul_dn(b, b)));
+}
+// 2^k as a float for |k| <= 126
+__host__ __device__ __forceinline__ float pow2f_bits(int k) { return bits_float((k + 127) << 23); }
 
 struct dd {
   double hi, lo;
@@ -462,7 +584,7 @@ __host__ __device__ __forceinline__ double low74_scaled(u128 x) {
 }
 
 // extended double-double from a 128-bit mantissa pair
-__device__ __forceinline__ xdd xdd_from_xint(const xint &v) {
+__host__ __device__ __forceinline__ xdd xdd_from_xint(const xint &v) {
   // component = (-1)^s (H + L 2^-74) 2^(e - 52), H = X >> 74 (53 bits), L = X mod 2^74
   const double hx = (double)(unsigned long long)(v.x >> 74);
   const double lx = low74_scaled(v.x);

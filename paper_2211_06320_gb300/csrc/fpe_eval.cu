@@ -34,6 +34,7 @@
 
 #include "fpe_device.cuh"
 #include "fpe_internal.h"
+#include "fpe_window.cuh"
 
 namespace fpe {
 
@@ -260,61 +261,6 @@ __global__ void k_scatter(DevPoly P, int n, const double *__restrict__ zre, cons
 // window sums (Alg. A_p: Q_lambda, eq. reducedQlambda)
 // ---------------------------------------------------------------------------
 
-// Horner over trimmed indices [lo, hi] on the rescaled coefficients b:
-// returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-lo) = h * 2^rho(lo).
-// Piece j runs at w_j = 2^beta_j z; entering piece j from j+1 multiplies h by
-// 2^delta_j (both exact).  Every term of a window has |h| <= L 2^(T + 66),
-// so nothing overflows.
-template <bool CC, bool CZ, bool COMP>
-__device__ __forceinline__ void window_horner(const DevPoly &P, const double *__restrict__ b, double zr, double zi,
-                                              long long lo, long long hi, double &hr, double &hm, double &cr,
-                                              double &cm, long long &rho_lo) {
-  int j = P.piece_first[hi >> P.log2_piece];
-  while (P.piece_k0[j + 1] <= hi) ++j;
-  if (CC) {
-    double2 c = reinterpret_cast<const double2 *>(b)[hi];
-    hr = c.x;
-    hm = c.y;
-  } else {
-    hr = b[hi];
-    hm = 0.0;
-  }
-  cr = 0.0;
-  cm = 0.0;
-  long long k = hi - 1;
-  long long k0 = max((long long)P.piece_k0[j], lo);
-  while (true) {
-    const int beta = P.piece_beta[j];
-    const double wr = scale2(zr, beta);
-    const double wi = CZ ? scale2(zi, beta) : 0.0;
-    if (CC) {
-      const double2 *b2 = reinterpret_cast<const double2 *>(b);
-#pragma unroll 4
-      for (; k >= k0; --k) {
-        double2 c = __ldg(&b2[k]);
-        horner_step<CC, CZ, COMP>(hr, hm, cr, cm, wr, wi, c.x, c.y);
-      }
-    } else {
-#pragma unroll 4
-      for (; k >= k0; --k) {
-        double c = __ldg(&b[k]);
-        horner_step<CC, CZ, COMP>(hr, hm, cr, cm, wr, wi, c, 0.0);
-      }
-    }
-    if (k < lo) break;
-    --j;  // k == piece_k0[j + 1] - 1: enter piece j
-    const double s = pow2i(P.piece_delta[j]);
-    hr *= s;
-    hm *= s;
-    if (COMP) {
-      cr *= s;
-      cm *= s;
-    }
-    k0 = max((long long)P.piece_k0[j], lo);
-  }
-  rho_lo = P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
-}
-
 __device__ __forceinline__ fpe_xc64 special_value(const DevPoly &P, int flags) {
   fpe_xc64 o;
   if (flags & kPointNonFinite) {
@@ -343,143 +289,28 @@ __device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, 
   }
 }
 
-// Bottom-up Horner over trimmed indices [lo, hi] with multiplier 1/z:
-// returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-hi) = h * 2^rho(hi).
-// 1/z = u 2^ue with u in extended double-double (u^3, u^4 likewise, each
-// with its own exponent).  Within piece j the step from k-1 to
-// k multiplies by v_j = 2^-beta_j / z; crossing from piece j to j+1 first
-// scales h by 2^-delta_j.  A single step is 8 FMA for complex z and
-// coefficients (v in double-double).
-//
-// Blocks of four.  With w = 1/v = 2^beta_j z (exact in FP64), four steps
-// from K to K+4 inside a piece are
-//   h_{K+4} = v^4 h_K + v^3 s_K,  s_K = b_{K+1} + w (b_{K+2} + w (b_{K+3} + w b_{K+4})),
-// so G = w^3 h obeys G_{K+4} = v^4 G_K + s_K (the first block of a run
-// starts from G = v h_K + s_K, and h = v^3 G at its end).  s_K is a top-down
-// FP64 Horner with the exact multiplier (3 complex FMA, rounding within
-// 3u of the block's term magnitudes) and the block step multiplies by v^4 in
-// double-double: 20 FMA per four terms instead of 32.  u3 = u^3, u4 = u^4.
-template <bool CC, bool CZ>
-__device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b, const xdd &u,
-                                                  const xdd &u3, const xdd &u4, bool blocks, int ue, double zr,
-                                                  double zi, long long lo, long long hi, double &hr, double &hm,
-                                                  long long &rho_hi) {
-  int j = P.piece_first[lo >> P.log2_piece];
-  while (P.piece_k0[j + 1] <= lo) ++j;
-  auto load = [&](long long k, double &br, double &bi) {
-    if (CC) {
-      const double2 c = __ldg(reinterpret_cast<const double2 *>(b) + k);
-      br = c.x;
-      bi = c.y;
-    } else {
-      br = __ldg(b + k);
-      bi = 0.0;
-    }
-  };
-  load(lo, hr, hm);
-  long long k = lo + 1;
-  while (k <= hi) {
-    const int beta = P.piece_beta[j];
-    const int sh = ue - beta;
-    const int s1 = (int)u.e + sh;
-    const double vhr = scale2(u.rh, s1), vlr = scale2(u.rl, s1);
-    const double vhi = CZ ? scale2(u.ih, s1) : 0.0, vli = CZ ? scale2(u.il, s1) : 0.0;
-    const long long kend = min((long long)P.piece_k0[j + 1] - 1, hi);
-    // h <- h v + (br + i bi), v in double-double
-    auto step_v = [&](double &xr, double &xm, double br, double bi) {
-      double nr, ni;
-      if (CZ) {
-        nr = fma(xr, vhr, fma(-xm, vhi, fma(xr, vlr, fma(-xm, vli, br))));
-        ni = fma(xr, vhi, fma(xm, vhr, fma(xr, vli, fma(xm, vlr, bi))));
-      } else {
-        nr = fma(xr, vhr, fma(xr, vlr, br));
-        ni = (CC || CZ) ? fma(xm, vhr, fma(xm, vlr, bi)) : 0.0;
-      }
-      xr = nr;
-      xm = ni;
-    };
-    if (blocks && kend - k + 1 >= 8 && sh > -200 && sh < 200) {  // v^4 and its low part stay normal
-      const double wr = scale2(zr, beta), wi = CZ ? scale2(zi, beta) : 0.0;
-      const int s4 = (int)u4.e + 4 * sh;
-      const double ahr = scale2(u4.rh, s4), alr = scale2(u4.rl, s4);
-      const double ahi = CZ ? scale2(u4.ih, s4) : 0.0, ali = CZ ? scale2(u4.il, s4) : 0.0;
-      // s over [k, k + 3] by top-down Horner with w
-      auto block_sum = [&](long long k0, double &sr, double &si) {
-        double cr, ci, dr = 0.0, dm = 0.0;
-        load(k0 + 3, sr, si);
-#pragma unroll
-        for (int t = 2; t >= 0; --t) {
-          load(k0 + t, cr, ci);
-          horner_step<CC, CZ, false>(sr, si, dr, dm, wr, wi, cr, ci);
-        }
-      };
-      double sr, si;
-      block_sum(k, sr, si);
-      step_v(hr, hm, sr, si);  // G = v h + s
-      k += 4;
-      for (; k + 3 <= kend; k += 4) {
-        block_sum(k, sr, si);
-        double nr, ni;  // G <- v^4 G + s
-        if (CZ) {
-          nr = fma(hr, ahr, fma(-hm, ahi, fma(hr, alr, fma(-hm, ali, sr))));
-          ni = fma(hr, ahi, fma(hm, ahr, fma(hr, ali, fma(hm, alr, si))));
-        } else {
-          nr = fma(hr, ahr, fma(hr, alr, sr));
-          ni = (CC || CZ) ? fma(hm, ahr, fma(hm, alr, si)) : 0.0;
-        }
-        hr = nr;
-        hm = ni;
-      }
-      // h = v^3 G
-      const int s3 = (int)u3.e + 3 * sh;
-      const double chr = scale2(u3.rh, s3), clr = scale2(u3.rl, s3);
-      const double chi = CZ ? scale2(u3.ih, s3) : 0.0, cli = CZ ? scale2(u3.il, s3) : 0.0;
-      double nr, ni;
-      if (CZ) {
-        nr = fma(hr, chr, fma(-hm, chi, fma(hr, clr, -hm * cli)));
-        ni = fma(hr, chi, fma(hm, chr, fma(hr, cli, hm * clr)));
-      } else {
-        nr = fma(hr, chr, hr * clr);
-        ni = (CC || CZ) ? fma(hm, chr, hm * clr) : 0.0;
-      }
-      hr = nr;
-      hm = ni;
-    }
-    for (; k <= kend; ++k) {
-      double br, bi;
-      load(k, br, bi);
-      step_v(hr, hm, br, bi);
-    }
-    if (k > hi) break;
-    // k is the first index of piece j + 1: rescale, one step with v_j, move on
-    const double s2 = pow2i(-P.piece_delta[j]);
-    hr *= s2;
-    hm *= s2;
-    double br, bi;
-    load(k, br, bi);
-    step_v(hr, hm, br, bi);
-    ++k;
-    ++j;
-  }
-  rho_hi = P.piece_rho0[j] + (long long)P.piece_beta[j] * (hi - P.piece_k0[j]);
-}
-
 // sum_{k=lo}^{hi} a_k z^(k - base) in extended double-double for a range on
 // either side of the peak kl or straddling it.  The part at or above kl is
 // summed top-down (relative to z^max(kl, lo)), the part below bottom-up
 // (relative to z^(its top index)); base is kl - 1 when both parts exist.
+// ok: both parts passed their rounding-error certificates (cert_pass); the
+// caller sums the range again on the integer pipe when it is false.
 template <bool CC, bool CZ>
 __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
-                                          const xint &u, long long lo, long long hi, long long kl, long long &base) {
+                                          const xint &u, long long lo, long long hi, long long kl, long long &base,
+                                          bool &ok) {
   constexpr long long kBlockMin = 16;  // below-peak terms from which the blocked pass pays for u^3, u^4
   xint X = xint_norm(0, 0, 0, 0, 0);
   const long long top_lo = max(kl, lo);
   const long long low_hi = min(top_lo - 1, hi);
   const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
+  ok = true;
   if (has_up) {
-    double hr, hm, cr, cm;
+    double hr, hm;
     long long rho;
-    window_horner<CC, CZ, false>(P, P.b, zr, zi, top_lo, hi, hr, hm, cr, cm, rho);
+    Cert ct;
+    window_horner<CC, CZ>(P, P.b, zr, zi, top_lo, hi, hr, hm, rho, ct);
+    ok = cert_pass(ct);
     X = xint_from_dd2(hr, 0.0, hm, 0.0, rho);
     base = top_lo;
   }
@@ -494,7 +325,9 @@ __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi
       u3 = xdd_from_xint(xint_mul(u2, u));
       u4 = xdd_from_xint(xint_sqr(u2));
     }
-    window_horner_rev<CC, CZ>(P, P.b, u1, u3, u4, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho);
+    Cert ct;
+    window_horner_rev<CC, CZ>(P, P.b, u1, u3, u4, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho, ct);
+    ok = ok && cert_pass(ct);
     if (has_up && (X.x || X.y)) X = xint_mul(X, xint_from_dd2(mr, 0.0, mi, 0.0, f));  // z^top_lo = z * z^low_hi
     X = xint_add(X, xint_from_dd2(hr, 0.0, hm, 0.0, rho));
     base = low_hi;
@@ -759,8 +592,14 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
         const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
         xint u = xint_norm(0, 0, 0, 0, 0);
         if (r.lo < r.kl) u = recip_xint(mr, mi);
-        const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base);
-        o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, r.zi, base + P.v, f)));
+        bool ok;
+        const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base, ok);
+        if (ok) {
+          o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, r.zi, base + P.v, f)));
+        } else {  // not certified: the exact integer-pipe sum
+          const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
+          o = xdd_out(xdd_mul(Y, xdd_pow_int(r.zr, r.zi, r.lo + P.v)));
+        }
       }
     }
   }
@@ -911,8 +750,12 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
     const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
     const xint u = recip_xint(mr, mi);
     long long base;
-    const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base);
-    if (chi < r.kl) {
+    bool ok;
+    const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base, ok);
+    if (!ok) {  // not certified: the chunk's exact integer-pipe sum, in its own slot
+      const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
+      sv = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
+    } else if (chi < r.kl) {
       carry = xint_mul(X, u);  // below the peak: X / z to the next slot
       carry.e -= f;
     } else if (base > clo) {
