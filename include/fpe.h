@@ -234,7 +234,7 @@ fpe_status fpe_eval_batch(const fpe_poly_t *P, int64_t npoly, const int64_t *pt_
  *   fpe_autotune).
  * fpe_autotune: times fpe_eval on the caller's n device points (z_re, z_im
  *   as in fpe_eval) at every setting of the grid long_window in {1024, 2048,
- *   4096, 8192} x lane_chunk in {256, 512, 1024, 2048}: one untimed call,
+ *   4096, 8192} x lane_chunk in {128, 256, 512, 1024, 2048}: one untimed call,
  *   then two calls between CUDA events on cuda_stream.  Keeps the fastest in
  *   the handle and returns it in *best (ms = its time per call).
  *   Synchronous; allocates and frees a temporary output array.  Errors as
@@ -296,6 +296,16 @@ fpe_status fpe_get_tensor_path(fpe_poly_t P, int64_t *min_window, int32_t *n_pie
  *   cuda_stream.  FPE_ERR_INVALID_ARG for NULL arguments or n < 6.
  */
 fpe_status fpe_tensor_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream);
+/*
+ * fpe_cert_stats: the rounding-error certificates of the handle's last
+ *   fpe_eval (default FP64 mode), in stats[0..1]: short windows whose FP64
+ *   sum failed its certificate and was summed again exactly on the integer
+ *   pipe, and lane chunks of long windows likewise.  The default mode's
+ *   values meet |P_gpu - P| <= 2^-50 sum |a_k||z|^k through these re-sums.
+ *   Zero for the other modes.  Waits for the work queued on cuda_stream.
+ *   FPE_ERR_INVALID_ARG for NULL arguments or n < 2.
+ */
+fpe_status fpe_cert_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream);
 
 /*
  * fpe_newton -- one Newton step N_P(z) = z - P(z)/P'(z) (§7.2, eq. newton) at n

@@ -40,7 +40,7 @@ EXPORTED = [
     "fpe_measure_fma_peak", "fpe_eval_noalloc", "fpe_batch_create", "fpe_batch_eval", "fpe_batch_sync",
     "fpe_batch_destroy", "fpe_newton", "fpe_grad_points", "fpe_grad_coeffs", "fpe_to_complex", "fpe_analyse",
     "fpe_set_tuning", "fpe_get_tuning", "fpe_autotune", "fpe_batch_set_tuning", "fpe_batch_autotune",
-    "fpe_set_tensor_path", "fpe_get_tensor_path", "fpe_tensor_stats", "fpe_measure_mma_peak",
+    "fpe_set_tensor_path", "fpe_get_tensor_path", "fpe_tensor_stats", "fpe_cert_stats", "fpe_measure_mma_peak",
 ]
 
 
@@ -113,6 +113,7 @@ def _load():
         "fpe_set_tensor_path": ([P, I64], I32),
         "fpe_get_tensor_path": ([P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32)], I32),
         "fpe_tensor_stats": ([P, ctypes.POINTER(I64), I32, P], I32),
+        "fpe_cert_stats": ([P, ctypes.POINTER(I64), I32, P], I32),
         "fpe_measure_mma_peak": ([I32, ctypes.POINTER(D)], I32),
     }
     for name, (args, res) in sig.items():
@@ -487,6 +488,17 @@ def fpe_tensor_stats(P: Poly, stream=None) -> dict:
     v = (ctypes.c_int64 * len(TENSOR_STATS))()
     _check(_load().fpe_tensor_stats(P.handle, v, len(TENSOR_STATS), _stream(stream)), "fpe_tensor_stats")
     return dict(zip(TENSOR_STATS, (int(x) for x in v)))
+
+
+CERT_STATS = ("resummed_windows", "resummed_chunks")
+
+
+def fpe_cert_stats(P: Poly, stream=None) -> dict:
+    """Windows and long-window chunks of the last fpe_eval whose FP64 sums
+    failed their rounding-error certificates and were summed again exactly."""
+    v = (ctypes.c_int64 * len(CERT_STATS))()
+    _check(_load().fpe_cert_stats(P.handle, v, len(CERT_STATS), _stream(stream)), "fpe_cert_stats")
+    return dict(zip(CERT_STATS, (int(x) for x in v)))
 
 
 def fpe_measure_mma_peak(reps: int = 5) -> float:

@@ -91,7 +91,7 @@ static fpe_status check_tuning(const fpe_tuning *t) {
 template <class Run>
 static fpe_status autotune_grid(Tuning &tune, double &tune_ms, Run run, cudaStream_t st, fpe_tuning *best) {
   static const int64_t kLW[] = {1024, 2048, 4096, 8192};
-  static const int64_t kLC[] = {256, 512, 1024, 2048};
+  static const int64_t kLC[] = {128, 256, 512, 1024, 2048};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);

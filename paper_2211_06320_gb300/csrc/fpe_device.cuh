@@ -59,13 +59,13 @@ __device__ __forceinline__ int frexp_exp(double x) {
 //   |computed - exact| <= 2^-53 2^-kMagOff E   and   S <= 2^kMagOff sum |b_k| |w|^(k - lo).
 // Magnitudes come from the upper word of a double by integer operations:
 // err_mag(r) = 2^(e(r) + kMagOff) with floor 2^-126 (a bound for every
-// smaller or zero result) and +inf above the FP32 range; mag_lo(x) <= |x|
-// 2^kMagOff <= mag_up(x) (mantissa cut to 20 bits, and one unit added for
-// mag_up; 0 or 2^-126 below the FP32 range).  A window
+// smaller or zero result) and +inf above the FP32 range; |x| 2^kMagOff <=
+// mag_up(x) (mantissa cut to 20 bits plus one unit; 2^-126 below the FP32
+// range).  The coefficients' magnitudes come from the host (coef_mag_lo in
+// fpe_internal.h, one float per coefficient).  A window
 // whose values leave the FP32 window [2^-186, 2^68] fails its certificate
 // and is summed again exactly.
 // ---------------------------------------------------------------------------
-constexpr int kMagOff = 60;
 constexpr int kMagBias = (1023 - 127 - kMagOff) << 20;  // double exponent field -> float exponent field
 
 __host__ __device__ __forceinline__ int dbl_hi(double x) {
@@ -96,16 +96,6 @@ __host__ __device__ __forceinline__ float mag_up(double x) {
   const int t = (dbl_hi(x) & 0x7fffffff) - kMagBias;
   return bits_float((min(max(t, (1 << 20) - 1), (255 << 20) - 1) + 1) << 3);
 }
-__host__ __device__ __forceinline__ int hi_abs(double x) { return dbl_hi(x) & 0x7fffffff; }
-__host__ __device__ __forceinline__ float mag_lo_hi(int habs) {
-  const int t = habs - kMagBias;
-  return bits_float(min(max(t, 0), (254 << 20) | 0xfffff) << 3);
-}
-// lower bound of |br + i bi| 2^kMagOff: max(|br|, |bi|)
-__host__ __device__ __forceinline__ float mag_lo2(double br, double bi) {
-  return mag_lo_hi(max(hi_abs(br), hi_abs(bi)));
-}
-
 // FP32 operations rounded up / down (device: the rounding-mode instructions;
 // host: round to nearest, then one step outward)
 #ifdef __CUDA_ARCH__
@@ -116,8 +106,6 @@ __device__ __forceinline__ float mul_up(float a, float b) { return __fmul_ru(a, 
 __device__ __forceinline__ float mul_dn(float a, float b) { return __fmul_rd(a, b); }
 __device__ __forceinline__ float sqrt_up(float a) { return __fsqrt_ru(a); }
 __device__ __forceinline__ float sqrt_dn(float a) { return __fsqrt_rd(a); }
-__device__ __forceinline__ float f_up(double x) { return __double2float_ru(x); }
-__device__ __forceinline__ float f_dn(double x) { return __double2float_rd(x); }
 #else
 inline float add_up(float a, float b) { return nextafterf(a + b, INFINITY); }
 inline float fma_up(float a, float b, float c) { return nextafterf(fmaf(a, b, c), INFINITY); }
@@ -126,33 +114,40 @@ inline float mul_up(float a, float b) { return nextafterf(a * b, INFINITY); }
 inline float mul_dn(float a, float b) { return fmaxf(0.0f, nextafterf(a * b, -INFINITY)); }
 inline float sqrt_up(float a) { return nextafterf(sqrtf(a), INFINITY); }
 inline float sqrt_dn(float a) { return fmaxf(0.0f, nextafterf(sqrtf(a), -INFINITY)); }
-inline float f_up(double x) {
-  float f = (float)x;
-  return (double)f < x ? nextafterf(f, INFINITY) : f;
-}
-inline float f_dn(double x) {
-  float f = (float)x;
-  return (double)f > x ? nextafterf(f, -INFINITY) : f;
-}
 #endif
+
+// |x| 2^s as a float rounded up / down, from x's upper word by integer
+// operations (no FP64 instruction): mantissa cut to 20 bits (plus one unit
+// for the upper bound); below the FP32 range 2^-126 / 0, above it +inf / the
+// largest float.
+template <int s>
+__host__ __device__ __forceinline__ float fabs_up(double x) {
+  const int t = (dbl_hi(x) & 0x7fffffff) - ((1023 - 127 - s) << 20);
+  return bits_float((min(max(t, (1 << 20) - 1), (255 << 20) - 1) + 1) << 3);
+}
+template <int s>
+__host__ __device__ __forceinline__ float fabs_dn(double x) {
+  const int t = (dbl_hi(x) & 0x7fffffff) - ((1023 - 127 - s) << 20);
+  return bits_float(min(max(t, 0), (254 << 20) | 0xfffff) << 3);
+}
 
 // bounds of |xr + i xi| (no scaling; x a multiplier of moderate size)
 __host__ __device__ __forceinline__ float cabs_up(double xr, double xi) {
-  const float a = f_up(fabs(xr)), b = f_up(fabs(xi));
+  const float a = fabs_up<0>(xr), b = fabs_up<0>(xi);
   return sqrt_up(fma_up(a, a, mul_up(b, b)));
 }
 __host__ __device__ __forceinline__ float cabs_dn(double xr, double xi) {
-  const float a = f_dn(fabs(xr)), b = f_dn(fabs(xi));
+  const float a = fabs_dn<0>(xr), b = fabs_dn<0>(xi);
   return sqrt_dn(fma_dn(a, a, mul_dn(b, b)));
 }
 // bounds of |(hr + lr) + i (hi + li)| for a double-double complex multiplier
 __host__ __device__ __forceinline__ float cabs_up_dd(double hr, double lr, double hi, double li) {
-  const float a = add_up(f_up(fabs(hr)), f_up(fabs(lr))), b = add_up(f_up(fabs(hi)), f_up(fabs(li)));
+  const float a = add_up(fabs_up<0>(hr), fabs_up<0>(lr)), b = add_up(fabs_up<0>(hi), fabs_up<0>(li));
   return sqrt_up(fma_up(a, a, mul_up(b, b)));
 }
 __host__ __device__ __forceinline__ float cabs_dn_dd(double hr, double lr, double hi, double li) {
-  const float a = fmaxf(fma_dn(-1.0f, f_up(fabs(lr)), f_dn(fabs(hr))), 0.0f);
-  const float b = fmaxf(fma_dn(-1.0f, f_up(fabs(li)), f_dn(fabs(hi))), 0.0f);
+  const float a = fmaxf(fma_dn(-1.0f, fabs_up<0>(lr), fabs_dn<0>(hr)), 0.0f);
+  const float b = fmaxf(fma_dn(-1.0f, fabs_up<0>(li), fabs_dn<0>(hi)), 0.0f);
   return sqrt_dn(fma_dn(a, a, mul_dn(b, b)));
 }
 // 2^k as a float for |k| <= 126

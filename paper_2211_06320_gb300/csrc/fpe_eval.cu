@@ -295,7 +295,7 @@ __device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, 
 // (relative to z^(its top index)); base is kl - 1 when both parts exist.
 // ok: both parts passed their rounding-error certificates (cert_pass); the
 // caller sums the range again on the integer pipe when it is false.
-template <bool CC, bool CZ>
+template <bool CC, bool CZ, bool LONG>
 __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
                                           const xint &u, long long lo, long long hi, long long kl, long long &base,
                                           bool &ok) {
@@ -304,12 +304,15 @@ __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi
   const long long top_lo = max(kl, lo);
   const long long low_hi = min(top_lo - 1, hi);
   const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
+  constexpr long long kTopBlockMin = 32;  // top-part terms from which blocks of eight may pay for z^8
   ok = true;
   if (has_up) {
     double hr, hm;
     long long rho;
     Cert ct;
-    window_horner<CC, CZ>(P, P.b, zr, zi, top_lo, hi, hr, hm, rho, ct);
+    const bool blocks8 = LONG && hi - top_lo + 1 >= kTopBlockMin;
+    const xdd z8 = blocks8 ? xdd_from_xint(xint_pow_z(zr, zi, 8, f)) : xdd_zero();
+    window_horner<CC, CZ, LONG>(P, P.b, zr, zi, top_lo, hi, z8, blocks8, hr, hm, rho, ct);
     ok = cert_pass(ct);
     X = xint_from_dd2(hr, 0.0, hm, 0.0, rho);
     base = top_lo;
@@ -319,14 +322,18 @@ __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi
     long long rho;
     const bool blocks = low_hi - lo + 1 >= kBlockMin;
     const xdd u1 = xdd_from_xint(u);
-    xdd u3 = u1, u4 = u1;
-    if (blocks) {  // powers of 1/m on the integer pipe
-      const xint u2 = xint_sqr(u);
-      u3 = xdd_from_xint(xint_mul(u2, u));
-      u4 = xdd_from_xint(xint_sqr(u2));
+    xdd up[4] = {u1, u1, u1, u1};
+    if (blocks) {  // powers u^3, u^4 (LONG: u^7, u^8) of 1/m on the integer pipe
+      const xint u2 = xint_sqr(u), u3 = xint_mul(u2, u), u4 = xint_sqr(u2);
+      up[0] = xdd_from_xint(u3);
+      up[1] = xdd_from_xint(u4);
+      if (LONG) {
+        up[2] = xdd_from_xint(xint_mul(u4, u3));
+        up[3] = xdd_from_xint(xint_sqr(u4));
+      }
     }
     Cert ct;
-    window_horner_rev<CC, CZ>(P, P.b, u1, u3, u4, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho, ct);
+    window_horner_rev<CC, CZ, LONG>(P, P.b, u1, up, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho, ct);
     ok = ok && cert_pass(ct);
     if (has_up && (X.x || X.y)) X = xint_mul(X, xint_from_dd2(mr, 0.0, mi, 0.0, f));  // z^top_lo = z * z^low_hi
     X = xint_add(X, xint_from_dd2(hr, 0.0, hm, 0.0, rho));
@@ -561,12 +568,67 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
   return int_tail<CC, CZ>(P, h, zr, zi, hi, lo);
 }
 
+// Sparse windows: when at most a quarter of [lo, hi] lies in G_p, Horner's
+// scheme runs over the good indices alone, X <- X z^(k' - k) + a_k, in 128-bit
+// fixed point on the integer pipe (every product and sum rounds at 2^-120 or
+// less of its operands, so the result is within L 2^-119 S of the window
+// sum; no certificate is needed).  The powers come by binary powering; a_k =
+// b_k 2^rho(k) exactly.  Returns sum_{good k in [lo, hi]} a_k z^(k - lo).
+__device__ __forceinline__ bool sparse_window(const DevPoly &P, long long lo, long long hi) {
+  const long long g = P.gcount[hi + 1] - P.gcount[lo];
+  return 4 * g < hi - lo + 1;
+}
+template <bool CC>
+__device__ __forceinline__ xint window_sum_sparse(const DevPoly &P, double zr, double zi, int f, long long lo,
+                                                  long long hi) {
+  const int g0 = P.gcount[lo], g1 = P.gcount[hi + 1];
+  xint X = xint_norm(0, 0, 0, 0, 0);
+  if (g0 >= g1) return X;
+  auto coef = [&](long long k, int &j) {  // a_k as an xint; j: a piece at or above k's, moved down to it
+    while (P.piece_k0[j] > k) --j;
+    const long long rho = P.piece_rho0[j] + (long long)P.piece_beta[j] * (k - P.piece_k0[j]);
+    double br, bi = 0.0;
+    if (CC) {
+      const double2 c = __ldg(reinterpret_cast<const double2 *>(P.b) + k);
+      br = c.x;
+      bi = c.y;
+    } else {
+      br = __ldg(P.b + k);
+    }
+    return xint_from_dd2(br, 0.0, bi, 0.0, rho);
+  };
+  long long k = __ldg(P.good_idx + g1 - 1);
+  int j = P.piece_first[k >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= k) ++j;
+  X = coef(k, j);
+  for (int g = g1 - 2; g >= g0; --g) {
+    const long long k2 = __ldg(P.good_idx + g);
+    X = xint_add(xint_mul(X, xint_pow_z(zr, zi, k - k2, f)), coef(k2, j));
+    k = k2;
+  }
+  if (k > lo && (X.x || X.y)) X = xint_mul(X, xint_pow_z(zr, zi, k - lo, f));
+  return X;
+}
+
+// Appends bucketed position q to the list of windows to sum again exactly
+// (one atomic per warp for the lanes that call it together).
+__device__ __forceinline__ void list_resum(uint32_t *cnt, uint32_t *list, int q) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(&cnt[kCntResum], (unsigned)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)q;
+}
+
 // One point of a short window (L <= the long-window threshold), or a special point: its
-// window's sum, then the power z^(base + v) in extended double-double.
+// window's sum, then the power z^(base + v) in extended double-double.  A default-mode
+// FP64 sum that fails its certificate is listed (resum, at bucketed position q) for
+// k_resum and its point left to it.
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
 __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__restrict__ table,
-                                          const PointRec &r, fpe_xc64 *__restrict__ out, int32_t *nterms,
-                                          int32_t *bits_lost) {
+                                          const PointRec &r, int q, uint32_t *cnt, uint32_t *resum,
+                                          fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
   const DevPoly &P = BATCH ? table[r.pid] : P0;
   fpe_xc64 o;
   if (r.flags) {
@@ -584,7 +646,11 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
       o.im = v.i;
       o.e = v.e;
     } else {
-      if (ACC) {
+      if (sparse_window(P, r.lo, r.hi)) {
+        const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+        const xint X = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, r.lo, r.hi);
+        o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, CZ ? r.zi : 0.0, r.lo + P.v, f)));
+      } else if (ACC) {
         const xdd X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
         o = xdd_out(xdd_mul(X, xdd_pow_int(r.zr, r.zi, base + P.v)));
       } else {  // bookkeeping in fixed point (integer pipe): 1/z, its powers, the final product
@@ -593,13 +659,12 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
         xint u = xint_norm(0, 0, 0, 0, 0);
         if (r.lo < r.kl) u = recip_xint(mr, mi);
         bool ok;
-        const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base, ok);
-        if (ok) {
-          o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, r.zi, base + P.v, f)));
-        } else {  // not certified: the exact integer-pipe sum
-          const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
-          o = xdd_out(xdd_mul(Y, xdd_pow_int(r.zr, r.zi, r.lo + P.v)));
+        const xint X = range_sum<CC, CZ, false>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base, ok);
+        if (!ok) {  // not certified: k_resum sums the window exactly
+          list_resum(cnt, resum, q);
+          return;
         }
+        o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, r.zi, base + P.v, f)));
       }
     }
   }
@@ -674,19 +739,21 @@ template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
 __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, const DevPoly *__restrict__ table,
                                                                     int n, const PointRec *__restrict__ rec,
                                                                     fpe_xc64 *__restrict__ out, int32_t *nterms,
-                                                                    int32_t *bits_lost, long long long_window) {
+                                                                    int32_t *bits_lost, long long long_window,
+                                                                    uint32_t *cnt, uint32_t *resum) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const PointRec r = rec[q];
   if (r.flags & kPointTC) return;
-  if (r.flags || r.hi - r.lo + 1 <= long_window) sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
+  if (r.flags || r.hi - r.lo + 1 <= long_window)
+    sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, q, cnt, resum, out, nterms, bits_lost);
 }
 
 // Group g of a long window (ng groups): lane i sums its chunk, the 32 slots
 // are combined; lane 0 returns the group's value sv and carry gout.
 template <bool CC, bool CZ, bool ACC, bool F32>
-__device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, int ng, int g, int lane, xdd &sv_out,
-                                          xdd &gout_out) {
+__device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, int ng, int g, int lane, uint32_t *cnt,
+                                          xdd &sv_out, xdd &gout_out) {
   const long long L = r.hi - r.lo + 1;
   const long long C = (L + 32LL * ng - 1) / (32LL * ng);
   const long long clo = r.lo + (long long)g * 32 * C + lane * C;
@@ -734,7 +801,15 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
   }
   if (ACC) {
     xdd sv = xdd_zero();
-    if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
+    if (clo <= chi) {
+      if (sparse_window(P, clo, chi)) {
+        const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+        const xint X = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, clo, chi);
+        sv = xdd_from_xint(X);
+      } else {
+        sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
+      }
+    }
     if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
     for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
     sv_out = sv;
@@ -746,13 +821,16 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
   const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
   const xint zero = xint_norm(0, 0, 0, 0, 0);
   xint sv = zero, carry = zero;
-  if (clo <= chi) {
+  if (clo <= chi && sparse_window(P, clo, chi)) {
+    sv = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, clo, chi);
+  } else if (clo <= chi) {
     const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
     const xint u = recip_xint(mr, mi);
     long long base;
     bool ok;
-    const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base, ok);
+    const xint X = range_sum<CC, CZ, true>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base, ok);
     if (!ok) {  // not certified: the chunk's exact integer-pipe sum, in its own slot
+      atomicAdd(&cnt[kCntResumGroups], 1u);
       const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
       sv = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
     } else if (chi < r.kl) {
@@ -784,6 +862,70 @@ __device__ __forceinline__ void finalize_one(const DevPoly &P, const PointRec &r
   write_diag(P, r, o, nterms, bits_lost);
 }
 
+// The short windows whose FP64 sums failed their certificates (listed by
+// sum_point), summed again exactly on the integer pipe (the Horner of
+// FPE_ACCURATE).  A window of at most kResumThreadMax terms takes one thread;
+// a longer one SEG lanes (8 up to kResumSegMax terms, else a whole warp):
+// lane i sums the chunk [l + i C, l + (i + 1) C - 1], C = ceil(L / SEG),
+// multiplies it by z^(l + i C + v), and a butterfly over the window's lanes
+// adds them, so no lane's chain is long.
+constexpr long long kResumThreadMax = 48;
+constexpr long long kResumSegMax = 256;
+template <bool CC, bool CZ, int SEG>
+__device__ __forceinline__ void resum_window(const DevPoly &P, const PointRec &r, bool valid, int sl,
+                                             fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost) {
+  xdd sv = xdd_zero();
+  if (valid) {
+    const long long L = r.hi - r.lo + 1, C = (L + SEG - 1) / SEG;
+    const long long clo = r.lo + sl * C, chi = min(clo + C - 1, r.hi);
+    if (clo <= chi) sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
+    if (sv.rh != 0.0 || sv.ih != 0.0) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, clo + P.v));
+  }
+  for (int s = SEG / 2; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
+  if (valid && sl == 0) {
+    const fpe_xc64 o = xdd_out(sv);
+    out[r.orig] = o;
+    write_diag(P, r, o, nterms, bits_lost);
+  }
+}
+template <bool CC, bool CZ, bool BATCH>
+__global__ void __launch_bounds__(128) k_resum(DevPoly P0, const DevPoly *__restrict__ table,
+                                               const PointRec *__restrict__ rec, const uint32_t *cnt,
+                                               const uint32_t *__restrict__ list, fpe_xc64 *__restrict__ out,
+                                               int32_t *nterms, int32_t *bits_lost) {
+  const uint32_t m = *(volatile const uint32_t *)&cnt[kCntResum];
+  const int lane = threadIdx.x & 31;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  for (uint32_t i = tid; i < m; i += nthr) {  // the shortest, a thread each
+    const PointRec r = rec[list[i]];
+    if (r.hi - r.lo + 1 > kResumThreadMax) continue;
+    const DevPoly &P = BATCH ? table[r.pid] : P0;
+    const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
+    const fpe_xc64 o = xdd_out(xdd_mul(Y, xdd_pow_int(r.zr, r.zi, r.lo + P.v)));
+    out[r.orig] = o;
+    write_diag(P, r, o, nterms, bits_lost);
+  }
+  const uint32_t wid = tid >> 5, nw = nthr >> 5;
+  for (uint32_t b = wid * 4; b < m; b += nw * 4) {  // four windows of at most kResumSegMax terms per warp
+    const uint32_t i = b + (lane >> 3);
+    PointRec r{};
+    bool valid = i < m;
+    if (valid) {
+      r = rec[list[i]];
+      const long long L = r.hi - r.lo + 1;
+      valid = L > kResumThreadMax && L <= kResumSegMax;
+    }
+    const DevPoly &P = BATCH ? table[valid ? r.pid : 0] : P0;
+    resum_window<CC, CZ, 8>(P, r, valid, lane & 7, out, nterms, bits_lost);
+  }
+  for (uint32_t i = wid; i < m; i += nw) {  // the longer ones, a warp each
+    const PointRec r = rec[list[i]];
+    if (r.hi - r.lo + 1 <= kResumSegMax) continue;  // warp-uniform
+    const DevPoly &P = BATCH ? table[r.pid] : P0;
+    resum_window<CC, CZ, 32>(P, r, true, lane, out, nterms, bits_lost);
+  }
+}
+
 // Warp groups of the long windows, one evaluation of one polynomial:
 // persistent warps take group items from a counter and store each group's
 // value and carry; k_finalize_long combines them.
@@ -813,7 +955,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_groups(
     }
     const PointRec r = rec[long_list[i]];
     xdd sv, gout;
-    sum_group<CC, CZ, ACC, F32>(P, r, long_ngroups[i] & 0xffff, g, lane, sv, gout);
+    sum_group<CC, CZ, ACC, F32>(P, r, long_ngroups[i] & 0xffff, g, lane, cnt, sv, gout);
     if (lane == 0) {
       const int slot = group_slot(i, g, long_gbase[i], cap);
       gval[slot] = sv;
@@ -918,7 +1060,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
     const int32_t *__restrict__ long_list, int32_t *long_ngroups, const int32_t *__restrict__ long_gbase,
     const int32_t *__restrict__ extra_owner, const int32_t *__restrict__ extra_group, uint32_t *cnt, int cap,
     int extra_cap, xdd *gval, xdd *gcarry, fpe_xc64 *__restrict__ out, int32_t *nterms, int32_t *bits_lost,
-    long long long_window) {
+    long long long_window, uint32_t *resum) {
   const int lane = threadIdx.x & 31;
   const uint32_t nlong = *(volatile uint32_t *)&cnt[kCntLong];
   // every extra slot below min(reserved, extra_cap) is written by the scatter: an owner, or -1
@@ -935,7 +1077,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
       if (q < n) {
         const PointRec r = rec[q];
         if (r.flags || r.hi - r.lo + 1 <= long_window)
-          sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, out, nterms, bits_lost);
+          sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, (int)q, cnt, resum, out, nterms, bits_lost);
       }
       continue;
     }
@@ -952,7 +1094,7 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sums(
     const PointRec r = rec[long_list[i]];
     const DevPoly &P = BATCH ? table[r.pid] : P0;
     xdd sv, gout;
-    sum_group<CC, CZ, ACC, F32>(P, r, ng, g, lane, sv, gout);
+    sum_group<CC, CZ, ACC, F32>(P, r, ng, g, lane, cnt, sv, gout);
     if (ng == 1) {  // the whole window: finish it here
       if (lane == 0) finalize_one(P, r, sv, out, nterms, bits_lost);
     } else {
@@ -998,7 +1140,11 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
   {
     ProfScope ps("k_sum_short", st);
     k_sum_short<CC, CZ, ACC, F32, false><<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms,
-                                                                          bits_lost, P->tune.long_window);
+                                                                          bits_lost, P->tune.long_window, cnt, w.key);
+  }
+  if (!ACC && !F32) {
+    ProfScope ps("k_resum", st);
+    k_resum<CC, CZ, false><<<num_sms() * 6, 128, 0, st>>>(P->dev, nullptr, w.rec, cnt, w.key, out, nterms, bits_lost);
   }
   {
     ProfScope ps("k_sum_groups", st);
@@ -1189,7 +1335,10 @@ static void launch_batch_sums(fpe_batch_s *B, fpe_xc64 *out, int32_t *nterms, cu
   k_sums<CC, CZ, ACC, F32, true><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(
       DevPoly{}, B->d_table, (int)B->ntotal, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,
       w.extra_group, B->d_cnt, (int)w.cap, (int)w.extra_cap, (xdd *)w.group_val, (xdd *)w.group_carry, out, nterms,
-      nullptr, B->tune.long_window);
+      nullptr, B->tune.long_window, w.key);
+  if (!ACC && !F32)
+    k_resum<CC, CZ, true><<<num_sms() * 6, 128, 0, st>>>(DevPoly{}, B->d_table, w.rec, B->d_cnt, w.key, out, nterms,
+                                                         nullptr);
 }
 
 fpe_status launch_batch(fpe_batch_s *B, const double *z_re, const double *z_im, fpe_xc64 *out, int32_t *nterms,
@@ -1385,7 +1534,10 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
   do {                                                                                                         \
     k_sum_short<CCv, CZv, ACCv, F32v, false>                                                                   \
         <<<(ni + 127) / 128, 128, 0, st>>>(P->dev, nullptr, ni, w.rec, out, nterms, bits_lost,                 \
-                                           P->tune.long_window);                                               \
+                                           P->tune.long_window, w.bins + 2 * kNumBins, w.key);                 \
+    if (!ACCv && !F32v)                                                                                        \
+      k_resum<CCv, CZv, false><<<num_sms() * 6, 128, 0, st>>>(P->dev, nullptr, w.rec, w.bins + 2 * kNumBins,   \
+                                                              w.key, out, nterms, bits_lost);                  \
     k_sum_groups<CCv, CZv, ACCv, F32v><<<num_sms() * kSumBlocksPerSm, 128, 0, st>>>(                           \
         P->dev, w.rec, w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner, w.extra_group,                \
         w.bins + 2 * kNumBins, cap, xcap, (xdd *)w.group_val, (xdd *)w.group_carry);                          \

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,24 @@ constexpr int kLog2PieceLenF32 = 5;    // FP32 coefficients: keeps b_k and parti
 // a component with e < -kQBias (below 2^-459, negligible beside the other
 // component of a kept coefficient) or a zero is stored as 0.
 constexpr int kQBias = 512;
+
+// Scale of the FP32 rounding-error bookkeeping of the FP64 window sums:
+// magnitudes are kept as |x| 2^kMagOff (fpe_device.cuh, fpe_window.cuh).
+constexpr int kMagOff = 60;
+
+// A lower bound of |br + i bi| 2^kMagOff as a float: the FP64 modulus with a
+// margin above its rounding (two squares, a sum and a root err by under
+// 3 2^-53), rounded down to FP32; 0 below the FP32 range, the largest float
+// above it.  One per kept coefficient (DevPoly::bmag).
+inline float coef_mag_lo(double br, double bi) {
+  const double a = std::sqrt(br * br + bi * bi) * (1.0 - 0x1p-50);
+  const double x = std::ldexp(a, kMagOff);
+  if (!(x > 0.0)) return 0.0f;
+  if (x >= (double)std::numeric_limits<float>::max()) return std::numeric_limits<float>::max();
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, 0.0f);
+  return f;
+}
 
 // the packed word of x, or ~0 when x's exponent does not fit the field
 inline uint64_t qpack(double x) {
@@ -104,7 +123,9 @@ constexpr int kCntTcTiles = 12;    // tensor-core tiles
 constexpr int kCntTcSubtiles = 13; // tensor-core MMA sub-tiles
 constexpr int kCntTcPoints = 14;   // points summed on the tensor cores
 constexpr int kCntTcRejected = 15; // tensor-core points handed back to the FP64 kernels
-constexpr int kNumCounters = 16;
+constexpr int kCntResum = 16;      // short windows whose FP64 sum was not certified, listed for the exact re-sum
+constexpr int kCntResumGroups = 17; // lane chunks of long windows re-summed exactly in place
+constexpr int kNumCounters = 18;
 
 // Device view of a preconditioned polynomial, passed to kernels by value.
 struct DevPoly {
@@ -113,6 +134,7 @@ struct DevPoly {
   const double *b_full;        // every coefficient, same layout (Horner baselines)
   const float *bf;             // FPE_FP32: the FPE coefficients rounded to FP32 (same layout)
   const uint64_t *bq;          // the FPE coefficients packed by qpack (same layout; FP64 modes)
+  const float *bmag;           // FP64 modes: coef_mag_lo of each FPE coefficient, k = 0..D
   const int32_t *piece_k0;     // npieces + 1 entries, last = D + 1
   const int32_t *piece_beta;   // integer slope of rho on the piece
   const int32_t *piece_delta;  // exponent shift applied to h when entering piece j from j + 1
@@ -122,6 +144,7 @@ struct DevPoly {
   const double *hull_s;        // their scales
   const double *hull_sig;      // slopes of the n_hull - 1 segments
   const int32_t *gcount;       // gcount[k] = #{good j < k}, D + 2 entries
+  const int32_t *good_idx;     // the good (trimmed) indices in increasing order, gcount[D + 1] entries
   int64_t D;                   // trimmed degree d - v
   int64_t v;                   // valuation (first nonzero index)
   double T;                    // p + s(d) + 3

@@ -1115,3 +1115,25 @@ extern "C" fpe_status fpe_tensor_stats(fpe_poly_t P, int64_t *stats, int n, void
   stats[5] = c[kCntTcRejected];
   return FPE_OK;
 }
+
+extern "C" fpe_status fpe_cert_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream) {
+  using namespace fpe;
+  if (!P || !stats || n < 2) {
+    set_error("fpe_cert_stats: NULL handle or output, or n < 2");
+    return FPE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) stats[i] = 0;
+  if (!P->ws.bins || P->dev.fp32 || P->dev.accurate) return FPE_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != P->device) cudaSetDevice(P->device);
+  uint32_t c[kNumCounters];
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemcpyAsync(c, P->ws.bins + 2 * P->ws.nbins, sizeof c, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (prev >= 0 && prev != P->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "fpe_cert_stats");
+  stats[0] = c[kCntResum];
+  stats[1] = c[kCntResumGroups];
+  return FPE_OK;
+}

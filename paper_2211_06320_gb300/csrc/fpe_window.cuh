@@ -39,7 +39,9 @@ constexpr float kCertC = 7.6f;
 // by less than 2^-970 of |w|
 constexpr float kCertMinMult = 0x1p-100f;
 // largest |w| = |2^beta z| at which the bottom-up pass sums in blocks of four
-constexpr float kBlockMaxW = 1.5f;
+// (with random-phase terms the blocks' certificates fail for under 3% of
+// windows up to |w| = 2.25, for a quarter at 2.5)
+constexpr float kBlockMaxW = 2.3f;
 
 __host__ __device__ __forceinline__ bool cert_pass(const Cert &c) {
   return c.ok && add_up(c.E, c.M) <= mul_dn(c.S, kCertC);
@@ -51,16 +53,11 @@ __host__ __device__ __forceinline__ void cert_set(Cert &c, float E, float S, boo
   c.ok = ok;
 }
 
-// |b| lower bound of a coefficient, scaled
-template <bool CC>
-__host__ __device__ __forceinline__ float coef_mag(double br, double bi) {
-  return CC ? mag_lo2(br, bi) : mag_lo_hi(hi_abs(br));
-}
-
-// h <- h w + b (exact w) with its certificate terms; 4 FP64 FMA for complex z
+// h <- h w + b (exact w) with its certificate terms; 4 FP64 FMA for complex z.
+// bm: the coefficient's magnitude lower bound (DevPoly::bmag).
 template <bool CC, bool CZ>
 __host__ __device__ __forceinline__ void cstep_w(double &hr, double &hm, double wr, double wi, double br, double bi,
-                                                 float Wu, float Wd, float &E, float &S) {
+                                                 float bm, float Wu, float Wd, float &E, float &S) {
   float loc;
   if (CZ) {
     const double t1 = fma(-hm, wi, br), t2 = fma(hm, wr, bi);
@@ -77,14 +74,14 @@ __host__ __device__ __forceinline__ void cstep_w(double &hr, double &hm, double 
     }
   }
   E = fma_up(E, Wu, loc);
-  S = fma_dn(S, Wd, coef_mag<CC>(br, bi));
+  S = fma_dn(S, Wd, bm);
 }
 
 // bounds of |w| for w = wr + i wi (exact)
 template <bool CZ>
 __host__ __device__ __forceinline__ void mult_bounds(double wr, double wi, float &Wu, float &Wd) {
-  Wu = CZ ? cabs_up(wr, wi) : f_up(fabs(wr));
-  Wd = CZ ? cabs_dn(wr, wi) : f_dn(fabs(wr));
+  Wu = CZ ? cabs_up(wr, wi) : fabs_up<0>(wr);
+  Wd = CZ ? cabs_dn(wr, wi) : fabs_dn<0>(wr);
 }
 
 // scale a certificate by 2^d along with its value (|d| <= 120, else not covered)
@@ -93,63 +90,6 @@ __host__ __device__ __forceinline__ void cert_scale(float &E, float &S, bool &ok
   const float f = pow2f_bits(min(max(d, -120), 120));
   E = mul_up(E, f);
   S = mul_dn(S, f);
-}
-
-// Horner over trimmed indices [lo, hi] on the rescaled coefficients b:
-// returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-lo) = h * 2^rho(lo).
-// Piece j runs at w_j = 2^beta_j z; entering piece j from j+1 multiplies h by
-// 2^delta_j (both exact).  Every term of a window has |h| <= L 2^(T + 66),
-// so nothing overflows.
-template <bool CC, bool CZ>
-__host__ __device__ __forceinline__ void window_horner(const DevPoly &P, const double *__restrict__ b, double zr,
-                                                       double zi, long long lo, long long hi, double &hr,
-                                                       double &hm, long long &rho_lo, Cert &ct) {
-  int j = P.piece_first[hi >> P.log2_piece];
-  while (P.piece_k0[j + 1] <= hi) ++j;
-  if (CC) {
-    double2 c = reinterpret_cast<const double2 *>(b)[hi];
-    hr = c.x;
-    hm = c.y;
-  } else {
-    hr = b[hi];
-    hm = 0.0;
-  }
-  float E = 0.0f, S = coef_mag<CC>(hr, hm);
-  bool ok = true;
-  long long k = hi - 1;
-  long long k0 = max((long long)P.piece_k0[j], lo);
-  while (true) {
-    const int beta = P.piece_beta[j];
-    const double wr = scale2(zr, beta);
-    const double wi = CZ ? scale2(zi, beta) : 0.0;
-    float Wu, Wd;
-    mult_bounds<CZ>(wr, wi, Wu, Wd);
-    ok = ok && Wd >= kCertMinMult;
-    if (CC) {
-      const double2 *b2 = reinterpret_cast<const double2 *>(b);
-#pragma unroll 4
-      for (; k >= k0; --k) {
-        double2 c = FPE_LDG(&b2[k]);
-        cstep_w<CC, CZ>(hr, hm, wr, wi, c.x, c.y, Wu, Wd, E, S);
-      }
-    } else {
-#pragma unroll 4
-      for (; k >= k0; --k) {
-        double c = FPE_LDG(&b[k]);
-        cstep_w<CC, CZ>(hr, hm, wr, wi, c, 0.0, Wu, Wd, E, S);
-      }
-    }
-    if (k < lo) break;
-    --j;  // k == piece_k0[j + 1] - 1: enter piece j
-    const int dl = P.piece_delta[j];
-    const double s = pow2i(dl);
-    hr *= s;
-    hm *= s;
-    cert_scale(E, S, ok, dl);
-    k0 = max((long long)P.piece_k0[j], lo);
-  }
-  rho_lo = P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
-  cert_set(ct, E, S, ok, hr, hm);
 }
 
 // x <- x v + (br + i bi) with v = (vhr + vlr) + i (vhi + vli) in double-double
@@ -198,40 +138,231 @@ __host__ __device__ __forceinline__ void mult_bounds_dd(double hr, double lr, do
   if (CZ) {
     Vu = cabs_up_dd(hr, lr, hi, li);
     Vd = cabs_dn_dd(hr, lr, hi, li);
-    Vl = add_up(f_up(fabs(lr) * 0x1p53), f_up(fabs(li) * 0x1p53));
+    Vl = add_up(fabs_up<53>(lr), fabs_up<53>(li));
   } else {
-    Vu = add_up(f_up(fabs(hr)), f_up(fabs(lr)));
-    Vd = fmaxf(fma_dn(-1.0f, f_up(fabs(lr)), f_dn(fabs(hr))), 0.0f);
-    Vl = f_up(fabs(lr) * 0x1p53);
+    Vu = add_up(fabs_up<0>(hr), fabs_up<0>(lr));
+    Vd = fmaxf(fma_dn(-1.0f, fabs_up<0>(lr), fabs_dn<0>(hr)), 0.0f);
+    Vl = fabs_up<53>(lr);
   }
 }
 
+// smallest |w| = |2^beta z| at which the top-down pass sums in blocks of eight
+// (above it the terms decay slowly, long stretches of them are alike, and a
+// single Horner chain rounds its growing partial sum at every step)
+constexpr float kTopBlockMinW = 0.9f;
+
+// Horner over trimmed indices [lo, hi] on the rescaled coefficients b:
+// returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-lo) = h * 2^rho(lo).
+// Piece j runs at w_j = 2^beta_j z; entering piece j from j+1 multiplies h by
+// 2^delta_j (both exact).  Every term of a window has |h| <= L 2^(T + 66),
+// so nothing overflows.
+//
+// Blocks of eight (LONG: the lane chunks of long windows; with z8 = z^8 in
+// extended double-double, blocks8 set, and |w| >= kTopBlockMinW): eight steps
+// from k + 1 down to k - 7 are
+//   h_{k-7} = w^8 h_{k+1} + s,  s = b_{k-7} + w (b_{k-6} + ... + w b_k),
+// s by Horner with the exact w and the step by w^8 = 2^(8 beta) z8 in
+// double-double (36 FMA per eight terms instead of 32): the partial sum h
+// is rounded once per block, so over long windows of alike terms the
+// certificate grows with L / 8 such roundings instead of L.
+template <bool CC, bool CZ, bool LONG>
+__host__ __device__ __forceinline__ void window_horner(const DevPoly &P, const double *__restrict__ b, double zr,
+                                                       double zi, long long lo, long long hi, const xdd &z8,
+                                                       bool blocks8, double &hr, double &hm, long long &rho_lo,
+                                                       Cert &ct) {
+  int j = P.piece_first[hi >> P.log2_piece];
+  while (P.piece_k0[j + 1] <= hi) ++j;
+  if (CC) {
+    double2 c = reinterpret_cast<const double2 *>(b)[hi];
+    hr = c.x;
+    hm = c.y;
+  } else {
+    hr = b[hi];
+    hm = 0.0;
+  }
+  const float *__restrict__ bmag = P.bmag;
+  float E = 0.0f, S = FPE_LDG(&bmag[hi]);
+  bool ok = true;
+  long long k = hi - 1;
+  long long k0 = max((long long)P.piece_k0[j], lo);
+  while (true) {
+    const int beta = P.piece_beta[j];
+    const double wr = scale2(zr, beta);
+    const double wi = CZ ? scale2(zi, beta) : 0.0;
+    float Wu, Wd;
+    mult_bounds<CZ>(wr, wi, Wu, Wd);
+    ok = ok && Wd >= kCertMinMult;
+    const int s8 = (int)z8.e + 8 * beta;
+    if (LONG && blocks8 && k - 15 >= k0 && Wd >= kTopBlockMinW && s8 > -900 && s8 < 900) {
+      const double ahr = scale2(z8.rh, s8), alr = scale2(z8.rl, s8);
+      const double ahi = CZ ? scale2(z8.ih, s8) : 0.0, ali = CZ ? scale2(z8.il, s8) : 0.0;
+      float Au, Ad, Al;
+      mult_bounds_dd<CZ>(ahr, alr, ahi, ali, Au, Ad, Al);
+      ok = ok && Ad >= kCertMinMult;
+      for (; k - 7 >= k0; k -= 8) {
+        double sr, si;
+        float Es = 0.0f, Ss = FPE_LDG(&bmag[k]);
+        if (CC) {
+          const double2 c = FPE_LDG(reinterpret_cast<const double2 *>(b) + k);
+          sr = c.x;
+          si = c.y;
+        } else {
+          sr = FPE_LDG(b + k);
+          si = 0.0;
+        }
+#pragma unroll
+        for (int t = 1; t < 8; ++t) {
+          double cr, ci;
+          if (CC) {
+            const double2 c = FPE_LDG(reinterpret_cast<const double2 *>(b) + (k - t));
+            cr = c.x;
+            ci = c.y;
+          } else {
+            cr = FPE_LDG(b + (k - t));
+            ci = 0.0;
+          }
+          cstep_w<CC, CZ>(sr, si, wr, wi, cr, ci, FPE_LDG(&bmag[k - t]), Wu, Wd, Es, Ss);
+        }
+        cstep_v<CC, CZ>(hr, hm, ahr, alr, ahi, ali, sr, si, Au, Ad, Al, Es, Ss, E, S);  // h <- w^8 h + s
+      }
+    }
+    if (CC) {
+      const double2 *b2 = reinterpret_cast<const double2 *>(b);
+#pragma unroll 4
+      for (; k >= k0; --k) {
+        double2 c = FPE_LDG(&b2[k]);
+        cstep_w<CC, CZ>(hr, hm, wr, wi, c.x, c.y, FPE_LDG(&bmag[k]), Wu, Wd, E, S);
+      }
+    } else {
+#pragma unroll 4
+      for (; k >= k0; --k) {
+        double c = FPE_LDG(&b[k]);
+        cstep_w<CC, CZ>(hr, hm, wr, wi, c, 0.0, FPE_LDG(&bmag[k]), Wu, Wd, E, S);
+      }
+    }
+    if (k < lo) break;
+    --j;  // k == piece_k0[j + 1] - 1: enter piece j
+    const int dl = P.piece_delta[j];
+    const double s = pow2i(dl);
+    hr *= s;
+    hm *= s;
+    cert_scale(E, S, ok, dl);
+    k0 = max((long long)P.piece_k0[j], lo);
+  }
+  rho_lo = P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
+  cert_set(ct, E, S, ok, hr, hm);
+}
+
+// Blocks of B terms of the bottom-up pass, from k (the first index not yet
+// summed) while a whole block fits in [k, kend].  With w = 1/v = 2^beta_j z
+// (exact in FP64), B steps from K to K + B inside a piece are
+//   h_{K+B} = v^B h_K + v^(B-1) s_K,  s_K = b_{K+1} + w (b_{K+2} + ... + w b_{K+B}),
+// so G = w^(B-1) h obeys G_{K+B} = v^B G_K + s_K: the first block starts from
+// G = v h_K + s_K, and h = v^(B-1) G at the end.  s_K is a top-down FP64
+// Horner with the exact multiplier (B - 1 complex FMA steps, its rounding
+// relative to the block's own terms) and the block step multiplies by v^B in
+// double-double: 4 B + 4 FMA per B terms instead of 8 B.  uB = u^B and uB1 =
+// u^(B-1) carry their own exponents; sh scales u to v on the piece.  The
+// certificate follows the same recurrences: a block sum's bound is that of
+// its exact-multiplier steps; the block steps and the final v^(B-1) add
+// their own roundings.
+template <bool CC, bool CZ, int B>
+__host__ __device__ __forceinline__ void rev_blocks(const double *__restrict__ b, const float *__restrict__ bmag,
+                                                    long long &k, long long kend, double wr, double wi, float Wu,
+                                                    float Wd, double vhr, double vlr, double vhi, double vli,
+                                                    float Vu, float Vd, float Vl, const xdd &uB, const xdd &uB1,
+                                                    int sh, double &hr, double &hm, float &E, float &S, bool &ok) {
+  auto load = [&](long long q, double &br, double &bi) {
+    if (CC) {
+      const double2 c = FPE_LDG(reinterpret_cast<const double2 *>(b) + q);
+      br = c.x;
+      bi = c.y;
+    } else {
+      br = FPE_LDG(b + q);
+      bi = 0.0;
+    }
+  };
+  const int sB = (int)uB.e + B * sh;
+  const double ahr = scale2(uB.rh, sB), alr = scale2(uB.rl, sB);
+  const double ahi = CZ ? scale2(uB.ih, sB) : 0.0, ali = CZ ? scale2(uB.il, sB) : 0.0;
+  float Au, Ad, Al;
+  mult_bounds_dd<CZ>(ahr, alr, ahi, ali, Au, Ad, Al);
+  ok = ok && Wd >= kCertMinMult && Ad >= kCertMinMult;
+  // s over [k0, k0 + B - 1] by top-down Horner with w, and its certificate
+  auto block_sum = [&](long long k0, double &sr, double &si, float &Es, float &Ss) {
+    load(k0 + B - 1, sr, si);
+    Es = 0.0f;
+    Ss = FPE_LDG(&bmag[k0 + B - 1]);
+#pragma unroll
+    for (int t = B - 2; t >= 0; --t) {
+      double cr, ci;
+      load(k0 + t, cr, ci);
+      cstep_w<CC, CZ>(sr, si, wr, wi, cr, ci, FPE_LDG(&bmag[k0 + t]), Wu, Wd, Es, Ss);
+    }
+  };
+  double sr, si;
+  float Es, Ss;
+  block_sum(k, sr, si, Es, Ss);
+  cstep_v<CC, CZ>(hr, hm, vhr, vlr, vhi, vli, sr, si, Vu, Vd, Vl, Es, Ss, E, S);  // G = v h + s
+  k += B;
+  for (; k + B - 1 <= kend; k += B) {
+    block_sum(k, sr, si, Es, Ss);
+    cstep_v<CC, CZ>(hr, hm, ahr, alr, ahi, ali, sr, si, Au, Ad, Al, Es, Ss, E, S);  // G <- v^B G + s
+  }
+  // h = v^(B-1) G
+  const int sC = (int)uB1.e + (B - 1) * sh;
+  const double chr = scale2(uB1.rh, sC), clr = scale2(uB1.rl, sC);
+  const double chi = CZ ? scale2(uB1.ih, sC) : 0.0, cli = CZ ? scale2(uB1.il, sC) : 0.0;
+  float Cu, Cd, Cl;
+  mult_bounds_dd<CZ>(chr, clr, chi, cli, Cu, Cd, Cl);
+  (void)Cl;  // the low-part products below are rounded on their own, at their own tiny scale
+  ok = ok && Cd >= kCertMinMult;
+  float loc;
+  double nr, ni;
+  if (CZ) {
+    const double r1 = -hm * cli, q1 = hm * clr;
+    const double r2 = fma(hr, clr, r1), q2 = fma(hr, cli, q1);
+    const double r3 = fma(-hm, chi, r2), q3 = fma(hm, chr, q2);
+    nr = fma(hr, chr, r3);
+    ni = fma(hr, chi, q3);
+    loc = add_up(add_up(add_up(err_mag(r1), err_mag(r2)), add_up(err_mag(r3), err_mag(nr))),
+                 add_up(add_up(err_mag(q1), err_mag(q2)), add_up(err_mag(q3), err_mag(ni))));
+  } else {
+    const double r1 = hr * clr;
+    nr = fma(hr, chr, r1);
+    loc = add_up(err_mag(r1), err_mag(nr));
+    ni = 0.0;
+    if (CC) {
+      const double q1 = hm * clr;
+      ni = fma(hm, chr, q1);
+      loc = add_up(loc, add_up(err_mag(q1), err_mag(ni)));
+    }
+  }
+  hr = nr;
+  hm = ni;
+  E = fma_up(E, Cu, loc);
+  S = mul_dn(S, Cd);
+}
+
+// largest |w| at which the bottom-up pass sums in blocks of eight rather than four
+constexpr float kBlock8MaxW = 1.1f;
+
 // Bottom-up Horner over trimmed indices [lo, hi] with multiplier 1/z:
 // returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-hi) = h * 2^rho(hi).
-// 1/z = u 2^ue with u in extended double-double (u^3, u^4 likewise, each
-// with its own exponent).  Within piece j the step from k-1 to
-// k multiplies by v_j = 2^-beta_j / z; crossing from piece j to j+1 first
-// scales h by 2^-delta_j.  A single step is 8 FMA for complex z and
-// coefficients (v in double-double).
-//
-// Blocks of four.  With w = 1/v = 2^beta_j z (exact in FP64), four steps
-// from K to K+4 inside a piece are
-//   h_{K+4} = v^4 h_K + v^3 s_K,  s_K = b_{K+1} + w (b_{K+2} + w (b_{K+3} + w b_{K+4})),
-// so G = w^3 h obeys G_{K+4} = v^4 G_K + s_K (the first block of a run
-// starts from G = v h_K + s_K, and h = v^3 G at its end).  s_K is a top-down
-// FP64 Horner with the exact multiplier (3 complex FMA, rounding within
-// 3u of the block's term magnitudes) and the block step multiplies by v^4 in
-// double-double: 20 FMA per four terms instead of 32.  u3 = u^3, u4 = u^4.
-//
-// The certificate follows the same recurrences: a block sum's bound is that
-// of its three exact-multiplier steps; the block step, the single steps and
-// the final v^3 add their own roundings.  v, v^3, v^4 are within 2^-96 of
-// the exact powers (a reciprocal good to 2^-100, then a few 128-bit
-// products), which the threshold kCertC allows for.
-template <bool CC, bool CZ>
+// 1/z = u 2^ue with u in extended double-double (its powers up[0..3] = u^3,
+// u^4, u^7, u^8 likewise, each with its own exponent).  Within piece j the
+// step from k-1 to k multiplies by v_j = 2^-beta_j / z; crossing from piece
+// j to j+1 first scales h by 2^-delta_j.  A single step is 8 FMA for complex
+// z and coefficients (v in double-double).  With blocks set, runs of a piece
+// go in blocks (rev_blocks): of eight terms (LONG) while |w| <= kBlock8MaxW, where
+// the terms are alike over long stretches and the block steps are what the
+// certificate sees, of four while |w| <= kBlockMaxW.  v and its powers are
+// within 2^-96 of the exact ones (a reciprocal good to 2^-100, then a few
+// 128-bit products), which the threshold kCertC allows for.
+template <bool CC, bool CZ, bool LONG>
 __host__ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b,
-                                                           const xdd &u, const xdd &u3, const xdd &u4, bool blocks,
-                                                           int ue, double zr, double zi, long long lo, long long hi,
+                                                           const xdd &u, const xdd *up, bool blocks, int ue,
+                                                           double zr, double zi, long long lo, long long hi,
                                                            double &hr, double &hm, long long &rho_hi, Cert &ct) {
   int j = P.piece_first[lo >> P.log2_piece];
   while (P.piece_k0[j + 1] <= lo) ++j;
@@ -245,8 +376,9 @@ __host__ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, con
       bi = 0.0;
     }
   };
+  const float *__restrict__ bmag = P.bmag;
   load(lo, hr, hm);
-  float E = 0.0f, S = coef_mag<CC>(hr, hm);
+  float E = 0.0f, S = FPE_LDG(&bmag[lo]);
   bool ok = true;
   long long k = lo + 1;
   while (k <= hi) {
@@ -259,78 +391,25 @@ __host__ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, con
     mult_bounds_dd<CZ>(vhr, vlr, vhi, vli, Vu, Vd, Vl);
     ok = ok && Vd >= kCertMinMult;
     const long long kend = min((long long)P.piece_k0[j + 1] - 1, hi);
-    const double wr = scale2(zr, beta), wi = CZ ? scale2(zi, beta) : 0.0;
-    float Wu, Wd;
-    mult_bounds<CZ>(wr, wi, Wu, Wd);
-    // blocks while |w| <= kBlockMaxW: beyond it the top term of a block, rounded at
-    // each of the block sum's three steps, costs more in the certificate than
-    // the single steps' double-double roundings
-    if (blocks && kend - k + 1 >= 8 && sh > -200 && sh < 200 && Wu <= kBlockMaxW) {  // v^4 and its low part stay normal
-      const int s4 = (int)u4.e + 4 * sh;
-      const double ahr = scale2(u4.rh, s4), alr = scale2(u4.rl, s4);
-      const double ahi = CZ ? scale2(u4.ih, s4) : 0.0, ali = CZ ? scale2(u4.il, s4) : 0.0;
-      float Au, Ad, Al;
-      mult_bounds_dd<CZ>(ahr, alr, ahi, ali, Au, Ad, Al);
-      ok = ok && Wd >= kCertMinMult && Ad >= kCertMinMult;
-      // s over [k, k + 3] by top-down Horner with w, and its certificate
-      auto block_sum = [&](long long k0, double &sr, double &si, float &Es, float &Ss) {
-        load(k0 + 3, sr, si);
-        Es = 0.0f;
-        Ss = coef_mag<CC>(sr, si);
-#pragma unroll
-        for (int t = 2; t >= 0; --t) {
-          double cr, ci;
-          load(k0 + t, cr, ci);
-          cstep_w<CC, CZ>(sr, si, wr, wi, cr, ci, Wu, Wd, Es, Ss);
-        }
-      };
-      double sr, si;
-      float Es, Ss;
-      block_sum(k, sr, si, Es, Ss);
-      cstep_v<CC, CZ>(hr, hm, vhr, vlr, vhi, vli, sr, si, Vu, Vd, Vl, Es, Ss, E, S);  // G = v h + s
-      k += 4;
-      for (; k + 3 <= kend; k += 4) {
-        block_sum(k, sr, si, Es, Ss);
-        cstep_v<CC, CZ>(hr, hm, ahr, alr, ahi, ali, sr, si, Au, Ad, Al, Es, Ss, E, S);  // G <- v^4 G + s
-      }
-      // h = v^3 G
-      const int s3 = (int)u3.e + 3 * sh;
-      const double chr = scale2(u3.rh, s3), clr = scale2(u3.rl, s3);
-      const double chi = CZ ? scale2(u3.ih, s3) : 0.0, cli = CZ ? scale2(u3.il, s3) : 0.0;
-      float Cu, Cd, Cl;
-      mult_bounds_dd<CZ>(chr, clr, chi, cli, Cu, Cd, Cl);
-      (void)Cl;  // the low-part products below are rounded on their own, at their own tiny scale
-      ok = ok && Cd >= kCertMinMult;
-      float loc;
-      double nr, ni;
-      if (CZ) {
-        const double r1 = -hm * cli, q1 = hm * clr;
-        const double r2 = fma(hr, clr, r1), q2 = fma(hr, cli, q1);
-        const double r3 = fma(-hm, chi, r2), q3 = fma(hm, chr, q2);
-        nr = fma(hr, chr, r3);
-        ni = fma(hr, chi, q3);
-        loc = add_up(add_up(add_up(err_mag(r1), err_mag(r2)), add_up(err_mag(r3), err_mag(nr))),
-                     add_up(add_up(err_mag(q1), err_mag(q2)), add_up(err_mag(q3), err_mag(ni))));
-      } else {
-        const double r1 = hr * clr;
-        nr = fma(hr, chr, r1);
-        loc = add_up(err_mag(r1), err_mag(nr));
-        ni = 0.0;
-        if (CC) {
-          const double q1 = hm * clr;
-          ni = fma(hm, chr, q1);
-          loc = add_up(loc, add_up(err_mag(q1), err_mag(ni)));
-        }
-      }
-      hr = nr;
-      hm = ni;
-      E = fma_up(E, Cu, loc);
-      S = mul_dn(S, Cd);
+    if (blocks) {
+      const double wr = scale2(zr, beta), wi = CZ ? scale2(zi, beta) : 0.0;
+      float Wu, Wd;
+      mult_bounds<CZ>(wr, wi, Wu, Wd);
+      // blocks of four while |w| <= kBlockMaxW: beyond it the top term of a block,
+      // rounded at each of the block sum's steps, costs more in the certificate
+      // than the single steps' double-double roundings (8 FMA a term, not 5);
+      // v^B and its low part stay normal for the shifts allowed
+      if (LONG && kend - k + 1 >= 16 && sh > -100 && sh < 100 && Wu <= kBlock8MaxW)
+        rev_blocks<CC, CZ, 8>(b, bmag, k, kend, wr, wi, Wu, Wd, vhr, vlr, vhi, vli, Vu, Vd, Vl, up[3], up[2], sh,
+                              hr, hm, E, S, ok);
+      else if (kend - k + 1 >= 8 && sh > -200 && sh < 200 && Wu <= kBlockMaxW)
+        rev_blocks<CC, CZ, 4>(b, bmag, k, kend, wr, wi, Wu, Wd, vhr, vlr, vhi, vli, Vu, Vd, Vl, up[1], up[0], sh,
+                              hr, hm, E, S, ok);
     }
     for (; k <= kend; ++k) {
       double br, bi;
       load(k, br, bi);
-      cstep_v<CC, CZ>(hr, hm, vhr, vlr, vhi, vli, br, bi, Vu, Vd, Vl, 0.0f, coef_mag<CC>(br, bi), E, S);
+      cstep_v<CC, CZ>(hr, hm, vhr, vlr, vhi, vli, br, bi, Vu, Vd, Vl, 0.0f, FPE_LDG(&bmag[k]), E, S);
     }
     if (k > hi) break;
     // k is the first index of piece j + 1: rescale, one step with v_j, move on
@@ -341,7 +420,7 @@ __host__ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, con
     cert_scale(E, S, ok, dl);
     double br, bi;
     load(k, br, bi);
-    cstep_v<CC, CZ>(hr, hm, vhr, vlr, vhi, vli, br, bi, Vu, Vd, Vl, 0.0f, coef_mag<CC>(br, bi), E, S);
+    cstep_v<CC, CZ>(hr, hm, vhr, vlr, vhi, vli, br, bi, Vu, Vd, Vl, 0.0f, FPE_LDG(&bmag[k]), E, S);
     ++k;
     ++j;
   }

@@ -318,6 +318,10 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
     }
     P->n_good = gcount[D + 1];
   }
+  std::vector<int32_t> good_idx;  // for the sparse window sums
+  good_idx.reserve(P->n_good);
+  for (int64_t k = 0; k <= D; ++k)
+    if (P->good[v + k]) good_idx.push_back((int32_t)k);
 
   // pieces: cut [0, D] at multiples of the piece length and at every vertex
   const int log2_piece = fp32 ? kLog2PieceLenF32 : kLog2PieceLen;
@@ -435,10 +439,13 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   }
 
   std::vector<uint64_t> bq;
+  std::vector<float> bm;  // FP64 modes: magnitude lower bounds for the rounding-error certificates
   if (fp32) {  // the p-bit representation of the kept coefficients (Thm. equivAlgo's tilde a_k)
     bf.resize(b.size());
     for (size_t i = 0; i < b.size(); ++i) bf[i] = (float)b[i];
   } else {  // integer-pipe copy for the window sums
+    bm.resize(D + 1);
+    for (int64_t k = 0; k <= D; ++k) bm[k] = coef_mag_lo(b[k * stride], cplx ? b[k * stride + 1] : 0.0);
     bq.resize(b.size());
     for (size_t i = 0; i < b.size(); ++i) {
       bq[i] = qpack(b[i]);
@@ -471,7 +478,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   DevPoly &dp = P->dev;
   if (!host_only) {
     if ((st = upload(P, b, &dp.b)) != FPE_OK || (st = upload(P, bf, &dp.bf)) != FPE_OK ||
-        (st = upload(P, bq, &dp.bq)) != FPE_OK ||
+        (st = upload(P, bq, &dp.bq)) != FPE_OK || (st = upload(P, bm, &dp.bmag)) != FPE_OK ||
         (st = upload(P, bfull, &dp.b_full)) != FPE_OK ||
         (st = upload(P, pk0, &dp.piece_k0)) != FPE_OK ||
         (st = upload(P, pbeta, &dp.piece_beta)) != FPE_OK ||
@@ -481,7 +488,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
         (st = upload(P, dhk, &dp.hull_k)) != FPE_OK ||
         (st = upload(P, dhs, &dp.hull_s)) != FPE_OK ||
         (st = upload(P, dsig, &dp.hull_sig)) != FPE_OK ||
-        (st = upload(P, gcount, &dp.gcount)) != FPE_OK) {
+        (st = upload(P, gcount, &dp.gcount)) != FPE_OK || (st = upload(P, good_idx, &dp.good_idx)) != FPE_OK) {
       free_handle(P);
       return st;
     }

@@ -1,12 +1,21 @@
 // Host build of the certified FP64 window sums (fpe_window.cuh) for a CPU
 // test against exact rational sums.  Compiled by tests/test_window_cert_host.py.
+#include <vector>
+
 #include "fpe_window.cuh"
 using namespace fpe;
 
+static std::vector<float> g_bmag;
+
+// the handle's view of the coefficients b (n of them); bmag as preconditioning makes it
 static DevPoly make_poly(const double *b, int cc, const int32_t *k0, const int32_t *beta, const int32_t *delta,
                          const int64_t *rho0, const int32_t *first, int npieces, int log2_piece) {
   DevPoly P;
   memset(&P, 0, sizeof P);
+  const int n = k0[npieces];
+  g_bmag.resize(n);
+  for (int k = 0; k < n; ++k) g_bmag[k] = coef_mag_lo(cc ? b[2 * k] : b[k], cc ? b[2 * k + 1] : 0.0);
+  P.bmag = g_bmag.data();
   P.b = b;
   P.piece_k0 = k0;
   P.piece_beta = beta;
@@ -20,21 +29,27 @@ static DevPoly make_poly(const double *b, int cc, const int32_t *k0, const int32
 }
 
 template <bool CC, bool CZ>
-static void top(const DevPoly &P, double zr, double zi, long long lo, long long hi, double *out, long long *rho,
-                Cert &ct) {
-  window_horner<CC, CZ>(P, P.b, zr, zi, lo, hi, out[0], out[1], *rho, ct);
+static void top(const DevPoly &P, double zr, double zi, long long lo, long long hi, int blocks, double *out,
+                long long *rho, Cert &ct) {
+  // z^8 as the evaluation kernels form it
+  int f;
+  frexp(fmax(fabs(zr), fabs(zi)), &f);
+  const xdd z8 = xdd_from_xint(xint_pow_z(zr, zi, 8, f));
+  window_horner<CC, CZ, true>(P, P.b, zr, zi, lo, hi, z8, blocks != 0, out[0], out[1], *rho, ct);
 }
 
-// top-down pass over [lo, hi]: out = (hr, hm), *rho = rho(lo), es = (E, S); returns ok
+// top-down pass over [lo, hi] (blocks of eight allowed when blocks is set):
+// out = (hr, hm), *rho = rho(lo), es = (E, S); returns ok
 extern "C" int wc_top(const double *b, int cc, int cz, const int32_t *k0, const int32_t *beta, const int32_t *delta,
                       const int64_t *rho0, const int32_t *first, int npieces, int log2_piece, double zr, double zi,
-                      long long lo, long long hi, double *out, long long *rho, float *es) {
+                      long long lo, long long hi, int blocks, double *out, long long *rho, float *es) {
   const DevPoly P = make_poly(b, cc, k0, beta, delta, rho0, first, npieces, log2_piece);
   Cert ct;
-  if (cc && cz) top<true, true>(P, zr, zi, lo, hi, out, rho, ct);
-  else if (cc) top<true, false>(P, zr, zi, lo, hi, out, rho, ct);
-  else if (cz) top<false, true>(P, zr, zi, lo, hi, out, rho, ct);
-  else top<false, false>(P, zr, zi, lo, hi, out, rho, ct);
+  if (!cz) zi = 0.0;
+  if (cc && cz) top<true, true>(P, zr, zi, lo, hi, blocks, out, rho, ct);
+  else if (cc) top<true, false>(P, zr, zi, lo, hi, blocks, out, rho, ct);
+  else if (cz) top<false, true>(P, zr, zi, lo, hi, blocks, out, rho, ct);
+  else top<false, false>(P, zr, zi, lo, hi, blocks, out, rho, ct);
   es[0] = ct.E;
   es[1] = ct.S;
   return ct.ok;
@@ -49,9 +64,10 @@ static void rev(const DevPoly &P, double zr, double zi, long long lo, long long 
   const double mr = ldexp(zr, -f), mi = ldexp(zi, -f);
   const xint u = recip_xint(mr, mi);
   const xdd u1 = xdd_from_xint(u);
-  const xint u2 = xint_sqr(u);
-  const xdd u3 = xdd_from_xint(xint_mul(u2, u)), u4 = xdd_from_xint(xint_sqr(u2));
-  window_horner_rev<CC, CZ>(P, P.b, u1, u3, u4, blocks != 0, -f, zr, zi, lo, hi, out[0], out[1], *rho, ct);
+  const xint u2 = xint_sqr(u), u3 = xint_mul(u2, u), u4 = xint_sqr(u2);
+  const xdd up[4] = {xdd_from_xint(u3), xdd_from_xint(u4), xdd_from_xint(xint_mul(u4, u3)),
+                     xdd_from_xint(xint_sqr(u4))};
+  window_horner_rev<CC, CZ, true>(P, P.b, u1, up, blocks != 0, -f, zr, zi, lo, hi, out[0], out[1], *rho, ct);
 }
 
 // bottom-up pass over [lo, hi]: out = (hr, hm), *rho = rho(hi), es = (E, S); returns ok
@@ -69,20 +85,21 @@ extern "C" int wc_rev(const double *b, int cc, int cz, const int32_t *k0, const 
   return ct.ok;
 }
 
-// the magnitude helpers: err_mag(x), mag_lo of (x, y)
+// the magnitude helpers: err_mag(x), mag_up(x), coef_mag_lo(x, y)
 extern "C" void wc_mags(double x, double y, float *o) {
   o[0] = err_mag(x);
-  o[1] = mag_lo2(x, y);
+  o[1] = mag_up(x);
+  o[2] = coef_mag_lo(x, y);
 }
 
 // one exact-multiplier step h w + b: out = (new hr, new hm), returns the step's error bound
 extern "C" float wc_step_w(int cc, int cz, double hr, double hm, double wr, double wi, double br, double bi,
                            double *out) {
   float E = 0.0f, S = 0.0f;
-  if (cc && cz) cstep_w<true, true>(hr, hm, wr, wi, br, bi, 1.0f, 1.0f, E, S);
-  else if (cc) cstep_w<true, false>(hr, hm, wr, 0.0, br, bi, 1.0f, 1.0f, E, S);
-  else if (cz) cstep_w<false, true>(hr, hm, wr, wi, br, 0.0, 1.0f, 1.0f, E, S);
-  else cstep_w<false, false>(hr, hm, wr, 0.0, br, 0.0, 1.0f, 1.0f, E, S);
+  if (cc && cz) cstep_w<true, true>(hr, hm, wr, wi, br, bi, 0.0f, 1.0f, 1.0f, E, S);
+  else if (cc) cstep_w<true, false>(hr, hm, wr, 0.0, br, bi, 0.0f, 1.0f, 1.0f, E, S);
+  else if (cz) cstep_w<false, true>(hr, hm, wr, wi, br, 0.0, 0.0f, 1.0f, 1.0f, E, S);
+  else cstep_w<false, false>(hr, hm, wr, 0.0, br, 0.0, 0.0f, 1.0f, 1.0f, E, S);
   out[0] = hr;
   out[1] = hm;
   return E;

@@ -12,7 +12,7 @@ from _parity import TOL_FP64, error_ratio
 pytestmark = pytest.mark.gpu
 
 GRID_LW = {1024, 2048, 4096, 8192}
-GRID_LC = {256, 512, 1024, 2048}
+GRID_LC = {128, 256, 512, 1024, 2048}
 
 
 @pytest.fixture(scope="module")

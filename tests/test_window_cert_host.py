@@ -42,7 +42,7 @@ def lib(tmp_path_factory):
            os.path.join(ROOT, "tests", "native", "window_cert_host.cu"), "-o", out]
     subprocess.run(cmd, check=True, capture_output=True)
     L = ctypes.CDLL(out)
-    L.wc_top.argtypes = [P, I, I, P, P, P, P, P, I, I, D, D, LL, LL, P, P, P]
+    L.wc_top.argtypes = [P, I, I, P, P, P, P, P, I, I, D, D, LL, LL, I, P, P, P]
     L.wc_rev.argtypes = [P, I, I, P, P, P, P, P, I, I, D, D, LL, LL, I, P, P, P]
     L.wc_top.restype = I
     L.wc_rev.restype = I
@@ -146,10 +146,8 @@ def run(lib, kind, b, cc, cz, pieces, zr, zi, lo, hi, blocks=1):
     es = np.zeros(2, np.float32)
     args = [b.ctypes.data, cc, cz, k0.ctypes.data, beta.ctypes.data, delta.ctypes.data, rho0.ctypes.data,
             first.ctypes.data, len(beta), LOG2_PIECE, zr, zi, lo, hi]
-    if kind == "top":
-        ok = lib.wc_top(*args, out.ctypes.data, rho.ctypes.data, es.ctypes.data)
-    else:
-        ok = lib.wc_rev(*args, blocks, out.ctypes.data, rho.ctypes.data, es.ctypes.data)
+    fn = lib.wc_top if kind == "top" else lib.wc_rev
+    ok = fn(*args, blocks, out.ctypes.data, rho.ctypes.data, es.ctypes.data)
     return bool(ok), out, int(rho[0]), float(es[0]), float(es[1])
 
 
@@ -157,9 +155,9 @@ def coef(b, cc, k):
     return (dy(b[2 * k]), dy(b[2 * k + 1])) if cc else (dy(b[k]), (0, 0))
 
 
-def check_top(lib, b, cc, cz, pieces, zr, zi, lo, hi):
+def check_top(lib, b, cc, cz, pieces, zr, zi, lo, hi, blocks=1):
     k0, beta, delta, rho0, _ = pieces
-    ok, out, rho, E, S = run(lib, "top", b, cc, cz, pieces, zr, zi, lo, hi)
+    ok, out, rho, E, S = run(lib, "top", b, cc, cz, pieces, zr, zi, lo, hi, blocks)
     assert rho == rho_of(lo, k0, beta, rho0)
     z = (dy(zr), dy(zi if cz else 0.0))
     acc, pw, absum = ((0, 0), (0, 0)), ((1, 0), (0, 0)), 0.0
@@ -233,22 +231,22 @@ def unit_disk(n, rng, cc):
 # ------------------------------------------------------------ tests
 
 def test_magnitude_helpers(lib):
-    o = np.zeros(2, np.float32)
+    o = np.zeros(3, np.float32)
     rng = np.random.default_rng(3)
     for x in np.concatenate([2.0 ** rng.uniform(-180, 60, 400) * rng.choice([-1, 1], 400), [1.0, -0.75, 2.0 ** -186]]):
-        lib.wc_mags(float(x), 0.0, o.ctypes.data)
+        y = float(x) * rng.uniform(-2, 2)
+        lib.wc_mags(float(x), y, o.ctypes.data)
         e = math.floor(math.log2(abs(x)))
-        want = 2.0 ** (e + 60)
-        assert o[0] == np.float32(max(want, 2.0 ** -126)), x  # err_mag: 2^(e(x) + 60), floor 2^-126
-        ref = abs(x) * 2.0 ** 60
-        assert o[1] <= ref and (ref < 2.0 ** -149 or o[1] >= ref * (1 - 2.0 ** -19) - 2.0 ** -149), x
+        assert o[0] == np.float32(max(2.0 ** (e + 60), 2.0 ** -126)), x  # err_mag: 2^(e(x) + 60), floor 2^-126
+        ref = abs(x) * 2.0 ** 60  # mag_up: above, within 2^-19 (floor 2^-126)
+        assert o[1] >= ref and o[1] <= max(ref * (1 + 2.0 ** -19), 2.0 ** -126), x
+        ref = math.hypot(x, y) * 2.0 ** 60  # coef_mag_lo: below, within 2^-23 while a normal float
+        assert o[2] <= ref and (ref < 2.0 ** -126 or o[2] >= ref * (1 - 2.0 ** -23)), x
     for x in (0.0, 2.0 ** -300):
         lib.wc_mags(x, 0.0, o.ctypes.data)
-        assert o[0] == np.float32(2.0 ** -126) and o[1] == 0.0
-    lib.wc_mags(2.0 ** 70, 0.0, o.ctypes.data)
-    assert np.isinf(o[0]) and 3.4e38 < o[1] <= np.finfo(np.float32).max  # saturated lower bound
-    lib.wc_mags(0.25, -3.0, o.ctypes.data)  # mag_lo of a pair: max of the two
-    assert o[1] == np.float32(3.0 * 2.0 ** 60)
+        assert o[0] == np.float32(2.0 ** -126) and o[1] == np.float32(2.0 ** -126) and o[2] == 0.0
+    lib.wc_mags(2.0 ** 70, 0.0, o.ctypes.data)  # beyond the FP32 range: inf above, the largest float below
+    assert np.isinf(o[0]) and np.isinf(o[1]) and o[2] == np.finfo(np.float32).max
 
 
 @pytest.mark.parametrize("cc,cz", [(1, 1), (0, 1), (1, 0), (0, 0)])
@@ -369,25 +367,48 @@ def _single_piece(n):
 
 
 def test_blocked_pass_counts_block_sum_roundings(lib):
-    """z = 1 (every multiplier exact), blocks of four whose sums round the same
-    way: (1, t, t, t) rounds to 1 and (-1, t', t', t') to -1, t = 0.499 2^-52
-    and t' = 0.499 2^-53, so each block sum errs by about 3 t or 3 t' with
-    one sign while the partial sum G returns to 0 after every second block
-    (its own roundings vanish).  The error, about 4.5 2^-53 per pair of
-    blocks, is then most of the bound (7 units per pair): a bound without the
-    block sums' roundings would fall below it."""
+    """z = 1 (every multiplier exact; |w| = 1 takes blocks of eight), blocks
+    whose sums round the same way: (1, t, ..., t) rounds to 1 and (-1, t',
+    ..., t') to -1, t = 0.499 2^-52 and t' = 0.499 2^-53, so each block sum
+    errs by about 7 t or 7 t' with one sign while the partial sum G returns
+    to 0 after every second block (its own roundings vanish).  The error,
+    about 10.5 2^-53 per pair of blocks, is then most of the bound (15 units
+    per pair): a bound without the block sums' roundings would fall below it."""
+    B = 8
     nb = 40
-    n = 1 + 4 * nb
+    n = 1 + B * nb
     b = np.zeros(n)
     t, t2 = 0.499 * 2.0 ** -52, 0.499 * 2.0 ** -53
     for m in range(nb):
-        k0 = 1 + 4 * m  # block sum over b[k0 .. k0 + 3], the top index first
+        k0 = 1 + B * m  # block sum over b[k0 .. k0 + B - 1], the top index first
         if m % 2 == 0:
-            b[k0 + 3], b[k0:k0 + 3] = 1.0, t
+            b[k0 + B - 1], b[k0:k0 + B - 1] = 1.0, t
         else:
-            b[k0 + 3], b[k0:k0 + 3] = -1.0, t2
+            b[k0 + B - 1], b[k0:k0 + B - 1] = -1.0, t2
     ok, E, S, absum = check_rev(lib, b, 0, 0, _single_piece(n), 1.0, 0.0, 0, n - 1, 1)
     _, out, _, E2, _ = run(lib, "rev", b, 0, 0, _single_piece(n), 1.0, 0.0, 0, n - 1, 1)
     err = abs(math.fsum([*b]) - out[0])  # z = 1: the window sum is the plain sum (fsum: exact here)
     assert err > 0.5 * E2 * 2.0 ** -113, (err, E2)
 
+
+
+def test_top_down_blocks_of_eight(lib):
+    """One piece of 300 terms at |z| = 0.97 and |z| = 1 (blocks of eight with
+    w^8 in double-double throughout), complex and real points: the bound
+    holds, and at |z| = 1 (terms of random phase and equal size) it stays
+    inside the certificate where single steps do not."""
+    rng = np.random.default_rng(17)
+    n = 300
+    b = unit_disk(n, rng, 1)
+    for mod in (0.97, 1.0):
+        ph = rng.uniform(0, 2 * math.pi)
+        check_top(lib, b, 1, 1, _single_piece(n), mod * math.cos(ph), mod * math.sin(ph), 0, n - 1, 1)
+        check_top(lib, b, 1, 0, _single_piece(n), -mod, 0.0, 0, n - 1, 1)
+    qs = {0: [], 1: []}
+    for t in range(20):
+        b = unit_disk(n, rng, 1)
+        ph = rng.uniform(0, 2 * math.pi)
+        for blocks in (0, 1):
+            ok, E, S, _ = check_top(lib, b, 1, 1, _single_piece(n), math.cos(ph), math.sin(ph), 0, n - 1, blocks)
+            qs[blocks].append(E / S)
+    assert np.median(qs[1]) < 0.6 * np.median(qs[0]), (np.median(qs[0]), np.median(qs[1]))
