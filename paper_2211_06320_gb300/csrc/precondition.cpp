@@ -365,22 +365,25 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
       int64_t len = pk0[j + 1] - pk0[j];
       pdelta[j] = (j + 1 < np) ? (int32_t)(prho0[j + 1] - prho0[j] - (int64_t)pbeta[j] * len) : 0;
     }
-    // Merge a piece into its predecessor when the cut changes nothing: same
-    // slope and no exponent jump, so rho continues as the same integer line
-    // (an integer cover slope, e.g. a flat cover, never drifts from it).
-    // The stored b_k are unchanged; the summation loops see fewer crossings.
+    // Merge a piece into its predecessor when the predecessor's rho line,
+    // continued, stays close to the piece's own: same slope, and (FP32 mode)
+    // no exponent jump, or (FP64 modes) a line offset of at most
+    // kMergeDrift bits.  A nearly flat cover then becomes one piece (the
+    // rounding of rho0 to integers no longer cuts it every few hundred
+    // terms), so its windows stay inside one piece for the tensor-core sums
+    // and the FP64 loops see fewer crossings; b_k stays within kMergeDrift
+    // bits of where the unmerged pieces put it.
     {
+      constexpr int64_t kMergeDrift = 8;
+      const int64_t max_off = fp32 ? 0 : kMergeDrift;
       int m = 0;
       for (int j = 1; j < np; ++j) {
-        if (pbeta[j] == pbeta[m] && pdelta[m] == 0) {
-          pdelta[m] = pdelta[j];  // the merged piece ends where piece j ended
-        } else {
-          ++m;
-          pk0[m] = pk0[j];
-          pbeta[m] = pbeta[j];
-          prho0[m] = prho0[j];
-          pdelta[m] = pdelta[j];
-        }
+        const int64_t off = prho0[m] + (int64_t)pbeta[m] * (pk0[j] - pk0[m]) - prho0[j];
+        if (pbeta[j] == pbeta[m] && off >= -max_off && off <= max_off) continue;  // piece j joins piece m
+        ++m;
+        pk0[m] = pk0[j];
+        pbeta[m] = pbeta[j];
+        prho0[m] = prho0[j];
       }
       const int nm = np > 0 ? m + 1 : 0;
       pk0[nm] = (int32_t)(D + 1);
@@ -388,6 +391,8 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
       pbeta.resize(nm);
       prho0.resize(nm);
       pdelta.resize(nm);
+      for (int q = 0; q < nm; ++q)  // the exponent jumps between the merged pieces
+        pdelta[q] = (q + 1 < nm) ? (int32_t)(prho0[q + 1] - prho0[q] - (int64_t)pbeta[q] * (pk0[q + 1] - pk0[q])) : 0;
     }
     const int npm = (int)pbeta.size();
     int64_t nblk = D / kPieceLen + 1;
