@@ -2,6 +2,7 @@
 // the concave cover of k -> s(a_k), the good set G_p, and the device layout of
 // the coefficients.  Runs once per polynomial; not on the evaluation path.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -365,31 +366,74 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
       int64_t len = pk0[j + 1] - pk0[j];
       pdelta[j] = (j + 1 < np) ? (int32_t)(prho0[j + 1] - prho0[j] - (int64_t)pbeta[j] * len) : 0;
     }
-    // Merge a piece into its predecessor when the predecessor's rho line,
-    // continued, stays close to the piece's own: same slope, and (FP32 mode)
-    // no exponent jump, or (FP64 modes) a line offset of at most
-    // kMergeDrift bits.  A nearly flat cover then becomes one piece (the
-    // rounding of rho0 to integers no longer cuts it every few hundred
-    // terms), so its windows stay inside one piece for the tensor-core sums
-    // and the FP64 loops see fewer crossings; b_k stays within kMergeDrift
-    // bits of where the unmerged pieces put it.
+    // Merge runs of pieces into one piece with an integer line rho(k) =
+    // rho0 + beta (k - k0) that stays within kMergeDrift bits of every
+    // merged piece's own line (at both ends of each, hence all along it;
+    // FP64 modes; the FP32 mode merges only exact continuations, to keep
+    // its values inside the FP32 range).  A nearly flat cover then becomes
+    // one piece instead of being cut every few hundred terms by the rounding
+    // of rho0 to integers, and a cover like that of P' (steep over its first
+    // few terms, then rising by one bit per doubling of k) one or two: the
+    // windows stay inside one piece for the tensor-core sums, and the FP64
+    // loops see fewer crossings.  b_k = a_k 2^-rho(k) stays within
+    // kMergeDrift bits (kMergeDriftSteep for a nonzero slope: the measured
+    // certificates of steep covers, e.g. 1/k!, fared better with shorter
+    // pieces) of where the unmerged pieces put it.  For a run starting at
+    // piece m the slopes of the next pieces are tried and the one that
+    // merges the longest run is kept; rho0 is the middle of the feasible
+    // range.
     {
-      constexpr int64_t kMergeDrift = 8;
-      const int64_t max_off = fp32 ? 0 : kMergeDrift;
-      int m = 0;
-      for (int j = 1; j < np; ++j) {
-        const int64_t off = prho0[m] + (int64_t)pbeta[m] * (pk0[j] - pk0[m]) - prho0[j];
-        if (pbeta[j] == pbeta[m] && off >= -max_off && off <= max_off) continue;  // piece j joins piece m
-        ++m;
-        pk0[m] = pk0[j];
-        pbeta[m] = pbeta[j];
-        prho0[m] = prho0[j];
+      constexpr int64_t kMergeDrift = 24, kMergeDriftSteep = 8;
+      // longest run m..e-1 mergeable with slope b; the feasible rho0 range in [lo_r, hi_r]
+      auto run_with = [&](int m, int64_t b, int64_t &lo_r, int64_t &hi_r) {
+        const int64_t max_off = fp32 ? 0 : (b == 0 ? kMergeDrift : kMergeDriftSteep);
+        lo_r = INT64_MIN / 4;
+        hi_r = INT64_MAX / 4;
+        int e = m;
+        for (; e < np; ++e) {
+          int64_t a = lo_r, c = hi_r;
+          for (int end = 0; end < 2; ++end) {
+            const int64_t k = end ? (int64_t)pk0[e + 1] : (int64_t)pk0[e];
+            const int64_t target = end ? prho0[e] + (int64_t)pbeta[e] * (pk0[e + 1] - pk0[e]) : prho0[e];
+            const int64_t base = target - b * (k - pk0[m]);  // rho0 that puts the line on target at k
+            a = std::max(a, base - max_off);
+            c = std::min(c, base + max_off);
+          }
+          if (a > c) break;
+          lo_r = a;
+          hi_r = c;
+        }
+        return e;
+      };
+      std::vector<int32_t> nk0, nbeta;
+      std::vector<int64_t> nrho0;
+      for (int m = 0; m < np;) {
+        int best_e = m + 1;
+        int64_t best_b = pbeta[m], best_lo = prho0[m], best_hi = prho0[m];
+        for (int q = m; q < np && q < m + 6; ++q) {
+          if (q > m && pbeta[q] == pbeta[q - 1]) continue;
+          int64_t lo_r, hi_r;
+          const int e = run_with(m, pbeta[q], lo_r, hi_r);
+          if (e > best_e || (e == best_e && q == m)) {
+            best_e = e;
+            best_b = pbeta[q];
+            best_lo = lo_r;
+            best_hi = hi_r;
+          }
+        }
+        if (best_e == m + 1 && best_b == pbeta[m]) {
+          best_lo = best_hi = prho0[m];  // a piece on its own keeps its line
+        }
+        nk0.push_back(pk0[m]);
+        nbeta.push_back((int32_t)best_b);
+        nrho0.push_back(best_lo + (best_hi - best_lo) / 2);
+        m = best_e;
       }
-      const int nm = np > 0 ? m + 1 : 0;
-      pk0[nm] = (int32_t)(D + 1);
-      pk0.resize(nm + 1);
-      pbeta.resize(nm);
-      prho0.resize(nm);
+      const int nm = (int)nk0.size();
+      pk0.assign(nk0.begin(), nk0.end());
+      pk0.push_back((int32_t)(D + 1));
+      pbeta = nbeta;
+      prho0 = nrho0;
       pdelta.resize(nm);
       for (int q = 0; q < nm; ++q)  // the exponent jumps between the merged pieces
         pdelta[q] = (q + 1 < nm) ? (int32_t)(prho0[q + 1] - prho0[q] - (int64_t)pbeta[q] * (pk0[q + 1] - pk0[q])) : 0;
