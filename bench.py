@@ -87,18 +87,25 @@ def parse():
     return ap.parse_args()
 
 
-def workload(args, rank: int = 0):
+def workload(args, rank: int = 0, world: int = 1):
+    """The polynomial and this rank's points.  Under torchrun the ranks share
+    one point set of world x points points (the same coefficients, the
+    points drawn after them from the same generator), split by
+    lambda-sorted round-robin buckets (sharding.lambda_round_robin), so each
+    rank gets about `points` points and a like share of the window work."""
     import workloads as W
-    wl = W.unit_disk_d2pow20(n_points=args.points, d=args.degree)
-    if rank:  # each rank its own points, same polynomial
-        rng = np.random.default_rng(1000 + rank)
-        wl.points = W.sphere_points(args.points, rng)
+    from paper_2211_06320_gb300.sharding import lambda_round_robin
+    wl = W.unit_disk_d2pow20(n_points=args.points * world, d=args.degree)
+    if world > 1:
+        idx = lambda_round_robin(wl.points.re, wl.points.im, rank, world)
+        wl.points = W.Points(np.ascontiguousarray(wl.points.re[idx]), np.ascontiguousarray(wl.points.im[idx]))
     return wl
 
 
 def config(args, flush: bool):
     return {"workload": f"unit_disk_complex d={args.degree} (a_k uniform in unit disk, seed 1), "
-                        f"{args.points} sphere-uniform points per GPU, p=53",
+                        f"{args.points} sphere-uniform points per GPU (one shared set of {args.points} x GPUs, "
+                        f"split by lambda-sorted round-robin buckets), p=53",
             "degree": args.degree, "points_per_gpu": args.points, "p": 53,
             "l2": "flushed between steps (256 MiB write)" if flush else "not flushed"}
 
@@ -349,7 +356,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     F._load()
 
-    wl = workload(args, rank)
+    wl = workload(args, rank, world)
     n = wl.points.n
     t0 = time.perf_counter()
     P = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, None, 53)
@@ -409,7 +416,34 @@ def main():
         t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_dev = float(t.item())
-    value = world * n * args.steps / t_dev
+    if world > 1:  # the shared point set's size: every rank's share was evaluated
+        nt_all = torch.tensor([n], dtype=torch.int64, device="cuda")
+        dist.all_reduce(nt_all)
+        n_job = int(nt_all.item())
+    else:
+        n_job = n
+    value = n_job * args.steps / t_dev
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the
+    # timed region; every rank its own share, the slowest rank's time
+    hz_r = torch.from_numpy(wl.points.re).pin_memory()
+    hz_i = torch.from_numpy(wl.points.im).pin_memory()
+    hout = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        F.host_eval_raw(P, hz_r.data_ptr(), hz_i.data_ptr(), n, hout.data_ptr())
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s = F.host_eval_raw(P, hz_r.data_ptr(), hz_i.data_ptr(), n, hout.data_ptr())
+        assert s == 0
+    dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    e2e = {"value": n_job * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n_job,
+           "d2h_bytes_per_step": 24 * n_job}
 
     extras = {}
     if rank == 0:
@@ -488,20 +522,7 @@ def main():
         extras["tuning"] = dict(tuning, autotune_s=t_tune, autotuned=not args.no_tune)
         extras["wall_s_timed_region"] = wall
 
-        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-        hz_r = torch.from_numpy(wl.points.re).pin_memory()
-        hz_i = torch.from_numpy(wl.points.im).pin_memory()
-        hout = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-        for _ in range(2):
-            F.host_eval_raw(P, hz_r.data_ptr(), hz_i.data_ptr(), n, hout.data_ptr())
-        t0 = time.perf_counter()
-        e2e_steps = max(3, min(args.steps, 10))
-        for _ in range(e2e_steps):
-            s = F.host_eval_raw(P, hz_r.data_ptr(), hz_i.data_ptr(), n, hout.data_ptr())
-            assert s == 0
-        dt = time.perf_counter() - t0
-        extras["e2e"] = {"value": n * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
-                         "d2h_bytes_per_step": 24 * n}
+        extras["e2e"] = e2e
 
         if not args.no_extras:
             # GPU Horner baselines over all d+1 terms, one thread per point, on enough

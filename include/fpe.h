@@ -72,10 +72,14 @@ enum {
   FPE_HOST_ONLY = 8,   /* host analysis only (scales, cover, G_p; the -analyse
                           task of §8.1): no device memory is touched and the
                           handle cannot be evaluated                           */
-  FPE_ACCURATE = 16    /* window sums on the integer pipe in 128-bit fixed
+  FPE_ACCURATE = 16,   /* window sums on the integer pipe in 128-bit fixed
                           point: error <= u|P| + (2^-84 + L 2^-100) S for
                           every input (L = window length), at ~1.7x the time
                           of the default summation (see fpe_eval)              */
+  FPE_FORCE_DENSE = 32,  /* never use the sparse window sums (see fpe_eval)  */
+  FPE_FORCE_SPARSE = 64  /* use the sparse window sums for every window of
+                            the FP64 modes (see fpe_eval); not combinable
+                            with FPE_FORCE_DENSE                             */
 };
 
 /*
@@ -94,7 +98,8 @@ enum {
  *   n_coef   d + 1 >= 1 (leading zeros are trimmed: d is the last nonzero
  *            index, v the first; z^v is factored out as in §4.3).
  *   p        precision in significand bits, 2 <= p <= 53 (p <= 24 with FPE_FP32).
- *   flags    FPE_REAL | FPE_WITH_DERIV | FPE_FP32 | FPE_HOST_ONLY | FPE_ACCURATE.
+ *   flags    FPE_REAL | FPE_WITH_DERIV | FPE_FP32 | FPE_HOST_ONLY | FPE_ACCURATE,
+ *            FPE_FORCE_DENSE or FPE_FORCE_SPARSE.
  *   out      receives the handle.
  * Synchronous (uploads finish before return).  Errors: FPE_ERR_INVALID_ARG,
  * FPE_ERR_NONFINITE (a coefficient is NaN/inf), FPE_ERR_ZERO_POLY, FPE_ERR_OOM,
@@ -120,10 +125,21 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
  *   bits_lost   device int32[n] or NULL: estimated leading bits cancelled,
  *               max(0, ceil(N) - e) (Remark rmk:cancel, eq. slice).
  * Summation: by default each window is summed in FP64 toward its peak term
- * (top-down above k_lambda, bottom-up with a double-double 1/z below), which
- * keeps |P_gpu - P| within 2^-50 sum |a_k||z|^k for coefficients of random
- * phase; long runs of aligned terms (e.g. all a_k = 1 near z = 1) or of
- * negligible terms after a dominant one can exceed it by a small factor.
+ * (top-down above k_lambda, bottom-up with a double-double 1/z below), and
+ * every such sum carries a rounding-error certificate: beside the value the
+ * loop keeps, in FP32 rounded outward, a rigorous bound E of its rounding
+ * errors (half an ulp of each rounded result, carried by |w|) and a lower
+ * bound S' of its term magnitudes.  A window whose E plus the output
+ * rounding exceeds 7.6 u S' is summed again exactly on the integer pipe (as
+ * with FPE_ACCURATE), so for every input
+ *     |P_gpu - P| <= 2^-50 sum |a_k||z|^k   (FP64 modes, p = 53),
+ * with the dropped terms of §6 inside that budget (fpe_cert_stats counts the
+ * re-summed windows).  Windows of at least 384 terms inside one coefficient
+ * piece are summed exactly on the tensor cores (fpe_set_tensor_path).  A
+ * window with at most a quarter of its indices in G_p (FPE_FORCE_SPARSE: any
+ * window; FPE_FORCE_DENSE: none) is summed over its good indices alone, by
+ * Horner's scheme with power jumps z^(k' - k) in 128-bit fixed point on the
+ * integer pipe (error below L 2^-119 S, no certificate needed).
  * With FPE_ACCURATE the window is summed top-down by Horner's scheme on
  * the integer pipe: the partial sum is a complex 128-bit fixed-point value
  * with a 64-bit exponent, the point is used exactly, and each step truncates

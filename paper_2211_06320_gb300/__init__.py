@@ -31,6 +31,8 @@ FPE_WITH_DERIV = 2
 FPE_FP32 = 4
 FPE_HOST_ONLY = 8
 FPE_ACCURATE = 16
+FPE_FORCE_DENSE = 32
+FPE_FORCE_SPARSE = 64
 
 # every symbol include/fpe.h declares
 EXPORTED = [

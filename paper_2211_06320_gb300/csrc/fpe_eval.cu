@@ -575,6 +575,7 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
 // sum; no certificate is needed).  The powers come by binary powering; a_k =
 // b_k 2^rho(k) exactly.  Returns sum_{good k in [lo, hi]} a_k z^(k - lo).
 __device__ __forceinline__ bool sparse_window(const DevPoly &P, long long lo, long long hi) {
+  if (P.sparse_mode) return P.sparse_mode == 2;
   const long long g = P.gcount[hi + 1] - P.gcount[lo];
   return 4 * g < hi - lo + 1;
 }

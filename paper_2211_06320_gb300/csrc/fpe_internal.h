@@ -153,6 +153,7 @@ struct DevPoly {
   int32_t complex_coef;
   int32_t fp32;
   int32_t accurate;    // FPE_ACCURATE: window sums on the integer pipe
+  int32_t sparse_mode;  // 0: sparse window sums where G_p fills at most a quarter of the window; 1: never; 2: always
   int32_t log2_piece;  // kLog2PieceLen or kLog2PieceLenF32
   double a0_re, a0_im;  // a_0 as a normalised mantissa (0 when v > 0)
   int64_t a0_e;

@@ -211,13 +211,18 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
     set_error("fpe_precondition: re is NULL or n_coef out of [1, 2^30]");
     return FPE_ERR_INVALID_ARG;
   }
-  if (flags & ~(uint32_t)(FPE_REAL | FPE_WITH_DERIV | FPE_FP32 | FPE_HOST_ONLY | FPE_ACCURATE)) {
+  if (flags & ~(uint32_t)(FPE_REAL | FPE_WITH_DERIV | FPE_FP32 | FPE_HOST_ONLY | FPE_ACCURATE | FPE_FORCE_DENSE |
+                          FPE_FORCE_SPARSE)) {
     set_error("fpe_precondition: unknown flag bits");
     return FPE_ERR_INVALID_ARG;
   }
   const bool fp32 = (flags & FPE_FP32) != 0;
   if (p < 2 || p > 53 || (fp32 && p > 24)) {
     set_error("fpe_precondition: p must be in [2, 53] ([2, 24] with FPE_FP32)");
+    return FPE_ERR_INVALID_ARG;
+  }
+  if ((flags & FPE_FORCE_DENSE) && (flags & FPE_FORCE_SPARSE)) {
+    set_error("fpe_precondition: FPE_FORCE_DENSE and FPE_FORCE_SPARSE together");
     return FPE_ERR_INVALID_ARG;
   }
   if (fp32 && (flags & FPE_ACCURATE)) {
@@ -555,6 +560,7 @@ fpe_status precondition_host(const double *re, const double *im, const int64_t *
   dp.complex_coef = cplx ? 1 : 0;
   dp.fp32 = fp32 ? 1 : 0;
   dp.accurate = (flags & FPE_ACCURATE) ? 1 : 0;
+  dp.sparse_mode = (flags & FPE_FORCE_DENSE) ? 1 : ((flags & FPE_FORCE_SPARSE) ? 2 : 0);
   dp.log2_piece = log2_piece;
 
   // P' (§7.2): coefficients (k+1) a_{k+1}, rounded once, preconditioned separately

@@ -115,6 +115,12 @@ def test_precondition_errors(F):
     with pytest.raises(F.FpeError) as e:
         F.fpe_precondition(np.array([1.0]), None, np.array([1 << 50]), 53, F.FPE_HOST_ONLY)
     assert e.value.status == F.FPE_ERR_INVALID_ARG
+    with pytest.raises(F.FpeError) as e:  # the forced window-sum kinds exclude each other
+        F.fpe_precondition(np.array([1.0, 2.0]), None, None, 53,
+                           F.FPE_HOST_ONLY | F.FPE_FORCE_DENSE | F.FPE_FORCE_SPARSE)
+    assert e.value.status == F.FPE_ERR_INVALID_ARG
+    for fl in (F.FPE_FORCE_DENSE, F.FPE_FORCE_SPARSE):  # each alone is accepted
+        F.fpe_precondition(np.array([1.0, 2.0]), None, None, 53, F.FPE_HOST_ONLY | fl)
 
 
 def test_host_only_handle_refuses_evaluation(F):

@@ -442,3 +442,21 @@ def test_bits_lost_diagnostic(env, name):
     assert np.all(bl[~moderate] >= floor_bits[~moderate] - 8)
     if name == "inverse_factorial":
         assert bl.max() > 30  # e^x at x ~ -50 cancels ~144 bits in the sum
+
+
+@pytest.mark.parametrize("case", ["dense_forced_sparse", "sparse_forced_dense"])
+def test_forced_window_sum_kind(env, case):
+    """FPE_FORCE_SPARSE sums every window over its good indices alone (on a
+    dense polynomial: all windows); FPE_FORCE_DENSE never does (on a sparse
+    one: Horner over every index, zeros included, with the certificates).
+    Both meet the tolerance."""
+    torch, F = env
+    if case == "dense_forced_sparse":
+        wl = W.unit_square_d1000(n_points=4096)
+        flags = F.FPE_FORCE_SPARSE
+    else:
+        wl = W.sparse_d2pow22(n_points=1 << 13)
+        flags = F.FPE_FORCE_DENSE
+    st = check_workload(env, wl.coeffs, wl.points, n_full=48, flags=flags)
+    print(case, st)
+
