@@ -37,7 +37,8 @@ UNIT = "evals/s"
 # workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on: the file records their SHA-256.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_unit_disk_d2pow20.txt")
-KERNEL_SOURCES = ["fpe_eval.cu", "fpe_device.cuh", "fpe_internal.h", "fpe_tc.cu", "fpe_tc_arith.cuh"]
+KERNEL_SOURCES = ["fpe_eval.cu", "fpe_device.cuh", "fpe_internal.h", "fpe_window.cuh", "fpe_tc.cu",
+                  "fpe_tc_arith.cuh", "fpe_tc05.cuh"]
 
 
 def kernel_sources_sha() -> str:
