@@ -198,13 +198,18 @@ def oracle_cpu_baseline(wl, n_sample: int, variants: bool = False):
 
 def workload_legs(F, torch, st):
     """Evaluations/s on the benchmark's other workload shapes (the default
-    configuration of fpe_eval; the d = 1000 one also with the tensor path off)."""
+    configuration of fpe_eval; the d = 1000 one also with the tensor path off):
+    d = 1000 unit square, 1/k! at d = 10^5, the Mandelbrot iterate at n = 20
+    (d = 2^20, coefficients from workloads.mandelbrot_fast), sparse d = 2^22."""
     import workloads as W
     legs = {}
     for name, make in (("unit_square_d1000", lambda: W.unit_square_d1000()),
                        ("inverse_factorial_d1e5", lambda: W.inverse_factorial_d1e5(n_points=1 << 20)),
+                       ("mandelbrot_n20", lambda: W.mandelbrot_real(20, n_points=1 << 20)),
                        ("sparse_d2pow22", lambda: W.sparse_d2pow22(n_points=1 << 20))):
+        t0 = time.perf_counter()
         wl = make()
+        t_gen = time.perf_counter() - t0
         t0 = time.perf_counter()
         P = F.fpe_precondition(wl.coeffs.re, wl.coeffs.im, wl.coeffs.e2, wl.p)
         t_pre = time.perf_counter() - t0
@@ -213,7 +218,8 @@ def workload_legs(F, torch, st):
         n = wl.points.n
         out = F.empty_out(n)
         nt = torch.empty(n, dtype=torch.int32, device="cuda")
-        res = {"degree": wl.coeffs.n_coef - 1, "points": n, "precondition_ms": t_pre * 1e3}
+        res = {"degree": wl.coeffs.n_coef - 1, "points": n, "precondition_ms": t_pre * 1e3,
+               "generate_s": t_gen}
         for label, thr in (("default", None), ("tensor_off", 0)):
             if thr is not None and name != "unit_square_d1000":
                 continue

@@ -114,6 +114,14 @@ def test_mandelbrot(env):
     print("mandelbrot_n11", st)
 
 
+def test_mandelbrot_n20(env):
+    """The Mandelbrot iterate at n = 20 (d = 2^20, coefficients up to 2^616226),
+    2^14 real points in [-2, 0.25]."""
+    wl = W.mandelbrot_real(20, n_points=1 << 14)
+    st = check_workload(env, wl.coeffs, wl.points, n_full=16)
+    print("mandelbrot_n20", st)
+
+
 def test_sparse_d2pow22(env):
     wl = W.sparse_d2pow22(n_points=1 << 15)
     st = check_workload(env, wl.coeffs, wl.points, n_full=24)

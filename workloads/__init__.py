@@ -169,6 +169,34 @@ def mandelbrot(n: int) -> Coeffs:
     return Coeffs(m, None, e)
 
 
+def mandelbrot_fast(n: int) -> Coeffs:
+    """mandelbrot(n) by the C generator (mandelbrot_gen.c: the same convolution,
+    each output summed over the terms within 2^-128 of its largest, OpenMP),
+    practical up to n = 20; compiled with gcc on first use into a build
+    folder beside this file."""
+    import ctypes
+    import os
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "mandelbrot_gen.c")
+    out_dir = os.path.join(here, "_build")
+    lib = os.path.join(out_dir, "mandelbrot_gen.so")
+    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        os.makedirs(out_dir, exist_ok=True)
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, lib)
+    L = ctypes.CDLL(lib)
+    L.mandel_coeffs.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    L.mandel_coeffs.restype = ctypes.c_int
+    N = (1 << n) + 1
+    m = np.zeros(N)
+    e = np.zeros(N, dtype=np.int64)
+    if L.mandel_coeffs(int(n), m.ctypes.data, e.ctypes.data) != 0:
+        raise MemoryError("mandel_coeffs")
+    return Coeffs(m, None, e)
+
+
 def sparse_real(d: int, density: float, rng: np.random.Generator) -> Coeffs:
     """Bernoulli(density) mask then values U[-1, 1]; a_d forced nonzero.
     Draw order: mask uniforms (d+1), then values (d+1)."""
@@ -297,9 +325,11 @@ def inverse_factorial_d1e5(n_points: int = 1 << 20, d: int = 100_000) -> Workloa
 
 
 def mandelbrot_real(n: int, n_points: int = 1 << 20) -> Workload:
-    """Hyperbolic-centre polynomial p_n (degree 2^n); real points U[-2, 0.25] (seed 2)."""
+    """Hyperbolic-centre polynomial p_n (degree 2^n); real points U[-2, 0.25] (seed 2).
+    n > 12 uses the C generator (mandelbrot_fast)."""
     rng = np.random.default_rng(2)
-    return Workload(f"mandelbrot_n{n}", mandelbrot(n), real_line_points(n_points, -2.0, 0.25, rng), 53)
+    coef = mandelbrot(n) if n <= 12 else mandelbrot_fast(n)
+    return Workload(f"mandelbrot_n{n}", coef, real_line_points(n_points, -2.0, 0.25, rng), 53)
 
 
 def sparse_d2pow22(n_points: int = 1 << 20, d: int = 1 << 22) -> Workload:
