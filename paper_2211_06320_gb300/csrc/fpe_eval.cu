@@ -750,6 +750,9 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, 
     sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, q, cnt, resum, out, nterms, bits_lost);
 }
 
+// failing chunks of one warp group up to which the whole warp sums each in turn
+constexpr int kGroupResumShared = 4;
+
 // Group g of a long window (ng groups): lane i sums its chunk, the 32 slots
 // are combined; lane 0 returns the group's value sv and carry gout.
 template <bool CC, bool CZ, bool ACC, bool F32>
@@ -822,6 +825,7 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
   const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
   const xint zero = xint_norm(0, 0, 0, 0, 0);
   xint sv = zero, carry = zero;
+  bool failed = false;
   if (clo <= chi && sparse_window(P, clo, chi)) {
     sv = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, clo, chi);
   } else if (clo <= chi) {
@@ -830,10 +834,9 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
     long long base;
     bool ok;
     const xint X = range_sum<CC, CZ, true>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base, ok);
-    if (!ok) {  // not certified: the chunk's exact integer-pipe sum, in its own slot
-      atomicAdd(&cnt[kCntResumGroups], 1u);
-      const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
-      sv = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
+    failed = !ok;
+    if (failed) {
+      // summed exactly below
     } else if (chi < r.kl) {
       carry = xint_mul(X, u);  // below the peak: X / z to the next slot
       carry.e -= f;
@@ -841,6 +844,36 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
       sv = xint_mul(X, xint_pow_z(r.zr, r.zi, base - clo, f));
     } else {
       sv = X;
+    }
+  }
+  // Chunks whose FP64 sums were not certified get their exact integer-pipe sum,
+  // in their own slot.  A few are summed by the whole warp in turn (lane i
+  // taking the sub-chunk [c + i D, c + (i + 1) D - 1], D = ceil(C / 32), times
+  // z^(i D), then a butterfly), so one failing lane does not hold 31 others
+  // for C integer steps; many are summed by their own lanes at once.
+  const unsigned fm = __ballot_sync(0xffffffffu, failed);
+  if (fm) {
+    if (lane == 0) atomicAdd(&cnt[kCntResumGroups], (unsigned)__popc(fm));
+    if (__popc(fm) > kGroupResumShared) {
+      if (failed) {
+        const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
+        sv = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
+      }
+    } else {
+      for (unsigned m = fm; m; m &= m - 1) {
+        const int fl = __ffs(m) - 1;
+        const long long fclo = r.lo + (long long)g * 32 * C + (long long)fl * C, fchi = min(fclo + C - 1, r.hi);
+        const long long Ds = (fchi - fclo + 32) / 32;
+        const long long slo = fclo + lane * Ds, shi = min(slo + Ds - 1, fchi);
+        xint part = zero;
+        if (slo <= shi) {
+          const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, slo, shi);
+          part = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
+          if (lane > 0 && (part.x || part.y)) part = xint_mul(part, xint_pow_z(r.zr, r.zi, lane * Ds, f));
+        }
+        for (int s2 = 16; s2 >= 1; s2 >>= 1) part = xint_add(part, shfl_xint(part, s2, 2));
+        if (lane == fl) sv = part;
+      }
     }
   }
   const xint inc = shfl_xint(carry, 1, 0);
