@@ -124,8 +124,9 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
  *   nterms      device int32[n] or NULL: #(G_p cap [l, r]) per point.
  *   bits_lost   device int32[n] or NULL: estimated leading bits cancelled,
  *               max(0, ceil(N) - e) (Remark rmk:cancel, eq. slice).
- * Summation: by default each window is summed in FP64 toward its peak term
- * (top-down above k_lambda, bottom-up with a double-double 1/z below), and
+ * Summation: by default each window up to the long-window length (see
+ * fpe_set_tuning) is summed in FP64 toward its peak term (top-down above
+ * k_lambda, bottom-up with a double-double 1/z below), and
  * every such sum carries a rounding-error certificate: beside the value the
  * loop keeps, in FP32 rounded outward, a rigorous bound E of its rounding
  * errors (half an ulp of each rounded result, carried by |w|) and a lower
@@ -134,7 +135,9 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
  * with FPE_ACCURATE), so for every input
  *     |P_gpu - P| <= 2^-50 sum |a_k||z|^k   (FP64 modes, p = 53),
  * with the dropped terms of §6 inside that budget (fpe_cert_stats counts the
- * re-summed windows).  Windows of at least 384 terms inside one coefficient
+ * re-summed windows).  Longer windows are cut into lane chunks that are
+ * summed exactly on the integer pipe, as with FPE_ACCURATE (on this GPU that
+ * costs less than FP64 with certificates).  Windows of at least 384 terms inside one coefficient
  * piece are summed exactly on the tensor cores (fpe_set_tensor_path).  A
  * window with at most a quarter of its indices in G_p (FPE_FORCE_SPARSE: any
  * window; FPE_FORCE_DENSE: none) is summed over its good indices alone, by
@@ -314,12 +317,13 @@ fpe_status fpe_get_tensor_path(fpe_poly_t P, int64_t *min_window, int32_t *n_pie
 fpe_status fpe_tensor_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream);
 /*
  * fpe_cert_stats: the rounding-error certificates of the handle's last
- *   fpe_eval (default FP64 mode), in stats[0..1]: short windows whose FP64
- *   sum failed its certificate and was summed again exactly on the integer
- *   pipe, and lane chunks of long windows likewise.  The default mode's
- *   values meet |P_gpu - P| <= 2^-50 sum |a_k||z|^k through these re-sums.
- *   Zero for the other modes.  Waits for the work queued on cuda_stream.
- *   FPE_ERR_INVALID_ARG for NULL arguments or n < 2.
+ *   fpe_eval (default FP64 mode), in stats[0]: the windows whose FP64 sum
+ *   failed its certificate and was summed again exactly on the integer pipe.
+ *   The default mode's values meet |P_gpu - P| <= 2^-50 sum |a_k||z|^k
+ *   through these re-sums.  (Long windows, summed by warp groups, are summed
+ *   exactly on the integer pipe in the first place.)  stats[1 .. n-1] are
+ *   set to zero.  Zero for the other modes.  Waits for the work queued on
+ *   cuda_stream.  FPE_ERR_INVALID_ARG for NULL arguments or n < 1.
  */
 fpe_status fpe_cert_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream);
 

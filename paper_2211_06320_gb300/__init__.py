@@ -492,12 +492,12 @@ def fpe_tensor_stats(P: Poly, stream=None) -> dict:
     return dict(zip(TENSOR_STATS, (int(x) for x in v)))
 
 
-CERT_STATS = ("resummed_windows", "resummed_chunks")
+CERT_STATS = ("resummed_windows",)
 
 
 def fpe_cert_stats(P: Poly, stream=None) -> dict:
-    """Windows and long-window chunks of the last fpe_eval whose FP64 sums
-    failed their rounding-error certificates and were summed again exactly."""
+    """Windows of the last fpe_eval whose FP64 sums failed their
+    rounding-error certificates and were summed again exactly."""
     v = (ctypes.c_int64 * len(CERT_STATS))()
     _check(_load().fpe_cert_stats(P.handle, v, len(CERT_STATS), _stream(stream)), "fpe_cert_stats")
     return dict(zip(CERT_STATS, (int(x) for x in v)))

@@ -884,13 +884,15 @@ __host__ __device__ __forceinline__ void isum_step(isum &h, const iw &w, int we6
   h.G = G;
 }
 
-// extended double-double of a fixed-point sum
-__device__ __forceinline__ xdd xdd_from_isum(const isum &h) {
+// a fixed-point sum as a normalised xint (zero: the zero xint)
+__host__ __device__ __forceinline__ xint xint_from_isum(const isum &h) {
   const int sr = h.xr < 0, si = h.xi < 0;
   const u128 ar = sr ? (u128)(-h.xr) : (u128)h.xr, ai = si ? (u128)(-h.xi) : (u128)h.xi;
-  if (!ar && !ai) return xdd_zero();
-  return xdd_from_xint(xint_norm(ar, sr, ai, si, (long long)h.G + 126));
+  return xint_norm(ar, sr, ai, si, (long long)h.G + 126);
 }
+
+// extended double-double of a fixed-point sum
+__device__ __forceinline__ xdd xdd_from_isum(const isum &h) { return xdd_from_xint(xint_from_isum(h)); }
 
 // ---------------------------------------------------------------------------
 // Extended values of the FP32 mode: an FP64 complex mantissa with an int64

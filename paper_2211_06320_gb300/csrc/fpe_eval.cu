@@ -295,7 +295,7 @@ __device__ __forceinline__ void write_diag(const DevPoly &P, const PointRec &r, 
 // (relative to z^(its top index)); base is kl - 1 when both parts exist.
 // ok: both parts passed their rounding-error certificates (cert_pass); the
 // caller sums the range again on the integer pipe when it is false.
-template <bool CC, bool CZ, bool LONG>
+template <bool CC, bool CZ>
 __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi, double mr, double mi, int f,
                                           const xint &u, long long lo, long long hi, long long kl, long long &base,
                                           bool &ok) {
@@ -304,15 +304,12 @@ __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi
   const long long top_lo = max(kl, lo);
   const long long low_hi = min(top_lo - 1, hi);
   const bool has_up = top_lo <= hi, has_low = lo <= low_hi;
-  constexpr long long kTopBlockMin = 32;  // top-part terms from which blocks of eight may pay for z^8
   ok = true;
   if (has_up) {
     double hr, hm;
     long long rho;
     Cert ct;
-    const bool blocks8 = LONG && hi - top_lo + 1 >= kTopBlockMin;
-    const xdd z8 = blocks8 ? xdd_from_xint(xint_pow_z(zr, zi, 8, f)) : xdd_zero();
-    window_horner<CC, CZ, LONG>(P, P.b, zr, zi, top_lo, hi, z8, blocks8, hr, hm, rho, ct);
+    window_horner<CC, CZ>(P, P.b, zr, zi, top_lo, hi, hr, hm, rho, ct);
     ok = cert_pass(ct);
     X = xint_from_dd2(hr, 0.0, hm, 0.0, rho);
     base = top_lo;
@@ -322,18 +319,14 @@ __device__ __forceinline__ xint range_sum(const DevPoly &P, double zr, double zi
     long long rho;
     const bool blocks = low_hi - lo + 1 >= kBlockMin;
     const xdd u1 = xdd_from_xint(u);
-    xdd up[4] = {u1, u1, u1, u1};
-    if (blocks) {  // powers u^3, u^4 (LONG: u^7, u^8) of 1/m on the integer pipe
-      const xint u2 = xint_sqr(u), u3 = xint_mul(u2, u), u4 = xint_sqr(u2);
-      up[0] = xdd_from_xint(u3);
-      up[1] = xdd_from_xint(u4);
-      if (LONG) {
-        up[2] = xdd_from_xint(xint_mul(u4, u3));
-        up[3] = xdd_from_xint(xint_sqr(u4));
-      }
+    xdd up[2] = {u1, u1};
+    if (blocks) {  // powers u^3, u^4 of 1/m on the integer pipe
+      const xint u2 = xint_sqr(u);
+      up[0] = xdd_from_xint(xint_mul(u2, u));
+      up[1] = xdd_from_xint(xint_sqr(u2));
     }
     Cert ct;
-    window_horner_rev<CC, CZ, LONG>(P, P.b, u1, up, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho, ct);
+    window_horner_rev<CC, CZ>(P, P.b, u1, up, blocks, -f, zr, zi, lo, low_hi, hr, hm, rho, ct);
     ok = ok && cert_pass(ct);
     if (has_up && (X.x || X.y)) X = xint_mul(X, xint_from_dd2(mr, 0.0, mi, 0.0, f));  // z^top_lo = z * z^low_hi
     X = xint_add(X, xint_from_dd2(hr, 0.0, hm, 0.0, rho));
@@ -537,7 +530,8 @@ __device__ __forceinline__ int int_horner(const DevPoly &P, isum &h, const iw &w
 // 2^rho(top)) on the integer pipe down to lo; returns sum_{k=lo}^{..}
 // a_k z^(k - lo) as extended double-double.
 template <bool CC, bool CZ>
-__device__ __forceinline__ xdd int_tail(const DevPoly &P, isum h, double zr, double zi, long long top, long long lo) {
+__device__ __forceinline__ xint int_tail_x(const DevPoly &P, isum h, double zr, double zi, long long top,
+                                           long long lo) {
   int j = P.piece_first[top >> P.log2_piece];
   while (P.piece_k0[j + 1] <= top) ++j;
   const iw w = iw_from(zr, CZ ? zi : 0.0);
@@ -547,9 +541,13 @@ __device__ __forceinline__ xdd int_tail(const DevPoly &P, isum h, double zr, dou
   else
     j = int_horner<CC, CZ, false>(P, h, w, top - 1, j, lo, t0);
   isum_rotate(h, (int)((w.q * ((top - lo) & 3)) & 3));  // h = i^(q (top - lo)) g
-  xdd X = xdd_from_isum(h);
-  if (X.rh != 0.0 || X.ih != 0.0) X.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
+  xint X = xint_from_isum(h);
+  if (X.x || X.y) X.e += P.piece_rho0[j] + (long long)P.piece_beta[j] * (lo - P.piece_k0[j]);
   return X;
+}
+template <bool CC, bool CZ>
+__device__ __forceinline__ xdd int_tail(const DevPoly &P, isum h, double zr, double zi, long long top, long long lo) {
+  return xdd_from_xint(int_tail_x<CC, CZ>(P, h, zr, zi, top, lo));
 }
 
 // sum_{k=lo}^{hi} a_k z^(k - lo) in extended double-double by Horner taken
@@ -557,7 +555,8 @@ __device__ __forceinline__ xdd int_tail(const DevPoly &P, isum h, double zr, dou
 // or less of the partial sum, so the order that makes FP64 accurate (toward
 // the peak term) is not needed and no FP64 instruction is spent.
 template <bool CC, bool CZ>
-__device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, double zi, long long lo, long long hi) {
+__device__ __forceinline__ xint window_sum_int_x(const DevPoly &P, double zr, double zi, long long lo,
+                                                 long long hi) {
   isum h;
   if (CC) {
     const double2 c = reinterpret_cast<const double2 *>(P.b)[hi];
@@ -565,7 +564,11 @@ __device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, doubl
   } else {
     h = isum_from(P.b[hi], 0.0);
   }
-  return int_tail<CC, CZ>(P, h, zr, zi, hi, lo);
+  return int_tail_x<CC, CZ>(P, h, zr, zi, hi, lo);
+}
+template <bool CC, bool CZ>
+__device__ __forceinline__ xdd window_sum_int(const DevPoly &P, double zr, double zi, long long lo, long long hi) {
+  return xdd_from_xint(window_sum_int_x<CC, CZ>(P, zr, zi, lo, hi));
 }
 
 // Sparse windows: when at most a quarter of [lo, hi] lies in G_p, Horner's
@@ -660,7 +663,7 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
         xint u = xint_norm(0, 0, 0, 0, 0);
         if (r.lo < r.kl) u = recip_xint(mr, mi);
         bool ok;
-        const xint X = range_sum<CC, CZ, false>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base, ok);
+        const xint X = range_sum<CC, CZ>(P, r.zr, r.zi, mr, mi, f, u, r.lo, r.hi, r.kl, base, ok);
         if (!ok) {  // not certified: k_resum sums the window exactly
           list_resum(cnt, resum, q);
           return;
@@ -723,14 +726,15 @@ __device__ __forceinline__ xint shfl_xint(const xint &v, int sft, int mode) {
 // Long windows: warp groups.  A window of length L gets ng = ceil(L / (32 lane_chunk))
 // groups of S = 32 C terms with C = ceil(L / (32 ng)); lane i of group g owns
 // the chunk [c_i, c_i + C - 1], c_i = l + g S + i C, and a slot value s_i with
-//   sum over the window = z^l sum_g (z^S)^g sum_i (z^C)^i s_i:
-//   chunk above the peak:     s_i = sum a_k z^(k - c_i) (top-down);
-//   chunk below the peak:     its sum z^(c_{i+1} - 1) R goes to slot i+1 as R / z;
-//   chunk holding the peak:   both parts, times z^(base - c_i).
-// A group's value is sum_i (z^C)^i s_i: each lane multiplies its slot by its
-// own power, then a butterfly adds the slots; lane 31's carry goes to the
-// next group.  The warp that finishes a window's last group combines them
-// and applies z^(l + v).
+//   sum over the window = z^l sum_g (z^S)^g sum_i (z^C)^i s_i.
+// FP64 precision: s_i = sum a_k z^(k - c_i), exactly on the integer pipe, and
+// the group's value sum_i (z^C)^i s_i by a tree over the lanes (lanes_tree).
+// FP32 mode: FP32 passes toward the peak, so a chunk below the peak hands its
+// sum z^(c_{i+1} - 1) R to slot i+1 as R / z (the group's carry out of lane
+// 31 goes to the next group), the chunk holding the peak sums both parts, and
+// each lane scales its slot by its own power before a butterfly adds them.
+// The warp that finishes a window's last group combines the groups and
+// applies z^(l + v).
 __device__ __forceinline__ int group_slot(int i, int g, int gbase, int cap) {
   return g == 0 ? i : cap + gbase + g - 1;
 }
@@ -750,8 +754,47 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, 
     sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, q, cnt, resum, out, nterms, bits_lost);
 }
 
-// failing chunks of one warp group up to which the whole warp sums each in turn
-constexpr int kGroupResumShared = 4;
+// a b for xints of which only the parts the flags allow are nonzero: VC, a
+// complex; MC, b complex.  Real operands take one 128-bit product instead of
+// four, with the result xint_mul would give.
+template <bool VC, bool MC>
+__device__ __forceinline__ xint xint_mul_k(const xint &a, const xint &b) {
+  if (MC) return xint_mul(a, b);
+  if (!VC) return xint_norm(mulhi128(a.x, b.x), a.sx ^ b.sx, 0, 0, a.e + b.e + 2);
+  return xint_norm(mulhi128(a.x, b.x), a.sx ^ b.sx, mulhi128(a.y, b.x), a.sy ^ b.sx, a.e + b.e + 2);
+}
+
+// z^n (n >= 1) by binary powering on the integer pipe; CZ false: z real
+template <bool CZ>
+__device__ __forceinline__ xint xint_pow_z_k(double zr, double zi, long long n, int f) {
+  if (CZ) return xint_pow_z(zr, zi, n, f);
+  const double mr = scale2(zr, -f);
+  const xint z = xint_norm(u128_from_unit(mr), mr < 0.0, 0, 0, -1);
+  xint r = z;
+  for (int b = 62 - __clzll(n); b >= 0; --b) {
+    r = xint_mul_k<false, false>(r, r);
+    if ((n >> b) & 1) r = xint_mul_k<false, false>(r, z);
+  }
+  r.e += (long long)f * n;
+  return r;
+}
+
+// sum_i (z^C)^i v_i over the 32 lanes' values, into lane 0, by a tree: at
+// level s = 1, 2, 4, 8, 16 every lane adds the value of lane + s times
+// Z^s (Z = z^C, squared between levels).  Lane i with i a multiple of 2s then
+// holds sum_{j < 2s} Z^j v_(i+j); the other lanes' values are never read by
+// lane 0.  Every lane runs the same steps: no lane waits on another's branch.
+template <bool VC, bool CZ>
+__device__ __forceinline__ xint lanes_tree(xint v, double zr, double zi, long long C, int f) {
+  xint Z = xint_pow_z_k<CZ>(zr, zi, C, f);
+#pragma unroll 1
+  for (int s = 1; s < 32; s <<= 1) {
+    const xint o = shfl_xint(v, s, 1);
+    v = xint_add(v, xint_mul_k<VC || CZ, CZ>(o, Z));
+    if (s < 16) Z = CZ ? xint_sqr(Z) : xint_mul_k<false, false>(Z, Z);
+  }
+  return v;
+}
 
 // Group g of a long window (ng groups): lane i sums its chunk, the 32 slots
 // are combined; lane 0 returns the group's value sv and carry gout.
@@ -803,88 +846,20 @@ __device__ __forceinline__ void sum_group(const DevPoly &P, const PointRec &r, i
     gout_out = xdd_from_xd(go);
     return;
   }
-  if (ACC) {
-    xdd sv = xdd_zero();
-    if (clo <= chi) {
-      if (sparse_window(P, clo, chi)) {
-        const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
-        const xint X = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, clo, chi);
-        sv = xdd_from_xint(X);
-      } else {
-        sv = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
-      }
-    }
-    if (lane > 0 && (sv.rh != 0.0 || sv.ih != 0.0)) sv = xdd_mul(sv, xdd_pow_int(r.zr, r.zi, lane * C));
-    for (int s = 16; s >= 1; s >>= 1) sv = xdd_add(sv, shfl_xor_xdd(sv, s));
-    sv_out = sv;
-    gout_out = xdd_zero();
-    return;
-  }
-  // the bookkeeping in fixed point on the integer pipe: 1/z, the carries,
-  // the lanes' powers and the butterfly
+  // FP64 precision (either mode): each lane's chunk exactly on the integer
+  // pipe, top-down (the order does not matter there).  On this GPU an
+  // integer Horner step costs less issue time than an FP64 step with its
+  // certificate (one FP64 warp instruction takes as long as about 38 integer
+  // ones), and every lane runs the same loop: no split into chunks summed
+  // top-down and bottom-up, no re-sum of uncertified chunks.
   const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
-  const xint zero = xint_norm(0, 0, 0, 0, 0);
-  xint sv = zero, carry = zero;
-  bool failed = false;
-  if (clo <= chi && sparse_window(P, clo, chi)) {
-    sv = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, clo, chi);
-  } else if (clo <= chi) {
-    const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
-    const xint u = recip_xint(mr, mi);
-    long long base;
-    bool ok;
-    const xint X = range_sum<CC, CZ, true>(P, r.zr, r.zi, mr, mi, f, u, clo, chi, r.kl, base, ok);
-    failed = !ok;
-    if (failed) {
-      // summed exactly below
-    } else if (chi < r.kl) {
-      carry = xint_mul(X, u);  // below the peak: X / z to the next slot
-      carry.e -= f;
-    } else if (base > clo) {
-      sv = xint_mul(X, xint_pow_z(r.zr, r.zi, base - clo, f));
-    } else {
-      sv = X;
-    }
-  }
-  // Chunks whose FP64 sums were not certified get their exact integer-pipe sum,
-  // in their own slot.  A few are summed by the whole warp in turn (lane i
-  // taking the sub-chunk [c + i D, c + (i + 1) D - 1], D = ceil(C / 32), times
-  // z^(i D), then a butterfly), so one failing lane does not hold 31 others
-  // for C integer steps; many are summed by their own lanes at once.
-  const unsigned fm = __ballot_sync(0xffffffffu, failed);
-  if (fm) {
-    if (lane == 0) atomicAdd(&cnt[kCntResumGroups], (unsigned)__popc(fm));
-    if (__popc(fm) > kGroupResumShared) {
-      if (failed) {
-        const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, clo, chi);
-        sv = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
-      }
-    } else {
-      for (unsigned m = fm; m; m &= m - 1) {
-        const int fl = __ffs(m) - 1;
-        const long long fclo = r.lo + (long long)g * 32 * C + (long long)fl * C, fchi = min(fclo + C - 1, r.hi);
-        const long long Ds = (fchi - fclo + 32) / 32;
-        const long long slo = fclo + lane * Ds, shi = min(slo + Ds - 1, fchi);
-        xint part = zero;
-        if (slo <= shi) {
-          const xdd Y = window_sum_int<CC, CZ>(P, r.zr, r.zi, slo, shi);
-          part = xint_from_dd2(Y.rh, Y.rl, Y.ih, Y.il, Y.e);
-          if (lane > 0 && (part.x || part.y)) part = xint_mul(part, xint_pow_z(r.zr, r.zi, lane * Ds, f));
-        }
-        for (int s2 = 16; s2 >= 1; s2 >>= 1) part = xint_add(part, shfl_xint(part, s2, 2));
-        if (lane == fl) sv = part;
-      }
-    }
-  }
-  const xint inc = shfl_xint(carry, 1, 0);
-  if (lane > 0) sv = xint_add(sv, inc);
-  const xint gout = shfl_xint(carry, 31, 1);  // lane 31's carry, read by lane 0
-  // sum_i (z^C)^i s_i: each lane scales its slot by its own power, then a
-  // butterfly adds the 32 slots with every lane busy
-  if (lane > 0 && (sv.x || sv.y)) sv = xint_mul(sv, xint_pow_z(r.zr, r.zi, lane * C, f));
-  for (int s = 16; s >= 1; s >>= 1) sv = xint_add(sv, shfl_xint(sv, s, 2));
+  xint sv = xint_norm(0, 0, 0, 0, 0);
+  if (clo <= chi)
+    sv = sparse_window(P, clo, chi) ? window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, clo, chi)
+                                    : window_sum_int_x<CC, CZ>(P, r.zr, r.zi, clo, chi);
+  sv = lanes_tree<CC, CZ>(sv, r.zr, r.zi, C, f);
   sv_out = xdd_from_xint(sv);
-  gout_out = xdd_from_xint(gout);
+  gout_out = xdd_zero();
 }
 
 // A long window with one group: its value times z^(l + v), written by one thread.

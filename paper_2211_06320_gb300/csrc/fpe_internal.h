@@ -124,8 +124,7 @@ constexpr int kCntTcSubtiles = 13; // tensor-core MMA sub-tiles
 constexpr int kCntTcPoints = 14;   // points summed on the tensor cores
 constexpr int kCntTcRejected = 15; // tensor-core points handed back to the FP64 kernels
 constexpr int kCntResum = 16;      // short windows whose FP64 sum was not certified, listed for the exact re-sum
-constexpr int kCntResumGroups = 17; // lane chunks of long windows re-summed exactly in place
-constexpr int kNumCounters = 18;
+constexpr int kNumCounters = 17;
 
 // Device view of a preconditioned polynomial, passed to kernels by value.
 struct DevPoly {

@@ -1118,8 +1118,8 @@ extern "C" fpe_status fpe_tensor_stats(fpe_poly_t P, int64_t *stats, int n, void
 
 extern "C" fpe_status fpe_cert_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream) {
   using namespace fpe;
-  if (!P || !stats || n < 2) {
-    set_error("fpe_cert_stats: NULL handle or output, or n < 2");
+  if (!P || !stats || n < 1) {
+    set_error("fpe_cert_stats: NULL handle or output, or n < 1");
     return FPE_ERR_INVALID_ARG;
   }
   for (int i = 0; i < n; ++i) stats[i] = 0;
@@ -1134,6 +1134,5 @@ extern "C" fpe_status fpe_cert_stats(fpe_poly_t P, int64_t *stats, int n, void *
   if (prev >= 0 && prev != P->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, "fpe_cert_stats");
   stats[0] = c[kCntResum];
-  stats[1] = c[kCntResumGroups];
   return FPE_OK;
 }

@@ -146,30 +146,15 @@ __host__ __device__ __forceinline__ void mult_bounds_dd(double hr, double lr, do
   }
 }
 
-// smallest |w| = |2^beta z| at which the top-down pass sums in blocks of eight
-// (above it the terms decay slowly, long stretches of them are alike, and a
-// single Horner chain rounds its growing partial sum at every step)
-constexpr float kTopBlockMinW = 0.9f;
-
 // Horner over trimmed indices [lo, hi] on the rescaled coefficients b:
 // returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-lo) = h * 2^rho(lo).
 // Piece j runs at w_j = 2^beta_j z; entering piece j from j+1 multiplies h by
 // 2^delta_j (both exact).  Every term of a window has |h| <= L 2^(T + 66),
 // so nothing overflows.
-//
-// Blocks of eight (LONG: the lane chunks of long windows; with z8 = z^8 in
-// extended double-double, blocks8 set, and |w| >= kTopBlockMinW): eight steps
-// from k + 1 down to k - 7 are
-//   h_{k-7} = w^8 h_{k+1} + s,  s = b_{k-7} + w (b_{k-6} + ... + w b_k),
-// s by Horner with the exact w and the step by w^8 = 2^(8 beta) z8 in
-// double-double (36 FMA per eight terms instead of 32): the partial sum h
-// is rounded once per block, so over long windows of alike terms the
-// certificate grows with L / 8 such roundings instead of L.
-template <bool CC, bool CZ, bool LONG>
+template <bool CC, bool CZ>
 __host__ __device__ __forceinline__ void window_horner(const DevPoly &P, const double *__restrict__ b, double zr,
-                                                       double zi, long long lo, long long hi, const xdd &z8,
-                                                       bool blocks8, double &hr, double &hm, long long &rho_lo,
-                                                       Cert &ct) {
+                                                       double zi, long long lo, long long hi, double &hr,
+                                                       double &hm, long long &rho_lo, Cert &ct) {
   int j = P.piece_first[hi >> P.log2_piece];
   while (P.piece_k0[j + 1] <= hi) ++j;
   if (CC) {
@@ -192,40 +177,6 @@ __host__ __device__ __forceinline__ void window_horner(const DevPoly &P, const d
     float Wu, Wd;
     mult_bounds<CZ>(wr, wi, Wu, Wd);
     ok = ok && Wd >= kCertMinMult;
-    const int s8 = (int)z8.e + 8 * beta;
-    if (LONG && blocks8 && k - 15 >= k0 && Wd >= kTopBlockMinW && s8 > -900 && s8 < 900) {
-      const double ahr = scale2(z8.rh, s8), alr = scale2(z8.rl, s8);
-      const double ahi = CZ ? scale2(z8.ih, s8) : 0.0, ali = CZ ? scale2(z8.il, s8) : 0.0;
-      float Au, Ad, Al;
-      mult_bounds_dd<CZ>(ahr, alr, ahi, ali, Au, Ad, Al);
-      ok = ok && Ad >= kCertMinMult;
-      for (; k - 7 >= k0; k -= 8) {
-        double sr, si;
-        float Es = 0.0f, Ss = FPE_LDG(&bmag[k]);
-        if (CC) {
-          const double2 c = FPE_LDG(reinterpret_cast<const double2 *>(b) + k);
-          sr = c.x;
-          si = c.y;
-        } else {
-          sr = FPE_LDG(b + k);
-          si = 0.0;
-        }
-#pragma unroll
-        for (int t = 1; t < 8; ++t) {
-          double cr, ci;
-          if (CC) {
-            const double2 c = FPE_LDG(reinterpret_cast<const double2 *>(b) + (k - t));
-            cr = c.x;
-            ci = c.y;
-          } else {
-            cr = FPE_LDG(b + (k - t));
-            ci = 0.0;
-          }
-          cstep_w<CC, CZ>(sr, si, wr, wi, cr, ci, FPE_LDG(&bmag[k - t]), Wu, Wd, Es, Ss);
-        }
-        cstep_v<CC, CZ>(hr, hm, ahr, alr, ahi, ali, sr, si, Au, Ad, Al, Es, Ss, E, S);  // h <- w^8 h + s
-      }
-    }
     if (CC) {
       const double2 *b2 = reinterpret_cast<const double2 *>(b);
 #pragma unroll 4
@@ -344,22 +295,17 @@ __host__ __device__ __forceinline__ void rev_blocks(const double *__restrict__ b
   S = mul_dn(S, Cd);
 }
 
-// largest |w| at which the bottom-up pass sums in blocks of eight rather than four
-constexpr float kBlock8MaxW = 1.1f;
-
 // Bottom-up Horner over trimmed indices [lo, hi] with multiplier 1/z:
 // returns h with sum_{k=lo}^{hi} b_k 2^rho(k) z^(k-hi) = h * 2^rho(hi).
-// 1/z = u 2^ue with u in extended double-double (its powers up[0..3] = u^3,
-// u^4, u^7, u^8 likewise, each with its own exponent).  Within piece j the
+// 1/z = u 2^ue with u in extended double-double (its powers up[0], up[1] =
+// u^3, u^4 likewise, each with its own exponent).  Within piece j the
 // step from k-1 to k multiplies by v_j = 2^-beta_j / z; crossing from piece
 // j to j+1 first scales h by 2^-delta_j.  A single step is 8 FMA for complex
 // z and coefficients (v in double-double).  With blocks set, runs of a piece
-// go in blocks (rev_blocks): of eight terms (LONG) while |w| <= kBlock8MaxW, where
-// the terms are alike over long stretches and the block steps are what the
-// certificate sees, of four while |w| <= kBlockMaxW.  v and its powers are
+// go in blocks of four (rev_blocks) while |w| <= kBlockMaxW.  v and its powers are
 // within 2^-96 of the exact ones (a reciprocal good to 2^-100, then a few
 // 128-bit products), which the threshold kCertC allows for.
-template <bool CC, bool CZ, bool LONG>
+template <bool CC, bool CZ>
 __host__ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, const double *__restrict__ b,
                                                            const xdd &u, const xdd *up, bool blocks, int ue,
                                                            double zr, double zi, long long lo, long long hi,
@@ -399,10 +345,7 @@ __host__ __device__ __forceinline__ void window_horner_rev(const DevPoly &P, con
       // rounded at each of the block sum's steps, costs more in the certificate
       // than the single steps' double-double roundings (8 FMA a term, not 5);
       // v^B and its low part stay normal for the shifts allowed
-      if (LONG && kend - k + 1 >= 16 && sh > -100 && sh < 100 && Wu <= kBlock8MaxW)
-        rev_blocks<CC, CZ, 8>(b, bmag, k, kend, wr, wi, Wu, Wd, vhr, vlr, vhi, vli, Vu, Vd, Vl, up[3], up[2], sh,
-                              hr, hm, E, S, ok);
-      else if (kend - k + 1 >= 8 && sh > -200 && sh < 200 && Wu <= kBlockMaxW)
+      if (kend - k + 1 >= 8 && sh > -200 && sh < 200 && Wu <= kBlockMaxW)
         rev_blocks<CC, CZ, 4>(b, bmag, k, kend, wr, wi, Wu, Wd, vhr, vlr, vhi, vli, Vu, Vd, Vl, up[1], up[0], sh,
                               hr, hm, E, S, ok);
     }

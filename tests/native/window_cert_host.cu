@@ -28,28 +28,17 @@ static DevPoly make_poly(const double *b, int cc, const int32_t *k0, const int32
   return P;
 }
 
-template <bool CC, bool CZ>
-static void top(const DevPoly &P, double zr, double zi, long long lo, long long hi, int blocks, double *out,
-                long long *rho, Cert &ct) {
-  // z^8 as the evaluation kernels form it
-  int f;
-  frexp(fmax(fabs(zr), fabs(zi)), &f);
-  const xdd z8 = xdd_from_xint(xint_pow_z(zr, zi, 8, f));
-  window_horner<CC, CZ, true>(P, P.b, zr, zi, lo, hi, z8, blocks != 0, out[0], out[1], *rho, ct);
-}
-
-// top-down pass over [lo, hi] (blocks of eight allowed when blocks is set):
-// out = (hr, hm), *rho = rho(lo), es = (E, S); returns ok
+// top-down pass over [lo, hi]: out = (hr, hm), *rho = rho(lo), es = (E, S); returns ok
 extern "C" int wc_top(const double *b, int cc, int cz, const int32_t *k0, const int32_t *beta, const int32_t *delta,
                       const int64_t *rho0, const int32_t *first, int npieces, int log2_piece, double zr, double zi,
-                      long long lo, long long hi, int blocks, double *out, long long *rho, float *es) {
+                      long long lo, long long hi, double *out, long long *rho, float *es) {
   const DevPoly P = make_poly(b, cc, k0, beta, delta, rho0, first, npieces, log2_piece);
   Cert ct;
   if (!cz) zi = 0.0;
-  if (cc && cz) top<true, true>(P, zr, zi, lo, hi, blocks, out, rho, ct);
-  else if (cc) top<true, false>(P, zr, zi, lo, hi, blocks, out, rho, ct);
-  else if (cz) top<false, true>(P, zr, zi, lo, hi, blocks, out, rho, ct);
-  else top<false, false>(P, zr, zi, lo, hi, blocks, out, rho, ct);
+  if (cc && cz) window_horner<true, true>(P, P.b, zr, zi, lo, hi, out[0], out[1], *rho, ct);
+  else if (cc) window_horner<true, false>(P, P.b, zr, zi, lo, hi, out[0], out[1], *rho, ct);
+  else if (cz) window_horner<false, true>(P, P.b, zr, zi, lo, hi, out[0], out[1], *rho, ct);
+  else window_horner<false, false>(P, P.b, zr, zi, lo, hi, out[0], out[1], *rho, ct);
   es[0] = ct.E;
   es[1] = ct.S;
   return ct.ok;
@@ -64,10 +53,9 @@ static void rev(const DevPoly &P, double zr, double zi, long long lo, long long 
   const double mr = ldexp(zr, -f), mi = ldexp(zi, -f);
   const xint u = recip_xint(mr, mi);
   const xdd u1 = xdd_from_xint(u);
-  const xint u2 = xint_sqr(u), u3 = xint_mul(u2, u), u4 = xint_sqr(u2);
-  const xdd up[4] = {xdd_from_xint(u3), xdd_from_xint(u4), xdd_from_xint(xint_mul(u4, u3)),
-                     xdd_from_xint(xint_sqr(u4))};
-  window_horner_rev<CC, CZ, true>(P, P.b, u1, up, blocks != 0, -f, zr, zi, lo, hi, out[0], out[1], *rho, ct);
+  const xint u2 = xint_sqr(u);
+  const xdd up[2] = {xdd_from_xint(xint_mul(u2, u)), xdd_from_xint(xint_sqr(u2))};
+  window_horner_rev<CC, CZ>(P, P.b, u1, up, blocks != 0, -f, zr, zi, lo, hi, out[0], out[1], *rho, ct);
 }
 
 // bottom-up pass over [lo, hi]: out = (hr, hm), *rho = rho(hi), es = (E, S); returns ok
