@@ -136,8 +136,9 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
  *     |P_gpu - P| <= 2^-50 sum |a_k||z|^k   (FP64 modes, p = 53),
  * with the dropped terms of §6 inside that budget (fpe_cert_stats counts the
  * re-summed windows).  Longer windows are cut into lane chunks that are
- * summed exactly on the integer pipe, as with FPE_ACCURATE (on this GPU that
- * costs less than FP64 with certificates).  Windows of at least 384 terms inside one coefficient
+ * summed exactly on the integer pipe, as with FPE_ACCURATE, and so is every
+ * window of real points with real coefficients (on this GPU that costs less
+ * than FP64 with certificates).  Windows of at least 384 terms inside one coefficient
  * piece are summed exactly on the tensor cores (fpe_set_tensor_path).  A
  * window with at most a quarter of its indices in G_p (FPE_FORCE_SPARSE: any
  * window; FPE_FORCE_DENSE: none) is summed over its good indices alone, by

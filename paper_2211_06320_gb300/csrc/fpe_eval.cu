@@ -24,7 +24,11 @@
 // Top-down over the whole window (the paper's z^l times Horner) rounds a
 // partial sum already as large as P(z) at every one of the ~T/lambda steps
 // below the peak, which in FP64 exceeds 2^-50 S(z).  FPE_ACCURATE sums
-// top-down on the integer pipe in 128-bit fixed point instead.
+// top-down on the integer pipe in 128-bit fixed point instead, and so does
+// the default mode for the lane chunks of long windows and for every window
+// of real points with real coefficients: on this GPU (FP64 at about 1.7 FMA
+// per cycle per SM) the integer pipe sums those faster than the FP64 passes
+// with their certificates.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -187,36 +191,78 @@ __global__ void k_locate(DevPoly P, int n, const double *__restrict__ zre, const
   rank[p] = atomicAdd(&hist[k], 1u);  // the point's place within its bin
 }
 
-// exclusive scan of the nbins-word histogram (a multiple of 1024) into
-// cursors; resets the counters and records where each tensor-core piece's
-// points start in bucketed order
-__global__ void k_scan_bins(uint32_t *bins, int nbins) {
-  __shared__ uint32_t part[1024];
-  const int per = nbins / 1024;
-  int t = threadIdx.x;
-  uint32_t s = 0;
-  for (int i = 0; i < per; ++i) s += bins[t * per + i];
-  part[t] = s;
+// Exclusive scan of the nbins-word histogram (nbins a multiple of
+// kScanTile) into cursors, in two launches of one 256-thread block per tile
+// of kScanTile bins (coalesced 16-byte loads): k_scan_tiles writes each
+// tile's total after the counters, k_scan_bins adds the totals of the tiles
+// before its own to a scan of the tile.  k_scan_bins also resets the
+// counters and records where each tensor-core piece's points start in
+// bucketed order (a piece's first bin starts a tile).
+constexpr int kScanTile = 1024;
+static_assert(kNumBins % kScanTile == 0 && kTcBinsPerPiece % kScanTile == 0, "tiles of whole bins");
+
+__device__ __forceinline__ uint32_t block_sum256(uint32_t v, uint32_t *red) {
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = t >= off ? part[t - off] : 0u;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  uint32_t run = part[t] - s;
-  for (int i = 0; i < per; ++i) {
-    const uint32_t c = bins[t * per + i];
-    bins[nbins + t * per + i] = run;
-    run += c;
-  }
+  uint32_t tot = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) tot += red[i];
+  return tot;
+}
+
+__global__ void __launch_bounds__(256) k_scan_tiles(uint32_t *bins, int nbins) {
+  __shared__ uint32_t red[8];
+  const uint4 v = reinterpret_cast<const uint4 *>(bins + (size_t)blockIdx.x * kScanTile)[threadIdx.x];
+  const uint32_t tot = block_sum256(v.x + v.y + v.z + v.w, red);
+  if (threadIdx.x == 0) bins[2 * nbins + kNumCounters + blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_scan_bins(uint32_t *bins, int nbins) {
+  __shared__ uint32_t red[8], wsum[8];
+  const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int ntiles = nbins / kScanTile;
   uint32_t *cnt = bins + 2 * nbins;
-  if (t < kNumCounters) cnt[t] = 0;
-  __syncthreads();
-  if (t <= kTcMaxPieces) {
-    const int b = kNumBins + t * kTcBinsPerPiece;
-    cnt[kCntTcStart + t] = (t < kTcMaxPieces && b < nbins) ? bins[nbins + b] : part[1023];
+  const uint32_t *tile_tot = cnt + kNumCounters;
+  uint32_t part = 0;  // the tiles before this one
+  for (int i = t; i < b; i += 256) part += tile_tot[i];
+  const uint32_t off = block_sum256(part, red);
+  const uint4 v = reinterpret_cast<const uint4 *>(bins + (size_t)b * kScanTile)[t];
+  const uint32_t own = v.x + v.y + v.z + v.w;
+  uint32_t inc = own;  // inclusive scan of the threads' sums within the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
   }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  uint32_t before = 0;  // the warps before this one
+  for (int i = 0; i < wid; ++i) before += wsum[i];
+  uint4 o4;
+  o4.x = off + before + inc - own;
+  o4.y = o4.x + v.x;
+  o4.z = o4.y + v.y;
+  o4.w = o4.z + v.z;
+  reinterpret_cast<uint4 *>(bins + nbins + (size_t)b * kScanTile)[t] = o4;
+  // counters: reset by block 0, except the tensor-core piece starts, which the
+  // block holding the piece's first bin writes (the last block: pieces
+  // without bins, and the total)
+  if (b == 0 && t < kNumCounters && (t < kCntTcStart || t > kCntTcStart + kTcMaxPieces)) cnt[t] = 0;
+  if (t <= kTcMaxPieces) {
+    const int first = kNumBins + t * kTcBinsPerPiece;
+    if (t < kTcMaxPieces && first < nbins) {
+      if (first == b * kScanTile) cnt[kCntTcStart + t] = off;
+    } else if (b == ntiles - 1) {
+      uint32_t tot = 0;
+      for (int i = 0; i < 8; ++i) tot += wsum[i];
+      cnt[kCntTcStart + t] = off + tot;
+    }
+  }
+}
+
+static void launch_scan_bins(uint32_t *bins, int nbins, cudaStream_t st) {
+  k_scan_tiles<<<nbins / kScanTile, 256, 0, st>>>(bins, nbins);
+  k_scan_bins<<<nbins / kScanTile, 256, 0, st>>>(bins, nbins);
 }
 
 template <bool CZ>
@@ -625,8 +671,33 @@ __device__ __forceinline__ void list_resum(uint32_t *cnt, uint32_t *list, int q)
   list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)q;
 }
 
+// a b for xints of which only the parts the flags allow are nonzero: VC, a
+// complex; MC, b complex.  Real operands take one 128-bit product instead of
+// four, with the result xint_mul would give.
+template <bool VC, bool MC>
+__device__ __forceinline__ xint xint_mul_k(const xint &a, const xint &b) {
+  if (MC) return xint_mul(a, b);
+  if (!VC) return xint_norm(mulhi128(a.x, b.x), a.sx ^ b.sx, 0, 0, a.e + b.e + 2);
+  return xint_norm(mulhi128(a.x, b.x), a.sx ^ b.sx, mulhi128(a.y, b.x), a.sy ^ b.sx, a.e + b.e + 2);
+}
+
+// z^n (n >= 0) by binary powering on the integer pipe; CZ false: z real
+template <bool CZ>
+__device__ __forceinline__ xint xint_pow_z_k(double zr, double zi, long long n, int f) {
+  if (CZ || n <= 0) return xint_pow_z(zr, zi, n, f);
+  const double mr = scale2(zr, -f);
+  const xint z = xint_norm(u128_from_unit(mr), mr < 0.0, 0, 0, -1);
+  xint r = z;
+  for (int b = 62 - __clzll(n); b >= 0; --b) {
+    r = xint_mul_k<false, false>(r, r);
+    if ((n >> b) & 1) r = xint_mul_k<false, false>(r, z);
+  }
+  r.e += (long long)f * n;
+  return r;
+}
+
 // One point of a short window (L <= the long-window threshold), or a special point: its
-// window's sum, then the power z^(base + v) in extended double-double.  A default-mode
+// window's sum, then the power z^(base + v).  A default-mode
 // FP64 sum that fails its certificate is listed (resum, at bucketed position q) for
 // k_resum and its point left to it.
 template <bool CC, bool CZ, bool ACC, bool F32, bool BATCH>
@@ -654,9 +725,14 @@ __device__ __forceinline__ void sum_point(const DevPoly &P0, const DevPoly *__re
         const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
         const xint X = window_sum_sparse<CC>(P, r.zr, CZ ? r.zi : 0.0, f, r.lo, r.hi);
         o = xc64_from_xint(xint_mul(X, xint_pow_z(r.zr, CZ ? r.zi : 0.0, r.lo + P.v, f)));
-      } else if (ACC) {
-        const xdd X = window_sum_int<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
-        o = xdd_out(xdd_mul(X, xdd_pow_int(r.zr, r.zi, base + P.v)));
+      } else if (ACC || (!CC && !CZ)) {
+        // FPE_ACCURATE, and real points with real coefficients in every mode:
+        // the window exactly on the integer pipe (for real arithmetic this
+        // costs less on this GPU than the FP64 pass with its certificate and
+        // the re-sums of the windows it rejects), z^(l + v) likewise
+        const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
+        const xint X = window_sum_int_x<CC, CZ>(P, r.zr, r.zi, r.lo, r.hi);
+        o = xc64_from_xint(xint_mul_k<CC || CZ, CZ>(X, xint_pow_z_k<CZ>(r.zr, r.zi, r.lo + P.v, f)));
       } else {  // bookkeeping in fixed point (integer pipe): 1/z, its powers, the final product
         const int f = frexp_exp(fmax(fabs(r.zr), fabs(r.zi)));
         const double mr = scale2(r.zr, -f), mi = scale2(r.zi, -f);
@@ -752,31 +828,6 @@ __global__ void __launch_bounds__(128, kSumBlocksPerSm) k_sum_short(DevPoly P0, 
   if (r.flags & kPointTC) return;
   if (r.flags || r.hi - r.lo + 1 <= long_window)
     sum_point<CC, CZ, ACC, F32, BATCH>(P0, table, r, q, cnt, resum, out, nterms, bits_lost);
-}
-
-// a b for xints of which only the parts the flags allow are nonzero: VC, a
-// complex; MC, b complex.  Real operands take one 128-bit product instead of
-// four, with the result xint_mul would give.
-template <bool VC, bool MC>
-__device__ __forceinline__ xint xint_mul_k(const xint &a, const xint &b) {
-  if (MC) return xint_mul(a, b);
-  if (!VC) return xint_norm(mulhi128(a.x, b.x), a.sx ^ b.sx, 0, 0, a.e + b.e + 2);
-  return xint_norm(mulhi128(a.x, b.x), a.sx ^ b.sx, mulhi128(a.y, b.x), a.sy ^ b.sx, a.e + b.e + 2);
-}
-
-// z^n (n >= 1) by binary powering on the integer pipe; CZ false: z real
-template <bool CZ>
-__device__ __forceinline__ xint xint_pow_z_k(double zr, double zi, long long n, int f) {
-  if (CZ) return xint_pow_z(zr, zi, n, f);
-  const double mr = scale2(zr, -f);
-  const xint z = xint_norm(u128_from_unit(mr), mr < 0.0, 0, 0, -1);
-  xint r = z;
-  for (int b = 62 - __clzll(n); b >= 0; --b) {
-    r = xint_mul_k<false, false>(r, r);
-    if ((n >> b) & 1) r = xint_mul_k<false, false>(r, z);
-  }
-  r.e += (long long)f * n;
-  return r;
 }
 
 // sum_i (z^C)^i v_i over the 32 lanes' values, into lane 0, by a tree: at
@@ -1204,8 +1255,8 @@ fpe_status launch_front(fpe_poly_s *P, const double *z_re, const double *z_im, i
       k_locate<false><<<nb, 256, 0, st>>>(P->dev, n, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, tcw);
   }
   {
-    ProfScope ps("k_scan_bins", st);
-    k_scan_bins<<<1, 1024, 0, st>>>(w.bins, w.nbins);
+    ProfScope ps("k_scan_bins", st, 2);  // k_scan_tiles, k_scan_bins
+    launch_scan_bins(w.bins, w.nbins, st);
   }
   {
     ProfScope ps("k_scatter", st);
@@ -1441,7 +1492,8 @@ constexpr size_t kNaGroup = kNaOwner + align256(kNoAllocExtra * sizeof(int32_t))
 constexpr size_t kNaVal = kNaGroup + align256(kNoAllocExtra * sizeof(int32_t));
 constexpr size_t kNaCarry = kNaVal + align256((kNoAllocMaxPoints + kNoAllocExtra) * sizeof(xdd));
 constexpr size_t kNaBins = kNaCarry + align256((kNoAllocMaxPoints + kNoAllocExtra) * sizeof(xdd));
-constexpr size_t kNoAllocBytes = kNaBins + align256((2 * kNumBins + kNumCounters) * sizeof(uint32_t));
+constexpr size_t kNoAllocBytes =
+    kNaBins + align256((2 * kNumBins + kNumCounters + kNumBins / kScanTile) * sizeof(uint32_t));
 // the figure fpe.h states for the built-in scratch (9,429,248 bytes, about 9.0 MiB)
 static_assert(kNoAllocBytes == 9429248, "fpe.h states the size of the built-in scratch: update it with this layout");
 
@@ -1526,7 +1578,7 @@ extern "C" fpe_status fpe_eval_noalloc(fpe_poly_t P, const double *z_re, const d
         k_locate<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, 0);
       else
         k_locate<false><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, 0);
-      k_scan_bins<<<1, 1024, 0, st>>>(w.bins, kNumBins);
+      launch_scan_bins(w.bins, kNumBins, st);
       if (cz)
         k_scatter<true><<<nb, 256, 0, st>>>(P->dev, ni, z_re, z_im, w.lo, w.hi, w.kl, w.N, w.key, w.key + w.cap, w.bins, w.rec,
                                             w.long_list, w.long_ngroups, w.long_gbase, w.extra_owner,

@@ -195,7 +195,7 @@ struct Workspace {
   void *group_val = nullptr;        // per group: value (40-byte extended double-double)
   void *group_carry = nullptr;      // per group: carry into the next group
   int64_t extra_cap = 0;            // extra group slots (after the cap group-0 slots)
-  uint32_t *bins = nullptr;         // 2 * nbins histogram words + kNumCounters counters
+  uint32_t *bins = nullptr;         // 2 * nbins histogram words, kNumCounters counters, tile totals
   int nbins = kNumBins;             // bins of the last front pass (kNumBins, or + kTcBins with the tensor path)
   void *tc_tiles = nullptr;         // TcTile per tile
   int32_t *tc_item_base = nullptr;  // first work item of each tile (tiles + 1 entries)

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_tc_tau(const TcTile *__restrict__ tiles
   }
 }
 
-// per tile point (one thread each): u = w / tau, and the Z' slices of u^i
+// per tile point (four threads, eight powers each): u = w / tau, and the Z' slices of u^i
 // (i < 32) written to global memory in exactly the layout k_tc_sum copies
 // into shared memory as the MMA's A operand: per slice, the point's row of
 // 128 bytes (kappa = i for the real part of u^i, 32 + i for the imaginary
@@ -480,12 +480,15 @@ __global__ void __launch_bounds__(256) k_tc_tau(const TcTile *__restrict__ tiles
 // time, one chunk per slice and component); W^(2^k) = (u^32 tau^32)^(2^k),
 // W^(8 kTcFold), and Z's scale exponent.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
-                                                      const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
-                                                      const TcTau *__restrict__ taus, unsigned char *__restrict__ zglob,
-                                                      const uint32_t *cnt) {
-  const int ntiles = (int)cnt[kCntTcTiles], p = threadIdx.x;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+__global__ void __launch_bounds__(128) k_tc_pre(DevPoly P, const PointRec *__restrict__ rec,
+                                                const TcTile *__restrict__ tiles, TcPoint *__restrict__ pts,
+                                                const TcTau *__restrict__ taus, unsigned char *__restrict__ zglob,
+                                                const uint32_t *cnt) {
+  // a unit is 32 points of a tile (lane = point) times the four groups of eight
+  // powers (warp g: u^(8g) .. u^(8g + 7)); warp 0 also forms the points' W
+  const int ntiles = (int)cnt[kCntTcTiles], lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  for (int unit = blockIdx.x; unit < 4 * ntiles; unit += gridDim.x) {
+    const int t = unit >> 2, p = 32 * (unit & 3) + lane;
     const TcTile T = tiles[t];
     const bool valid = p < T.count;
     const xint zero = xint_norm(0, 0, 0, 0, 0);
@@ -503,58 +506,64 @@ __global__ void __launch_bounds__(kTcPoints) k_tc_pre(DevPoly P, const PointRec 
       const float my = (float)(unsigned long long)(u.y >> 64) * 0x1p-62f;
       const float l = 0.5f * log2f(fmaf(mx, mx, my * my)) + (float)u.e;
       eQ = max(0, (int)ceilf(31.0f * l + 1e-3f)) + 1;
+      // u^(8g) by squarings (u^24 = u^16 u^8)
       cur = xh_norm(1ull << 63, 0, 0, 0, 0);  // 1
+      if (g > 0) {
+        const xh u2 = xh_mul(uh, uh), u4 = xh_mul(u2, u2), u8 = xh_mul(u4, u4);
+        cur = g == 1 ? u8 : xh_mul(u8, u8);
+        if (g == 3) cur = xh_mul(cur, u8);
+      }
     }
-    // powers u^i in 64-bit mantissas: each product truncates at 2^-63, so u^31
-    // is within 2^-58 of its value relative to itself
+    // powers u^i in 64-bit mantissas: u^i comes from products whose exponents add
+    // up to i, each truncating at 2^-63 of its value, so u^31 is within 2^-58 of
+    // its value relative to itself
     unsigned char *zt = zglob + (size_t)t * kZBytes;
-#pragma unroll 1
-    for (int g = 0; g < kTB / 8; ++g) {
-      uint32_t wr[kSl][4], wi[kSl][4];  // bf16 pairs of powers 8g + 2q, 8g + 2q + 1
+    uint32_t wr[kSl][4], wi[kSl][4];  // bf16 pairs of powers 8g + 2q, 8g + 2q + 1
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t xr[2][kSl], xi[2][kSl];
-        DigitSign sr[2], si[2];
+    for (int q = 0; q < 4; ++q) {
+      uint32_t xr[2][kSl], xi[2][kSl];
+      DigitSign sr[2], si[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if ((g | q | h) != 0 && valid) cur = xh_mul(cur, uh);
-          // x 2^(e - 63) 2^(70 - eq) = x 2^-sh with eq = eQ + 1: fixed point below
-          // 2^69 (components <= 2^(eQ - 1))
-          const int sh = eQ + 1 + 63 - 70 - (int)cur.e;
-          bchunks70(valid ? shift_to70((u128)cur.x, sh) : (u128)0, xr[h]);
-          bchunks70(valid ? shift_to70((u128)cur.y, sh) : (u128)0, xi[h]);
-          sr[h] = digit_sign((uint32_t)cur.sx);
-          si[h] = digit_sign((uint32_t)cur.sy);
-        }
-#pragma unroll
-        for (int s = 0; s < kSl; ++s) {
-          wr[s][q] = bf16_pair(xr[0][s], sr[0], xr[1][s], sr[1]);
-          wi[s][q] = bf16_pair(xi[0][s], si[0], xi[1][s], si[1]);
-        }
+      for (int h = 0; h < 2; ++h) {
+        if ((q | h) != 0 && valid) cur = xh_mul(cur, uh);
+        // x 2^(e - 63) 2^(70 - eq) = x 2^-sh with eq = eQ + 1: fixed point below
+        // 2^69 (components <= 2^(eQ - 1))
+        const int sh = eQ + 1 + 63 - 70 - (int)cur.e;
+        bchunks70(valid ? shift_to70((u128)cur.x, sh) : (u128)0, xr[h]);
+        bchunks70(valid ? shift_to70((u128)cur.y, sh) : (u128)0, xi[h]);
+        sr[h] = digit_sign((uint32_t)cur.sx);
+        si[h] = digit_sign((uint32_t)cur.sy);
       }
 #pragma unroll
       for (int s = 0; s < kSl; ++s) {
-        *reinterpret_cast<uint4 *>(zt + s * kASlice + tc_swz(p, 8 * g)) =
-            make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-        *reinterpret_cast<uint4 *>(zt + s * kASlice + tc_swz(p, kTB + 8 * g)) =
-            make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+        wr[s][q] = bf16_pair(xr[0][s], sr[0], xr[1][s], sr[1]);
+        wi[s][q] = bf16_pair(xi[0][s], si[0], xi[1][s], si[1]);
       }
     }
-    TcPoint o;
-    xint W = zero;
-    if (valid) {  // W = u^32 tau^32 = w^32 from the 128-bit u: the block weights W^g and
-      // the Horner multipliers must not inherit the 64-bit powers' error
-      xint u32 = u;
-      for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
-      W = xint_mul(u32, taus[t].tau32);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+      *reinterpret_cast<uint4 *>(zt + s * kASlice + tc_swz(p, 8 * g)) =
+          make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+      *reinterpret_cast<uint4 *>(zt + s * kASlice + tc_swz(p, kTB + 8 * g)) =
+          make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
     }
-    o.W[0] = W;
-    for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
-    o.Wf = o.W[3];
-    for (int q = 1; (1 << q) <= kTcFold; ++q) o.Wf = xint_sqr(o.Wf);
-    o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
-    o.pad[0] = o.pad[1] = o.pad[2] = 0;
-    pts[(size_t)t * kTcPoints + p] = o;
+    if (g == 0) {
+      TcPoint o;
+      xint W = zero;
+      if (valid) {  // W = u^32 tau^32 = w^32 from the 128-bit u: the block weights W^g and
+        // the Horner multipliers must not inherit the 64-bit powers' error
+        xint u32 = u;
+        for (int k = 0; k < 5; ++k) u32 = xint_sqr(u32);
+        W = xint_mul(u32, taus[t].tau32);
+      }
+      o.W[0] = W;
+      for (int k = 1; k < 4; ++k) o.W[k] = xint_sqr(o.W[k - 1]);
+      o.Wf = o.W[3];
+      for (int q = 1; (1 << q) <= kTcFold; ++q) o.Wf = xint_sqr(o.Wf);
+      o.eq = eQ + 1;  // Z' = F 2^(eq - 70)
+      o.pad[0] = o.pad[1] = o.pad[2] = 0;
+      pts[(size_t)t * kTcPoints + p] = o;
+    }
   }
 }
 
@@ -1054,7 +1063,7 @@ fpe_status launch_tc_plan(fpe_poly_s *P, int n, cudaStream_t st) {
     ProfScope ps("k_tc_pre", st, 2);  // k_tc_tau, k_tc_pre
     k_tc_tau<<<std::min((tm + 7) / 8, tc_num_sms() * 8), 256, 0, st>>>((const TcTile *)w.tc_tiles,
                                                                        (TcTau *)w.tc_taus, cnt);
-    k_tc_pre<<<std::min(tm, tc_num_sms() * 16), kTcPoints, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles,
+    k_tc_pre<<<std::min(4 * tm, tc_num_sms() * 16), 128, 0, st>>>(P->dev, w.rec, (const TcTile *)w.tc_tiles,
                                                                     (TcPoint *)w.tc_points,
                                                                     (const TcTau *)w.tc_taus, (unsigned char *)w.tc_z, cnt);
   }

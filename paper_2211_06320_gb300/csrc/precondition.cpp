@@ -189,7 +189,8 @@ fpe_status alloc_workspace(Workspace &w, int64_t n) {
 fpe_status ensure_workspace(fpe_poly_s *P, int64_t n) {
   Workspace &w = P->ws;
   if (w.bins == nullptr) {
-    cudaError_t e = cudaMalloc((void **)&w.bins, (2 * (kNumBins + kTcBins) + kNumCounters) * sizeof(uint32_t));
+    cudaError_t e = cudaMalloc((void **)&w.bins,
+                                  (3 * (kNumBins + kTcBins) + kNumCounters) * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(bins)");
   }
   if (n <= w.cap) return FPE_OK;
