@@ -1193,14 +1193,14 @@ static int num_sms() {
 
 template <bool CC, bool CZ, bool ACC, bool F32>
 static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost,
-                         cudaStream_t st) {
+                         cudaStream_t st, int short_threads) {
   Workspace &w = P->ws;
   const int cap = (int)w.cap, xcap = (int)w.extra_cap;
   uint32_t *cnt = w.bins + 2 * w.nbins;
   {
     ProfScope ps("k_sum_short", st);
-    k_sum_short<CC, CZ, ACC, F32, false><<<(n + 127) / 128, 128, 0, st>>>(P->dev, nullptr, n, w.rec, out, nterms,
-                                                                          bits_lost, P->tune.long_window, cnt, w.key);
+    k_sum_short<CC, CZ, ACC, F32, false><<<(n + short_threads - 1) / short_threads, short_threads, 0, st>>>(
+        P->dev, nullptr, n, w.rec, out, nterms, bits_lost, P->tune.long_window, cnt, w.key);
   }
   if (!ACC && !F32) {
     ProfScope ps("k_resum", st);
@@ -1221,13 +1221,35 @@ static void launch_sums4(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, i
 }
 
 template <bool CC, bool CZ>
-static void launch_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost, cudaStream_t st) {
+static void launch_sums(fpe_poly_s *P, int n, fpe_xc64 *out, int32_t *nterms, int32_t *bits_lost, cudaStream_t st,
+                        int short_threads = 128) {
   if (P->dev.fp32)
-    launch_sums4<CC, CZ, false, true>(P, n, out, nterms, bits_lost, st);
+    launch_sums4<CC, CZ, false, true>(P, n, out, nterms, bits_lost, st, short_threads);
   else if (P->dev.accurate)
-    launch_sums4<CC, CZ, true, false>(P, n, out, nterms, bits_lost, st);
+    launch_sums4<CC, CZ, true, false>(P, n, out, nterms, bits_lost, st, short_threads);
   else
-    launch_sums4<CC, CZ, false, false>(P, n, out, nterms, bits_lost, st);
+    launch_sums4<CC, CZ, false, false>(P, n, out, nterms, bits_lost, st, short_threads);
+}
+
+// The handle's second stream and its two events, created on first use on the
+// current device (the handle's).
+static fpe_status ensure_tc_stream(fpe_poly_s *P) {
+  if (P->tc_stream && P->tc_fork && P->tc_join) return FPE_OK;
+  cudaError_t e = cudaSuccess;
+  if (!P->tc_stream) {
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetStreamPriorityRange");
+    // hi is the numerically smallest value: the greatest priority
+    const int prio = FPE_TC_CONCURRENT == 1 ? hi : 0;
+    e = cudaStreamCreateWithPriority(&P->tc_stream, cudaStreamNonBlocking, prio);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithPriority");
+  }
+  if (!P->tc_fork && (e = cudaEventCreateWithFlags(&P->tc_fork, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreateWithFlags");
+  if (!P->tc_join && (e = cudaEventCreateWithFlags(&P->tc_join, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreateWithFlags");
+  return FPE_OK;
 }
 
 // locate, bucket and scatter the points into P->ws.rec (the front of fpe_eval);
@@ -1286,18 +1308,42 @@ fpe_status launch_eval(fpe_poly_s *P, const double *z_re, const double *z_im, in
   const bool cz = z_im != nullptr;
   const bool cc = P->complex_coef;
   const bool tc = P->ws.nbins > kNumBins;
-  if (cc && cz)
-    launch_sums<true, true>(P, n, out, nterms, bits_lost, st);
-  else if (cc)
-    launch_sums<true, false>(P, n, out, nterms, bits_lost, st);
-  else if (cz)
-    launch_sums<false, true>(P, n, out, nterms, bits_lost, st);
-  else
-    launch_sums<false, false>(P, n, out, nterms, bits_lost, st);
-  if (tc) {
-    if ((s = launch_tc_plan(P, n, st)) != FPE_OK) return s;
-    if ((s = launch_tc_sums(P, n, out, nterms, bits_lost, st)) != FPE_OK) return s;
+  // With the tensor-core path the two kinds of window sums share nothing but
+  // the bucketed records (read only) and disjoint counters, and write
+  // disjoint outputs, so by default they run at once: the tensor-core branch
+  // (plan, slices, MMAs, finalize) on the handle's second stream, forked from
+  // st after the front and joined back into st.  Each SM then keeps its FP64
+  // pipe busy with k_sum_short beside the tensor and integer pipes' work.
+  cudaStream_t sf = st;  // the FP64 sums' stream
+  cudaStream_t stc = st;  // the tensor-core branch's stream
+  int short_threads = 128;
+  if (tc && FPE_TC_CONCURRENT != 0) {
+    if ((s = ensure_tc_stream(P)) != FPE_OK) return s;
+    cudaError_t e = cudaEventRecord(P->tc_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->tc_stream, P->tc_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core stream fork");
+    stc = P->tc_stream;
+    short_threads = kShortThreadsTc;
   }
+  fpe_status stc_status = FPE_OK;
+  if (tc) {
+    stc_status = launch_tc_plan(P, n, stc);
+    if (stc_status == FPE_OK) stc_status = launch_tc_sums(P, n, out, nterms, bits_lost, stc);
+  }
+  if (cc && cz)
+    launch_sums<true, true>(P, n, out, nterms, bits_lost, sf, short_threads);
+  else if (cc)
+    launch_sums<true, false>(P, n, out, nterms, bits_lost, sf, short_threads);
+  else if (cz)
+    launch_sums<false, true>(P, n, out, nterms, bits_lost, sf, short_threads);
+  else
+    launch_sums<false, false>(P, n, out, nterms, bits_lost, sf, short_threads);
+  if (stc != st) {  // join, also after a failed launch on the branch
+    cudaError_t e = cudaEventRecord(P->tc_join, stc);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->tc_join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core stream join");
+  }
+  if (stc_status != FPE_OK) return stc_status;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   P->last_n = n64;

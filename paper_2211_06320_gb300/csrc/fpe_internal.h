@@ -71,6 +71,24 @@ inline uint64_t qpack(double x) {
 #endif
 constexpr int kSumBlocksPerSm = FPE_SUM_BLOCKS_PER_SM;
 
+// Threads per block of k_sum_short when the tensor-core sums run beside it:
+// three warps (12288 registers) fit on an SM beside one k_tc_sum CTA
+// (17 warps of 96 registers), so the FP64 pipe keeps working while the
+// tensor and integer pipes take the long windows.
+#ifndef FPE_SHORT_THREADS_TC
+#define FPE_SHORT_THREADS_TC 96
+#endif
+constexpr int kShortThreadsTc = FPE_SHORT_THREADS_TC;
+static_assert(kShortThreadsTc % 32 == 0 && kShortThreadsTc <= 128, "whole warps, within the launch bound");
+
+// How fpe_eval runs the tensor-core sums against the FP64 ones: 0 one after
+// the other on the caller's stream; 1 on a second stream of the handle with
+// the highest priority, forked from and joined back into the caller's
+// stream; 2 the same at the default priority.
+#ifndef FPE_TC_CONCURRENT
+#define FPE_TC_CONCURRENT 1
+#endif
+
 // Bucketing of points by log2|z| before summation (points of similar modulus
 // get similar windows; §8.1 suggests grouping evaluations of similar size).
 constexpr int kNumBins = 4096;
@@ -236,6 +254,8 @@ struct fpe_poly_s {
   size_t aux_bytes = 0;
   fpe::Tuning tune;                     // launch parameters of the window sums
   double tune_ms = 0.0;                 // time per call of the setting fpe_autotune chose
+  cudaStream_t tc_stream = nullptr;     // the tensor-core sums' stream (created on first use)
+  cudaEvent_t tc_fork = nullptr, tc_join = nullptr;  // its fork from and join into the caller's stream
 };
 
 struct fpe_batch_s {

@@ -140,6 +140,9 @@ void free_handle(fpe_poly_s *P) {
   free_workspace(P->ws);
   if (P->aux) cudaFree(P->aux);
   if (P->d_status) cudaFree(P->d_status);
+  if (P->tc_stream) cudaStreamDestroy(P->tc_stream);
+  if (P->tc_fork) cudaEventDestroy(P->tc_fork);
+  if (P->tc_join) cudaEventDestroy(P->tc_join);
   cudaSetDevice(prev);
   if (P->deriv) free_handle(P->deriv);
   delete P;
