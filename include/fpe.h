@@ -346,7 +346,11 @@ fpe_status fpe_newton(fpe_poly_t P, const double *z_re, const double *z_im, int6
  * of the values P(z_j): dL/dz_j = g_j conj(P'(z_j)) with g_j = dL/dP(z_j) (the
  * conjugate Wirtinger convention; P is holomorphic in z).  P' is evaluated by
  * the FPE path (§7.2).  Requires FPE_WITH_DERIV.  g_re/g_im (g_im NULL = real)
- * and gz_re/gz_im (gz_im may be NULL) are device double[n].  Asynchronous.
+ * and gz_re/gz_im (gz_im may be NULL) are device double[n].  The gradient is
+ * written in FP64: where g conj(P') leaves the FP64 range it is +-inf (or NaN
+ * when an infinite part meets a zero one), and no status reports it; callers
+ * that need those points take P' from fpe_eval_deriv, whose values carry
+ * their own exponent.  Asynchronous.
  */
 fpe_status fpe_grad_points(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, const double *g_re,
                            const double *g_im, double *gz_re, double *gz_im, void *cuda_stream);
