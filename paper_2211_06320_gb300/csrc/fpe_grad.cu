@@ -18,6 +18,8 @@
 
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <mutex>
 
 #include "fpe_device.cuh"
 #include "fpe_internal.h"
@@ -298,6 +300,34 @@ static fpe_status eval_deriv_into(fpe_poly_s *P, const double *z_re, const doubl
   return launch_eval(P->deriv, z_re, z_im, n, D, nullptr, nullptr, st);
 }
 
+// fpe_newton evaluates P' on a second stream while P runs on the caller's
+// stream: the two evaluations use separate handles (workspaces, status words,
+// tensor-core streams) and separate halves of the scratch, so they can share
+// the GPU, and each fills the other's serial stretches (the fronts, the
+// planning launches, the exact re-sums).  One such stream per device, with
+// its fork and join events, is created on first use and kept until exit; the
+// mutex makes each fork / launch / join sequence atomic against other host
+// threads, which share the stream and the events.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static std::mutex g_side_mu;
+static std::map<int, SideStream> g_side;  // by device; guarded by g_side_mu
+
+static fpe_status side_stream(int device, SideStream **out) {
+  SideStream &ss = g_side[device];
+  cudaError_t e = cudaSuccess;
+  if (!ss.s && (e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  if (!ss.fork && (e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreateWithFlags");
+  if (!ss.join && (e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreateWithFlags");
+  *out = &ss;
+  return FPE_OK;
+}
+
 fpe_status launch_newton(fpe_poly_s *P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *inc,
                          double *znr, double *zni, cudaStream_t st) {
   if (n == 0) return FPE_OK;
@@ -305,8 +335,24 @@ fpe_status launch_newton(fpe_poly_s *P, const double *z_re, const double *z_im, 
   fpe_status s = aux_buffer(P, 2 * n * sizeof(fpe_xc64), &buf);
   if (s != FPE_OK) return s;
   fpe_xc64 *Pv = (fpe_xc64 *)buf, *Dv = Pv + n;
-  if ((s = launch_eval(P, z_re, z_im, n, Pv, nullptr, nullptr, st)) != FPE_OK) return s;
-  if ((s = eval_deriv_into(P, z_re, z_im, n, Dv, st)) != FPE_OK) return s;
+  if (P->deriv_zero || !P->deriv) {
+    if ((s = launch_eval(P, z_re, z_im, n, Pv, nullptr, nullptr, st)) != FPE_OK) return s;
+    if ((s = eval_deriv_into(P, z_re, z_im, n, Dv, st)) != FPE_OK) return s;
+  } else {
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    SideStream *ss = nullptr;
+    if ((s = side_stream(P->device, &ss)) != FPE_OK) return s;
+    cudaError_t e = cudaEventRecord(ss->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->s, ss->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "Newton stream fork");
+    const fpe_status sp = launch_eval(P, z_re, z_im, n, Pv, nullptr, nullptr, st);
+    const fpe_status sd = launch_eval(P->deriv, z_re, z_im, n, Dv, nullptr, nullptr, ss->s);
+    e = cudaEventRecord(ss->join, ss->s);  // join, also after a failed launch
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "Newton stream join");
+    if (sp != FPE_OK) return sp;
+    if (sd != FPE_OK) return sd;
+  }
   {
     ProfScope ps("k_newton_combine", st);
     k_newton_combine<<<(int)((n + 255) / 256), 256, 0, st>>>((int)n, Pv, Dv, z_re, z_im, inc, znr, zni);
