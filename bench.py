@@ -557,8 +557,16 @@ def main():
                 extras[key + "_evals_per_s"] = m / sec
                 # the plain scheme's count: 8 flop per complex term, d + 1 terms per point
                 fl = 8.0 * (args.degree + 1) * m
+                # FP64 instructions each complex term issues: plain, 4 FMA and the two
+                # multiplies of the coefficient's 2^-E scale; compensated, 4 TwoProd (2 each),
+                # 4 TwoSum (6 each), 6 adds of the error terms, 4 FMA of the error recurrence
+                # and the same 2 multiplies
+                ins = 44 if comp else 6
+                issue = ins * (args.degree + 1) * m / sec  # FP64 instructions per second
                 extras[key + "_fp64"] = {"points": m, "seconds": sec, "flops_8_per_term": fl,
-                                         "frac_of_fp64_peak": fl / sec / 1e12 / fp64_peak_tflops}
+                                         "frac_of_fp64_peak": fl / sec / 1e12 / fp64_peak_tflops,
+                                         "fp64_instructions_per_term": ins,
+                                         "frac_of_fp64_issue": issue / (fp64_peak_tflops * 1e12 / 2.0)}
             # accuracy on a sample against the oracle's extended-precision Horner
             import oracle
             sample = np.unique(np.concatenate([np.arange(48), np.argsort(-L)[:16]]))
