@@ -151,8 +151,15 @@ fpe_status fpe_precondition(const double *re, const double *im, const int64_t *e
  * u|P| + (2^-84 + L 2^-100) S for every input (u|P| from rounding the
  * output to FP64, 2^-84 S from the power z^l).
  * Asynchronous on cuda_stream.  The first call (and any call with a larger n
- * than before) allocates scratch memory on the handle.  Non-finite points
- * give NaN outputs and FPE_ERR_NONFINITE from the next fpe_sync().
+ * than before) allocates scratch memory on the handle.  When the tensor-core
+ * sums run, the call forks them onto a second stream of the handle (created
+ * on the first such call, at the device's highest stream priority) through
+ * an event recorded on cuda_stream, and makes cuda_stream wait for them
+ * through a second event: work queued on cuda_stream after the call sees
+ * every output.  A handle's calls must not overlap on the GPU
+ * (the handle's scratch is shared), so one handle is driven from one stream
+ * at a time.  Non-finite points give NaN outputs and FPE_ERR_NONFINITE from
+ * the next fpe_sync().
  */
 fpe_status fpe_eval(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *out,
                     int32_t *nterms, int32_t *bits_lost, void *cuda_stream);
@@ -336,7 +343,10 @@ fpe_status fpe_cert_stats(fpe_poly_t P, int64_t *stats, int n, void *cuda_stream
  * the same protection).  Requires FPE_WITH_DERIV.
  *   inc         device fpe_xc64[n]: P(z)/P'(z) (0 where P(z) = 0; NaN where only P' vanishes).
  *   z_next_re/im device double[n] or NULL: z - inc as FP64 (inf where inc overflows FP64).
- * Asynchronous; the first call allocates scratch on the handle.
+ * Asynchronous; the first call allocates scratch on the handle.  P' is
+ * evaluated on a second stream (one per device, created on first use and
+ * kept until exit) beside P on cuda_stream, forked from and joined back into
+ * cuda_stream, so the step is ordered on cuda_stream like any other call.
  */
 fpe_status fpe_newton(fpe_poly_t P, const double *z_re, const double *z_im, int64_t n, fpe_xc64 *inc,
                       double *z_next_re, double *z_next_im, void *cuda_stream);
