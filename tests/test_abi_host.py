@@ -198,3 +198,31 @@ def test_analyse_intervals_match_oracle_windows(F, family):
         clear = np.isnan(lo) | ((np.abs(lm - lo) > 1e-9) & (np.abs(lm - hi) > 1e-9))
         assert np.array_equal(kept[clear], pred[clear]), (family, lm)
     assert np.all(np.isnan(lo) == ~pre.good.astype(bool))
+
+
+def test_tensor_path_settings_host(F):
+    """The tensor-core threshold of a handle: 384 by default; 0 (off) and
+    [32, 2^30] accepted, anything else and a NULL handle refused without
+    changing the setting.  A flat cover is one long piece that qualifies;
+    FPE_FP32 and FPE_ACCURATE handles qualify none (those modes never take
+    the path)."""
+    lib = F._load()
+    c = W.unit_disk_complex(4096, np.random.default_rng(11))
+    for k in (0, 4096):  # |a_0| = |a_d| = 0.9: the largest scale at both ends, one flat piece
+        r = float(np.hypot(c.re[k], c.im[k])) or 1.0
+        c.re[k], c.im[k] = 0.9 * c.re[k] / r, 0.9 * c.im[k] / r
+    P = F.fpe_precondition(c.re, c.im, None, 53, F.FPE_HOST_ONLY)
+    assert F.fpe_get_tensor_path(P) == {"min_window": 384, "pieces": 1}
+    for mw in (0, 32, 1000, 1 << 30):
+        F.fpe_set_tensor_path(P, mw)
+        assert F.fpe_get_tensor_path(P)["min_window"] == mw
+    for mw in (-1, 1, 31, (1 << 30) + 1):
+        with pytest.raises(F.FpeError) as e:
+            F.fpe_set_tensor_path(P, mw)
+        assert e.value.status == F.FPE_ERR_INVALID_ARG
+    assert F.fpe_get_tensor_path(P)["min_window"] == 1 << 30
+    assert lib.fpe_set_tensor_path(None, 384) == F.FPE_ERR_INVALID_ARG
+    assert lib.fpe_get_tensor_path(None, None, None) == F.FPE_ERR_INVALID_ARG
+    for flag, p in ((F.FPE_FP32, 24), (F.FPE_ACCURATE, 53)):
+        Q = F.fpe_precondition(c.re, c.im, None, p, F.FPE_HOST_ONLY | flag)
+        assert F.fpe_get_tensor_path(Q)["pieces"] == 0
